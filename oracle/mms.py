@@ -1,0 +1,83 @@
+"""Manufactured-solution forcing S_MMS = d_t Q_ex + div Phi(Q_ex) - S(Q_ex) (Sec. 4).
+
+The derivatives are taken by forward-mode automatic differentiation of the exact
+fields (torch.func.jvp), so no derivative is written by hand.  Tracker components of
+the exact augmented state are the exact gradients of their parent fields (supplement,
+MMS section: trackers are initialised from the spatial derivatives of the fields).
+The forcing is applied to the conserved components only.
+"""
+from __future__ import annotations
+
+import torch
+from torch.func import jvp
+
+
+def _replace(xx, b, xb):
+    out = list(xx)
+    out[b] = xb
+    return tuple(out)
+
+
+def exact_augmented(system, exact, xx, t):
+    """Q+_ex = (Q_ex, trackers = grad of the parents) at coordinates xx and time t.
+
+    `exact(*xx, t)` returns the conserved exact fields [n_cons, *grid]."""
+    Qc = exact(*xx, t)
+    if system.K == system.n_cons:
+        return Qc
+    D = len(xx)
+    dP_b = []
+    for b in range(D):
+        def along_b(xb, b=b):
+            return torch.stack(system.parents(exact(*_replace(xx, b, xb), t)))
+        _, d = jvp(along_b, (xx[b],), (torch.ones_like(xx[b]),))
+        dP_b.append(d)
+    n_par = dP_b[0].shape[0]
+    dP = [[dP_b[b][p] for b in range(D)] for p in range(n_par)]
+    return torch.cat([Qc, torch.stack(system.trackers_from_grads(dP))])
+
+
+def mms_source(system, exact, xx, t):
+    """S_MMS(x, t) for the conserved components, [n_cons, *grid]."""
+    tt = torch.full_like(xx[0], float(t))
+    return mms_source_t(system, exact, xx, tt)
+
+
+def make_mms(system, exact, xx, dt=None, chunk=64):
+    """Callable t -> S_MMS(x, t) on the fixed node coordinates xx.
+
+    With a time step `dt`, the forcing is evaluated for `chunk` consecutive instants
+    t, t + dt, ... at once (the same definition, batched along a leading time axis to
+    amortise the differentiation overhead) and served from that cache."""
+    if dt is None:
+        return lambda t: mms_source(system, exact, xx, t)
+    cache = {"t0": None, "vals": None}
+
+    def fn(t):
+        t0 = cache["t0"]
+        if t0 is not None:
+            j = round((t - t0) / dt)
+            if 0 <= j < cache["vals"].shape[0] and abs(t - (t0 + j * dt)) <= 1e-9 * dt:
+                return cache["vals"][j]
+        ts = torch.tensor([t + j * dt for j in range(chunk)], dtype=torch.float64)
+        shp = (chunk,) + tuple(xx[0].shape)
+        tb = ts.reshape((chunk,) + (1,) * xx[0].dim()).expand(shp).contiguous()
+        xb = tuple(x.unsqueeze(0).expand(shp).contiguous() for x in xx)
+        vals = mms_source_t(system, exact, xb, tb)            # [n_cons, chunk, *grid]
+        cache["t0"], cache["vals"] = t, vals.transpose(0, 1).contiguous()
+        return cache["vals"][0]
+    return fn
+
+
+def mms_source_t(system, exact, xx, tt):
+    """S_MMS with a time tensor tt of the same shape as the coordinates."""
+    nc = system.n_cons
+    _, dQdt = jvp(lambda T: exact(*xx, T), (tt,), (torch.ones_like(tt),))
+    div = torch.zeros_like(dQdt)
+    for b in range(len(xx)):
+        def flux_b(xb, b=b):
+            return system.flux(exact_augmented(system, exact, _replace(xx, b, xb), tt))[:nc, b]
+        _, d = jvp(flux_b, (xx[b],), (torch.ones_like(xx[b]),))
+        div = div + d
+    Qp = exact_augmented(system, exact, xx, tt)
+    return dQdt + div - system.source(Qp)[:nc]
