@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused collide-and-stream step on one B300 (or N replicas).
+
+Default workload: compressible NSF with primitive trackers (K = 10) on D2Q9, a 1024^2
+periodic grid, reference/equilibrium-shifted FP32 populations, seeded Fourier fields
+around rho = 1, T = 1, Mach 0.3.  A step is one collide-and-stream pass over the whole
+grid (one kernel launch).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload nsf|mhd|adr] [--precision fp32|fp64|fp16]
+
+--impl reference times the CPU FP64 oracle on bounded samples of the same workload.
+Under torchrun (N > 1) every rank advances its own replica (weak scaling, no exchange)
+and rank 0 prints the line; the reference arm runs on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+import synthetic as syn  # noqa: E402
+
+PREC = {"fp64": 1, "fp32": 2, "fp16": 3}
+PREC_NAME = {"fp64": "f64", "fp32": "f32", "fp16": "f32 (f16 storage)"}
+STORE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "systems.cuh", "lattices.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2607_05668_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6400.0, "fallback"
+
+
+def profile_traffic(workload_key):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
+    when the summary is missing or was taken on other kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(workload_key)
+    if not d or d.get("source_sha") != kernel_source_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_case(workload, n=None):
+    if workload == "nsf":
+        return syn.NsfCase(n=n or 1024)
+    if workload == "mhd":
+        return syn.MhdCase(n=n or 256)
+    if workload == "adr":
+        return syn.AdrCase(n=n or 64)
+    raise ValueError(workload)
+
+
+def fields(workload, case):
+    return {"nsf": syn.nsf_fields, "mhd": syn.mhd_fields, "adr": syn.adr_fields}[workload](case)
+
+
+def scheme(W, L, workload, case, prec):
+    p = PREC[prec]
+    if workload == "nsf":
+        return W.nsf_scheme(case, p)
+    if workload == "mhd":
+        return W.mhd_scheme(case, p)
+    return W.adr_scheme(case, p)
+
+
+def kq(workload):
+    return {"nsf": (10, 9), "mhd": (11, 19), "adr": (3, 5)}[workload]
+
+
+def cells(workload, case):
+    return case.n ** (3 if workload == "mhd" else 2)
+
+
+# --------------------------------------------------------------------- our arm
+def run_ours(args):
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2607_05668_b300 import lbx as L, workloads as W
+
+    case = make_case(args.workload, args.n)
+    Q = fields(args.workload, case)
+    ncell = cells(args.workload, case)
+    K, q = kq(args.workload)
+    sch = scheme(W, L, args.workload, case, args.precision)
+    stream = torch.cuda.Stream()
+    st = L.State(sch, Q.cuda(), stream=stream)
+    st.step(args.warmup)
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        st.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    finite = st.check_finite()
+    value = ws * ncell * args.steps / (ms * 1e-3)
+
+    # roofline of the step kernel: algorithmic bytes 2 K q s per node update
+    bytes_launch = 2 * K * q * STORE_BYTES[args.precision] * ncell
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_launch / (ms_step * 1e-3) / 1e9
+    key = f"{args.workload}_{args.precision}_{case.n}"
+    traffic = profile_traffic(key)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch}
+    if args.precision == "fp64":
+        roof["note"] = "FP64 arithmetic on B300 is far below the HBM ridge; see fp64_alu"
+
+    # end to end through the C ABI with host buffers: init from pinned host fields,
+    # `steps` steps, moments back to pinned host memory
+    Qh = Q.contiguous().pin_memory()
+    out_h = torch.empty_like(Qh).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st2 = L.State(sch, Qh, stream=stream)
+    st2.step(args.steps)
+    Qd = st2.moments(device=True)
+    out_h.copy_(Qd, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    st2.close()
+    e2e = {"value": ws * ncell * args.steps / e2e_s, "unit": "LUP/s",
+           "h2d_bytes_per_step": Qh.numel() * 8 / args.steps,
+           "d2h_bytes_per_step": out_h.numel() * 8 / args.steps,
+           "run": f"lbx_init(host Q) + {args.steps} steps + lbx_moments -> host, per run"}
+    st.close()
+
+    result = {
+        "metric": "Lattice updates/s", "value": value, "unit": "LUP/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAME[args.precision], "data": "synthetic",
+        "config": {"workload": f"{args.workload}_d2q9_{case.n}x{case.n}_{args.precision}" if args.workload == "nsf"
+                   else f"{args.workload}_{case.n}_{args.precision}",
+                   "grid": [case.n] * (3 if args.workload == "mhd" else 2), "components": K, "velocities": q,
+                   "precision": args.precision, "l2": "inputs larger than L2 (each population buffer "
+                   f"{bytes_launch / 2 / 1e6:.0f} MB > 126 MB)", "parallelism": f"replicas x{ws}"},
+        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "finite": finite,
+        "clocks": clk.summary(),
+    }
+    if args.precision == "fp64" or args.probe:
+        pk = L.probe_peaks(2 << 30, stream=stream)
+        result["probe"] = pk
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(args, case)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- CPU oracle arm
+def _oracle_scheme(workload, case, shape):
+    import oracle
+    from oracle import systems as S
+    if workload == "nsf":
+        sysm = S.NsfPrimitive(case.gamma, case.R, case.mu, case.kappa, case.g_tau * case.dt)
+        lat = "D2Q9"
+    elif workload == "mhd":
+        sysm = S.MhdCurrent(case.gamma, case.eta, case.g_tau * case.dt)
+        lat = "D3Q19"
+    else:
+        sysm = S.AdrCascade(case.a_phys, case.nu, case.g_tau * case.dt)
+        lat = "D2Q5"
+    tau = oracle.tau_vector(sysm, case.dt, tau_R=getattr(case, "tau_R", None),
+                            tau_cons=getattr(case, "tau_u", None), g_tau=case.g_tau)
+    return oracle.Scheme(sysm, oracle.LATTICES[lat], shape, case.dx, case.dt, tau)
+
+
+def _oracle_sample(workload, case, rows):
+    """The oracle on a periodic slab of `rows` rows of the full grid (same per-node work)."""
+    Q = fields(workload, case)
+    Qs = Q[..., :rows, :].contiguous() if workload != "mhd" else Q[:, :rows].contiguous()
+    shape = tuple(Qs.shape[1:])
+    sch = _oracle_scheme(workload, case, shape)
+    return sch, sch.init(Qs), int(Qs[0].numel())
+
+
+def cpu_baseline(args, case, budget_s=15.0):
+    cores = torch.get_num_threads()
+    rows = 64 if args.workload != "mhd" else 8
+    sch, f, n = _oracle_sample(args.workload, case, rows)
+    f = sch.step(f, 0.0)                      # warm up
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        f = sch.step(f, 0.0)
+        steps += 1
+    el = time.perf_counter() - t0
+    return {"value": steps * n / el, "unit": "LUP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps on a periodic {rows}-row slab of the {case.n}-wide grid "
+                      f"({n} nodes), {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    case = make_case(args.workload, args.n)
+    K, q = kq(args.workload)
+    # each step is one oracle step on a slab sized so the whole run stays within minutes
+    budget = 150.0
+    sch, f, n = _oracle_sample(args.workload, case, 8 if args.workload != "mhd" else 2)
+    t0 = time.perf_counter()
+    f = sch.step(f, 0.0)
+    per_step = time.perf_counter() - t0
+    total = args.steps + args.warmup
+    rows = max(2, min(case.n, int(8 * budget / max(per_step * total, 1e-9))))
+    if args.workload == "mhd":
+        rows = max(2, min(case.n, rows // 4))
+    sch, f, n = _oracle_sample(args.workload, case, rows)
+    for _ in range(args.warmup):
+        f = sch.step(f, 0.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = sch.step(f, 0.0)
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    cores = torch.get_num_threads()
+    sample = f"each step: one FP64 oracle step on a periodic {rows}-row slab ({n} nodes) of the {case.n}-wide grid"
+    print(json.dumps({
+        "impl": "reference", "metric": "Lattice updates/s", "value": value, "unit": "LUP/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}_{case.n}_{args.precision}", "grid": case.n, "components": K,
+                   "velocities": q},
+        "cpu_baseline": {"value": value, "unit": "LUP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "LUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nsf", choices=["nsf", "mhd", "adr"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
+    ap.add_argument("--n", type=int, default=None, help="grid size override")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--probe", action="store_true", help="also run the copy / FMA peak probes")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * lbx.h - C ABI of the B300 (sm_103a) kinetic-relaxation lattice Boltzmann library.
+ *
+ * The library advances the discrete-velocity kinetic relaxation scheme that the paper
+ * "Automated Derivation of Lattice Boltzmann Methods for Systems of Conservation Laws"
+ * derives for a system dQ/dt + div Phi(Q) = S(Q) (Eq. pde_target): one population set
+ * f_{k,i} per conserved or gradient-tracker component k (Sec. 2.2.1), the exact-flux
+ * equilibrium f^eq_{k,i} = w_i (Q_k + c_i . [(dt/dx) Phi_k] / c_s^2) (Eq. feq) and the
+ * BGK collide-and-stream update (Eq. lbe_update)
+ *     f_{k,i}(x + c_i dx, t + dt) = f - (f - f^eq)/tau_k + dt w_i S_k(x, t + dt/2).
+ * The workflow follows the paper's statement of the problem (Algorithm 1, Fig. 1):
+ * declare the system, derive the lattice and grid scaling, then init / step(n) /
+ * moments / sub-characteristic check.
+ *
+ * Conventions shared by every call
+ *  - Status: every call returns an lbx_status; nothing calls exit() or abort().  The
+ *    message of the last failure on the calling thread is lbx_last_error().
+ *  - Fields: Q arrays are float64 [K][cells], cells = nz*ny*nx with x fastest (C order),
+ *    node coordinates x_i = i/N on the periodic unit domain.  Values are the
+ *    nondimensional physical ones: the flux factor dt/dx and the source factor dt are
+ *    applied inside the library (Eq. feq, Eq. lbe_update).
+ *  - Host arrays passed in or out are only accessed during the call.  Device pointers
+ *    must be device memory of the current CUDA device.
+ *  - Streams: device work is enqueued on the state's stream and is asynchronous unless
+ *    the call returns host values (those calls synchronise that stream).
+ *  - Ownership: handles are created and destroyed by the library.  Buffers the caller
+ *    passes in (f_buf_a/f_buf_b) stay owned by the caller and must outlive the state.
+ */
+#ifndef LBX_H
+#define LBX_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBX_OK = 0,
+    LBX_ERR_ARG = 1,          /* invalid argument, combination or size               */
+    LBX_ERR_CUDA = 2,         /* a CUDA runtime call failed                           */
+    LBX_ERR_OOM = 3,          /* device allocation failed                             */
+    LBX_ERR_SUBCHAR = 4,      /* sub-characteristic bound violated (Sec. 2.3.2)       */
+    LBX_ERR_NONFINITE = 5,    /* a NaN/Inf was detected in the state                  */
+    LBX_ERR_TIMEOUT = 6,      /* a device-side wait ran out of its iteration budget   */
+    LBX_ERR_STATE = 7,        /* call not valid for this state (e.g. flag raised)     */
+    LBX_ERR_IO = 8,           /* file error, bad magic, hash or CRC mismatch          */
+    LBX_ERR_UNSUPPORTED = 9   /* combination not compiled into this library           */
+} lbx_status;
+
+/* System families (Sec. 3).  Component orders:
+ *   ADR_CASCADE      (u, G_x, G_y)                                        K = 3, 2D
+ *   NSF_PRIM_TRACK   (rho, m_x, m_y, E, G_u(2), G_v(2), G_T(2))           K = 10, 2D
+ *   MHD_J_TRACK      (rho, m(3), B(3), E, j(3))                           K = 11, 3D
+ *   BURGERS (u), EULER (rho, m_x, m_y, E), MAXWELL_TM (E_z, H_x, H_y)     2D
+ * Trackers G_{V,b} ~ dV/dx_b follow Eq. gradient_advection with tau_grad = g_tau dt. */
+typedef enum {
+    LBX_ADR_CASCADE = 1,
+    LBX_NSF_PRIM_TRACK = 2,
+    LBX_MHD_J_TRACK = 3,
+    LBX_BURGERS = 4,
+    LBX_EULER = 5,
+    LBX_MAXWELL_TM = 6
+} lbx_family;
+
+typedef enum { LBX_D2Q5 = 1, LBX_D2Q9 = 2, LBX_D3Q7 = 3, LBX_D3Q19 = 4 } lbx_lattice;
+typedef enum { LBX_ACOUSTIC = 1, LBX_DIFFUSIVE = 2 } lbx_scaling;
+
+/* Storage and arithmetic (Sec. 2.4.3 reference/equilibrium shift):
+ *   FP64         populations f in float64, float64 arithmetic;
+ *   FP32_SHIFT   f* = f - f^eq(Q0, F0) stored and computed in float32;
+ *   FP16_SCALED  f* divided by s_k stored as IEEE binary16 (round to nearest), s_k a power of two
+ *                per component fixed at init (s_k = 2^ceil(log2(4 max|f*_k|))),
+ *                float32 arithmetic.
+ * Init and the moment/norm reductions are float64 in every mode. */
+typedef enum { LBX_FP64 = 1, LBX_FP32_SHIFT = 2, LBX_FP16_SCALED = 3 } lbx_precision;
+
+/* Manufactured forcing S_MMS = d_t Q_ex + div Phi(Q_ex) - S(Q_ex) (Sec. 4), added to the
+ * conserved components at t + dt/2:
+ *   NONE          no forcing;
+ *   ADR_SEPARABLE u_ex = 1 + A sin(2 pi x) cos(2 pi y) exp(-t) for the ADR cascade with
+ *                 R = 0; mms_amp = A. */
+typedef enum { LBX_MMS_NONE = 0, LBX_MMS_ADR_SEPARABLE = 1 } lbx_mms;
+
+typedef struct {
+    int family;            /* lbx_family                                                */
+    /* Physical parameters, by family:
+     *   ADR_CASCADE  {a_x, a_y, nu, R}
+     *   NSF          {gamma, R_gas, mu, kappa}
+     *   MHD          {gamma, eta}
+     *   BURGERS      {}            EULER {gamma}            MAXWELL_TM {c}            */
+    double params[8];
+    /* Reference (background) state Q0 [K] for the shifted storage modes; F0 = Phi(Q0). */
+    double Q0[16];
+} lbx_system_desc;
+
+typedef struct {
+    int lattice;           /* lbx_lattice; must match the family's dimension           */
+    int64_t extent[3];     /* nx, ny, nz (nz = 1 in 2D); each >= 2                      */
+    int scaling;           /* lbx_scaling: dt = f dx (acoustic) or f dx^2 (diffusive)   */
+    double f;              /* time-step factor f                                       */
+    double tau_lb;         /* > 0: tau_LB of the conserved fields, used directly        */
+    double tau_R;          /* used when tau_lb <= 0: tau_LB = 1/2 + tau_R dt (Sec. 2.3.1)*/
+    double g_tau;          /* tracker steps: tau_grad = g_tau dt, tracker tau_LB = g_tau+1 */
+    int precision;         /* lbx_precision                                             */
+    int mms;               /* lbx_mms                                                   */
+    double mms_amp;        /* amplitude A of the ADR manufactured solution              */
+    int allow_subchar_violation; /* nonzero: lbx_init does not fail on a violated bound */
+} lbx_scheme_desc;
+
+typedef struct lbx_system lbx_system;
+typedef struct lbx_scheme lbx_scheme;
+typedef struct lbx_state lbx_state;
+typedef struct lbx_batch lbx_batch;
+
+/* Message of the last failed call on this thread ("" if none).  Owned by the library. */
+const char* lbx_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int lbx_version(void);
+
+/* ---- 1. declare the system (Eq. pde_target, Sec. 2.1.1 cascade) ------------------- */
+lbx_status lbx_system_declare(const lbx_system_desc* desc, lbx_system** out);
+/* K = component count (conserved + trackers), n_cons = conserved count, dim = D. */
+lbx_status lbx_system_info(const lbx_system* sys, int* K, int* n_cons, int* dim);
+/* Name of component k (static string), or NULL if k is out of range. */
+const char* lbx_component_name(const lbx_system* sys, int k);
+void lbx_system_destroy(lbx_system* sys);
+
+/* ---- 2. derive the lattice scheme and grid scaling (Sec. 2.3.1, supplement recipes) - */
+/* Copies what it needs from sys; sys may be destroyed afterwards. */
+lbx_status lbx_scheme_derive(const lbx_system* sys, const lbx_scheme_desc* desc, lbx_scheme** out);
+/* dx = 1/nx, dt from the refinement law, lam = dt/dx, tau[K] the per-component tau_LB,
+ * q the velocity count.  Any output pointer may be NULL. */
+lbx_status lbx_scheme_info(const lbx_scheme* sch, double* dx, double* dt, double* lam,
+                           double* tau, int* q);
+void lbx_scheme_destroy(lbx_scheme* sch);
+
+/* Velocities (q x 3 ints, unused components 0) and weights of a lattice in the order
+ * the library stores populations.  c and w may be NULL to query q only. */
+lbx_status lbx_lattice_velocities(int lattice, int* q, int* c, double* w);
+
+/* ---- 3. state: init / step / moments / checks ---------------------------------------- */
+/* Populations start at the (shifted) equilibrium of Q (supplement, recipes paragraph).
+ * Q: float64 [K][cells], on the host (q_on_device = 0) or device (1).
+ * stream: a cudaStream_t (NULL = the legacy default stream).
+ * f_buf_a, f_buf_b: NULL to let the library allocate the two population buffers, or
+ * two device buffers of lbx_state_buffer_bytes() bytes each, owned by the caller.
+ * Runs the sub-characteristic check and fails with LBX_ERR_SUBCHAR on a violation
+ * unless the scheme allows it.  On failure *out is NULL and nothing is leaked. */
+lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_device, void* stream,
+                    void* f_buf_a, void* f_buf_b, lbx_state** out);
+/* Bytes of one population buffer for this scheme (K*q*cells*storage size). */
+size_t lbx_state_buffer_bytes(const lbx_scheme* sch);
+
+/* Advance n >= 0 steps of Eq. lbe_update (fused pull collide-and-stream), asynchronous.
+ * Fails with LBX_ERR_NONFINITE without stepping if a previous check found a NaN/Inf. */
+lbx_status lbx_step(lbx_state* st, int64_t n);
+
+/* Q_k = sum_i f_{k,i} (Eq. moments) at the current time, float64 [K][cells] into host
+ * (out_on_device = 0, synchronous) or device memory (1, asynchronous). */
+lbx_status lbx_moments(lbx_state* st, double* Q_out, int out_on_device);
+
+/* sum over nodes of Q_k, float64, fixed reduction order (deterministic). */
+lbx_status lbx_conserved_sums(lbx_state* st, double* sums /* [K] host */);
+
+/* Relative L2 ((N^-1 sum e^2)^1/2 over the same for Q_ref) and relative Linf
+ * (max|e| / max|Q_ref|) per component against Q_ref [K][cells] (Sec. 4).  Q_ref on host
+ * (ref_on_device = 0) or device (1).  Outputs are host arrays [K]; either may be NULL. */
+lbx_status lbx_error_norms(lbx_state* st, const double* Q_ref, int ref_on_device,
+                           double* relL2, double* relLinf);
+
+/* Sets *finite to 1 if every moment is finite, else 0 and raises the state's flag. */
+lbx_status lbx_check_finite(lbx_state* st, int* finite);
+
+/* Sub-characteristic check (Sec. 2.3.2, Eq. subchar_system) in lattice form:
+ * max_speed = (dt/dx) max over nodes of a closed-form bound of the spectral radius of
+ * sum_a n_a dPhi_a/dQ over unit n (exact for ADR, Burgers, Euler, Maxwell; an upper
+ * bound for NSF and MHD, including the tracker speeds); bound_cs = c_s;
+ * bound_monotone = c_s^2 (monotone equilibria, Sec. 3 Burgers); ok = max_speed <= c_s. */
+lbx_status lbx_subchar_check(lbx_state* st, double* max_speed, double* bound_cs,
+                             double* bound_monotone, int* ok);
+
+/* Pre-collision populations f_{k,i}(x, t) at the current time, float64 [K][q][cells]
+ * host arrays, in the unshifted and unscaled representation (f = f* + f^eq(Q0) and
+ * f* = s_k h).  Population order as lbx_lattice_velocities. */
+lbx_status lbx_get_populations(lbx_state* st, double* f_out);
+lbx_status lbx_set_populations(lbx_state* st, const double* f_in);
+
+/* Step counter and time t = step * dt. */
+lbx_status lbx_state_time(const lbx_state* st, int64_t* step, double* t);
+/* Device pointer to the buffer holding the current populations (storage type). */
+void* lbx_state_populations(const lbx_state* st);
+/* Wait for all work queued on the state's stream. */
+lbx_status lbx_synchronize(lbx_state* st);
+
+/* Checkpoint: header (magic, version, shape, precision, step, scheme hash), populations
+ * and a CRC32.  lbx_load checks all of them (LBX_ERR_IO on mismatch). */
+lbx_status lbx_save(lbx_state* st, const char* path);
+lbx_status lbx_load(lbx_state* st, const char* path);
+
+void lbx_state_destroy(lbx_state* st);
+
+/* ---- peak probes used for the roofline denominators ---------------------------------- */
+/* Streams a copy of `bytes` bytes (read + write counted) and a dependent FP64 FMA loop on
+ * the given stream; returns measured GB/s and FP64 GFLOP/s (CUDA events).  Either output
+ * may be NULL to skip that probe. */
+lbx_status lbx_probe_peaks(size_t bytes, void* stream, double* copy_gbs, double* fp64_gflops,
+                           double* fp32_gflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBX_H */

@@ -1,0 +1,386 @@
+// Device kernels of the kinetic relaxation scheme (sm_103a).
+//
+// Storage: structure of arrays A[k][i][cell], cell = (z*ny + y)*nx + x, one population
+// plane of `ncell` values per (component k, velocity i).  The buffer holds
+// post-collision populations of the previous step at the node they left, so the step
+// kernel PULLS f_{k,i}(x, t) = A[k][i][x - c_i] (periodic), collides at x and writes
+// B[k][i][x]: every store is coalesced and every load is a unit-stride run shifted by
+// at most one node (Eq. lbe_update read from the arrival side).
+//
+// One thread owns one node.  A warp issues one 32-wide coalesced access per population
+// plane (128 B for float32), and all K*q loads of a node are independent, so each
+// thread keeps K*q loads in flight; that memory-level parallelism is what saturates HBM
+// at moderate occupancy.  With REG the populations stay in registers between the
+// moment pass and the write pass; without it (large K*q) they are re-read with
+// ld.global.nc, which the first pass has just pulled into L1/L2, so DRAM sees each
+// population once.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lattices.cuh"
+#include "systems.cuh"
+
+namespace lbx {
+
+template <typename T>
+struct KParams {
+  int nx, ny, nz, pad_;
+  long long ncell;             // nodes per population plane
+  T Q0[KMAX];                  // background state (shift reference)
+  T F0l[KMAX][3];              // (dt/dx)/c_s^2 * Phi(Q0), used by the unshifted mode
+  T omega[KMAX];               // 1 / tau_LB per component
+  T scale[KMAX];               // float16 storage scale s_k (1 otherwise)
+  T inv_scale[KMAX];
+  T prm[NPRM];                 // system parameters (layout per system)
+  T lc;                        // (dt/dx) / c_s^2
+  T dt;                        // source factor
+  const T* mms_tab;            // ADR forcing tables sx[nx] cx[nx] sy[ny] cy[ny]; null = off
+  T mms_c0, mms_cx, mms_cy;    // A(-1 + 8 pi^2 nu), 2 pi A a_x, 2 pi A a_y
+  const long long* step_ptr;   // step index at the start of this launch sequence
+  int step_rel;                // offset of this launch in the sequence
+};
+
+// ----------------------------------------------------------------------------- storage
+struct StoreF64 {
+  using S = double;
+  using C = double;
+  static constexpr bool SHIFT = false, SCALE = false;
+  static constexpr int ID = 1;
+};
+struct StoreF32 {
+  using S = float;
+  using C = float;
+  static constexpr bool SHIFT = true, SCALE = false;
+  static constexpr int ID = 2;
+};
+struct StoreF16 {
+  using S = __half;
+  using C = float;
+  static constexpr bool SHIFT = true, SCALE = true;
+  static constexpr int ID = 3;
+};
+
+__device__ __forceinline__ double ld_nc(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_nc(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_nc(const __half* p) { return __half2float(__ldg(p)); }
+
+// Re-read that the compiler may not merge with the first read (asm volatile).
+__device__ __forceinline__ double ld_again(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_again(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_again(const __half* p) {
+  unsigned short v;
+  asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(v) : "l"(p));
+  return __half2float(__ushort_as_half(v));
+}
+
+__device__ __forceinline__ void store_f64(double* p, double v) { *p = v; }
+__device__ __forceinline__ void store_f64(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void store_f64(__half* p, double v) { *p = __double2half(v); }
+
+__device__ __forceinline__ void st_out(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st_out(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_out(__half* p, float v) { *p = __float2half_rn(v); }
+
+// Source node of the pull along c: x - c with periodic wrap; index c + 1.
+struct PullIdx {
+  int sx[3], sy[3], sz[3];
+  __device__ __forceinline__ PullIdx(int x, int y, int z, int nx, int ny, int nz) {
+    sx[0] = x == nx - 1 ? 0 : x + 1; sx[1] = x; sx[2] = x == 0 ? nx - 1 : x - 1;
+    sy[0] = y == ny - 1 ? 0 : y + 1; sy[1] = y; sy[2] = y == 0 ? ny - 1 : y - 1;
+    sz[0] = z == nz - 1 ? 0 : z + 1; sz[1] = z; sz[2] = z == 0 ? nz - 1 : z - 1;
+  }
+  template <class Lat>
+  __device__ __forceinline__ unsigned int src(int i, int nx, int ny) const {
+    return ((unsigned int)sz[Lat::c(i, 2) + 1] * (unsigned int)ny + (unsigned int)sy[Lat::c(i, 1) + 1]) *
+               (unsigned int)nx + (unsigned int)sx[Lat::c(i, 0) + 1];
+  }
+};
+
+// ADR manufactured forcing S_MMS(x, t + dt/2) for u_ex = 1 + A sin(2pi x)cos(2pi y)e^-t:
+// e^{-t}[A(-1 + 8 pi^2 nu) s_x c_y + 2 pi A (a_x c_x c_y - a_y s_x s_y)].
+template <typename T>
+__device__ __forceinline__ T adr_mms(const KParams<T>& p, int x, int y) {
+  const long long step = *p.step_ptr + p.step_rel;
+  const T th = (T(step) + T(0.5)) * p.dt;
+  const T e = exp(-th);
+  const T* tb = p.mms_tab;
+  const T sxv = tb[x], cxv = tb[p.nx + x], syv = tb[2 * p.nx + y], cyv = tb[2 * p.nx + p.ny + y];
+  return e * (p.mms_c0 * sxv * cyv + p.mms_cx * cxv * cyv - p.mms_cy * sxv * syv);
+}
+
+// --------------------------------------------------------------------------- the step
+template <class Lat, template <typename> class SysT, class St, bool REG>
+__global__ void k_step(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
+                       const KParams<typename St::C> p) {
+  using T = typename St::C;
+  using S = typename St::S;
+  using Sys = SysT<T>;
+  constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
+  const size_t plane = (size_t)p.ncell;
+  const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
+
+  // a1 + a2: pull every population of the node and accumulate its moments (Eq. moments)
+  T X[K];
+  T fv[REG ? K : 1][REG ? Q : 1];
+#pragma unroll
+  for (int k = 0; k < K; ++k) X[k] = T(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const S* a = A + pi.src<Lat>(i, p.nx, p.ny) + (size_t)i * plane;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      T v = ld_nc(a + (size_t)k * Q * plane);
+      if (St::SCALE) v *= p.scale[k];
+      if constexpr (REG) fv[k][i] = v;
+      X[k] += v;
+    }
+  }
+
+  // a3: primitives, flux and source at the node
+  T dQ[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) dQ[k] = St::SHIFT ? X[k] : X[k] - p.Q0[k];
+  T Phi[K][D], Src[K];
+  Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
+  if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y);
+
+  // a4 + a5 + a6: equilibrium (Eq. feq), BGK with source (Eq. lbe_update), store
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const T om = p.omega[k];
+    T ph[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) ph[d] = p.lc * Phi[k][d] + (St::SHIFT ? T(0) : p.F0l[k][d]);
+    const T sdt = p.dt * Src[k];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      T cph = T(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (Lat::c(i, d) == 1) cph += ph[d];
+        if (Lat::c(i, d) == -1) cph -= ph[d];
+      }
+      const T wi = T(Lat::w(i));
+      const T feq = wi * (X[k] + cph);
+      T f;
+      if constexpr (REG) {
+        f = fv[k][i];
+      } else {
+        f = ld_again(A + pi.src<Lat>(i, p.nx, p.ny) + ((size_t)k * Q + i) * plane);
+        if (St::SCALE) f *= p.scale[k];
+      }
+      T out = fma(om, feq - f, f) + wi * sdt;
+      if (St::SCALE) out *= p.inv_scale[k];
+      st_out(B + ((size_t)k * Q + i) * plane + cell, out);
+    }
+  }
+}
+
+// --------------------------------------------------------------------------- init
+// Populations at the (shifted) equilibrium of Q (FP64): node x computes its equilibrium
+// once and writes population i where the pull of the first step reads it, x - c_i.
+// With maxbits != null it also records max |value| per component (for float16 scales).
+template <class Lat, template <typename> class SysT, class St>
+__global__ void k_init(const double* __restrict__ Qf, typename St::S* __restrict__ A,
+                       const KParams<double> p, const double* __restrict__ feq0,
+                       unsigned long long* maxbits, int write) {
+  using Sys = SysT<double>;
+  constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const size_t plane = (size_t)p.ncell;
+  const size_t cell = ((size_t)z * p.ny + y) * p.nx + x;
+  double dQ[K];
+  for (int k = 0; k < K; ++k) dQ[k] = Qf[(size_t)k * plane + cell] - p.Q0[k];
+  double Phi[K][D], Src[K];
+  Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
+  // destination of population i: the pull at node x reads x - c_i, so the node y = x
+  // stores f_i(y + c_i); here node x writes its own f_i to x - c_i.
+  int dxs[3] = {x == p.nx - 1 ? 0 : x + 1, x, x == 0 ? p.nx - 1 : x - 1};
+  int dys[3] = {y == p.ny - 1 ? 0 : y + 1, y, y == 0 ? p.ny - 1 : y - 1};
+  int dzs[3] = {z == p.nz - 1 ? 0 : z + 1, z, z == 0 ? p.nz - 1 : z - 1};
+  for (int k = 0; k < K; ++k) {
+    for (int i = 0; i < Q; ++i) {
+      double cph = 0.0;
+      for (int d = 0; d < D; ++d) cph += Lat::c(i, d) * Phi[k][d];
+      double v = Lat::w(i) * (dQ[k] + p.lc * cph);          // f^eq(Q) - f^eq(Q0)
+      if (!St::SHIFT) v += feq0[k * Q + i];
+      if (maxbits) atomicMax(&maxbits[k], (unsigned long long)__double_as_longlong(fabs(v)));
+      if (write) {
+        const size_t dst = ((size_t)dzs[Lat::c(i, 2) + 1] * p.ny + dys[Lat::c(i, 1) + 1]) * p.nx +
+                           dxs[Lat::c(i, 0) + 1];
+        typename St::S* o = A + ((size_t)k * Q + i) * plane + dst;
+        if (St::SCALE) v *= p.inv_scale[k];
+        store_f64(o, v);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ moments / gather
+// Q_k(x) = sum_i f_{k,i}(x) (+ Q0 when shifted), float64; optionally the unshifted
+// pre-collision populations f_{k,i}(x) as well.
+template <class Lat, template <typename> class SysT, class St>
+__global__ void k_gather(const typename St::S* __restrict__ A, const KParams<double> p,
+                         const double* __restrict__ feq0, double* __restrict__ Qout,
+                         double* __restrict__ fout) {
+  constexpr int K = SysT<double>::K, Q = Lat::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
+  const size_t plane = (size_t)p.ncell;
+  const size_t cell = ((size_t)z * p.ny + y) * p.nx + x;
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      double v = (double)ld_nc(A + ((size_t)k * Q + i) * plane + pi.src<Lat>(i, p.nx, p.ny));
+      if (St::SCALE) v *= p.scale[k];
+      s += v;
+      if (fout) fout[((size_t)k * Q + i) * plane + cell] = v + (St::SHIFT ? feq0[k * Q + i] : 0.0);
+    }
+    if (Qout) Qout[(size_t)k * plane + cell] = s + (St::SHIFT ? p.Q0[k] : 0.0);
+  }
+}
+
+// Store given pre-collision populations f_{k,i}(x) (float64, unshifted) into the pull
+// layout: A[k][i][y] = f_{k,i}(y + c_i), shifted and scaled as the storage requires.
+template <class Lat, template <typename> class SysT, class St>
+__global__ void k_scatter(const double* __restrict__ fin, typename St::S* __restrict__ A,
+                          const KParams<double> p, const double* __restrict__ feq0) {
+  constexpr int K = SysT<double>::K, Q = Lat::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
+  const size_t plane = (size_t)p.ncell;
+  const size_t cell = ((size_t)z * p.ny + y) * p.nx + x;
+  for (int k = 0; k < K; ++k)
+    for (int i = 0; i < Q; ++i) {
+      double v = fin[((size_t)k * Q + i) * plane + cell] - (St::SHIFT ? feq0[k * Q + i] : 0.0);
+      if (St::SCALE) v *= p.inv_scale[k];
+      typename St::S* o = A + ((size_t)k * Q + i) * plane + pi.src<Lat>(i, p.nx, p.ny);
+      store_f64(o, v);
+    }
+}
+
+// ----------------------------------------------------------------------- reductions
+// Deterministic FP64 reductions over nodes.  Block b handles the fixed node set
+// {b*blockDim + t + j*gridDim*blockDim}; partials[b][k][4] are then summed in block order
+// by k_reduce_final.  Modes:
+//   0  sums:   acc0 = sum Q_k, acc3 = count of non-finite Q_k
+//   1  norms:  acc0 = sum (Q_k - R_k)^2, acc1 = sum R_k^2, acc2 = max|Q_k - R_k|, acc3 = max|R_k|
+//   2  subchar: acc2[0] = max over nodes of the closed-form wave-speed bound
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <class Lat, template <typename> class SysT, class St>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename St::S* __restrict__ A,
+                                                        const KParams<double> p,
+                                                        const double* __restrict__ Qref,
+                                                        double* __restrict__ partials, int mode) {
+  using Sys = SysT<double>;
+  constexpr int K = Sys::K, Q = Lat::Q;
+  double a0[K], a1[K], a2[K], a3[K];
+  for (int k = 0; k < K; ++k) a0[k] = a1[k] = a2[k] = a3[k] = 0.0;
+  const size_t plane = (size_t)p.ncell;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t cell = (size_t)blockIdx.x * blockDim.x + threadIdx.x; cell < plane; cell += stride) {
+    const int x = (int)(cell % p.nx);
+    const int y = (int)((cell / p.nx) % p.ny);
+    const int z = (int)(cell / ((size_t)p.nx * p.ny));
+    const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
+    double Qv[K];
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < Q; ++i) {
+        double v = (double)ld_nc(A + ((size_t)k * Q + i) * plane + pi.src<Lat>(i, p.nx, p.ny));
+        if (St::SCALE) v *= p.scale[k];
+        s += v;
+      }
+      Qv[k] = St::SHIFT ? s : s - p.Q0[k];     // fluctuation
+    }
+    if (mode == 0) {
+      for (int k = 0; k < K; ++k) {
+        const double q = Qv[k] + p.Q0[k];
+        a0[k] += q;
+        a3[k] += isfinite(q) ? 0.0 : 1.0;
+      }
+    } else if (mode == 1) {
+      for (int k = 0; k < K; ++k) {
+        const double r = Qref[(size_t)k * plane + cell];
+        const double e = Qv[k] + p.Q0[k] - r;
+        a0[k] += e * e;
+        a1[k] += r * r;
+        a2[k] = fmax(a2[k], fabs(e));
+        a3[k] = fmax(a3[k], fabs(r));
+      }
+    } else {
+      a2[0] = fmax(a2[0], Sys::max_speed(p.prm, p.Q0, Qv));
+    }
+  }
+  __shared__ double sm[RED_THREADS / 32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < K; ++k) {
+    double r0 = warp_sum(a0[k]), r1 = warp_sum(a1[k]);
+    double r2 = warp_max(a2[k]);
+    double r3 = mode == 1 ? warp_max(a3[k]) : warp_sum(a3[k]);
+    if (lane == 0) {
+      sm[warp][0] = r0; sm[warp][1] = r1; sm[warp][2] = r2; sm[warp][3] = r3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+      for (int w = 0; w < RED_THREADS / 32; ++w) {
+        t0 += sm[w][0]; t1 += sm[w][1]; t2 = fmax(t2, sm[w][2]);
+        t3 = mode == 1 ? fmax(t3, sm[w][3]) : t3 + sm[w][3];
+      }
+      double* o = partials + ((size_t)blockIdx.x * K + k) * 4;
+      o[0] = t0; o[1] = t1; o[2] = t2; o[3] = t3;
+    }
+    __syncthreads();
+  }
+}
+
+// Sum (or max) the partials of `nblk` blocks in block order: out[k][4].
+static __global__ void k_reduce_final(const double* __restrict__ partials, int nblk, int K, int mode,
+                               double* __restrict__ out) {
+  const int t = threadIdx.x;
+  if (t >= K * 4) return;
+  const int a = t & 3;
+  const bool is_max = (a == 2) || (a == 3 && mode == 1);
+  double acc = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    const double v = partials[(size_t)b * K * 4 + t];
+    acc = is_max ? fmax(acc, v) : acc + v;
+  }
+  out[t] = acc;
+}
+
+// Advance the device step counter after a launch sequence of n steps.
+static __global__ void k_advance(long long* step, long long n) { *step += n; }
+
+}  // namespace lbx

@@ -1,0 +1,827 @@
+// Host side of the C ABI declared in include/lbx.h: handles, parameter packing,
+// dispatch over (system family, lattice, storage) and launches of the kernels in
+// kernels.cuh.  Every entry point reports failures as an lbx_status with a message in
+// lbx_last_error(); none aborts.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbx.h"
+#include "kernels.cuh"
+#include "lbx_internal.h"
+
+using namespace lbx;
+
+// ------------------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+lbx_status lbx::fail(lbx_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+extern "C" const char* lbx_last_error(void) { return g_err.c_str(); }
+extern "C" int lbx_version(void) { return 100; }
+
+// ------------------------------------------------------------------------- systems
+static int family_K(int f) {
+  switch (f) {
+    case LBX_ADR_CASCADE: return 3;
+    case LBX_NSF_PRIM_TRACK: return 10;
+    case LBX_MHD_J_TRACK: return 11;
+    case LBX_BURGERS: return 1;
+    case LBX_EULER: return 4;
+    case LBX_MAXWELL_TM: return 3;
+  }
+  return 0;
+}
+static int family_NC(int f) {
+  switch (f) {
+    case LBX_ADR_CASCADE: return 1;
+    case LBX_NSF_PRIM_TRACK: return 4;
+    case LBX_MHD_J_TRACK: return 8;
+    default: return family_K(f);
+  }
+}
+static int family_D(int f) { return f == LBX_MHD_J_TRACK ? 3 : 2; }
+
+static const char* NAMES_ADR[] = {"u", "G_x", "G_y"};
+static const char* NAMES_NSF[] = {"rho", "m_x", "m_y", "E", "G_u_x", "G_u_y", "G_v_x", "G_v_y", "G_T_x", "G_T_y"};
+static const char* NAMES_MHD[] = {"rho", "m_x", "m_y", "m_z", "B_x", "B_y", "B_z", "E", "j_x", "j_y", "j_z"};
+static const char* NAMES_BUR[] = {"u"};
+static const char* NAMES_EUL[] = {"rho", "m_x", "m_y", "E"};
+static const char* NAMES_MAX[] = {"E_z", "H_x", "H_y"};
+
+extern "C" lbx_status lbx_system_declare(const lbx_system_desc* desc, lbx_system** out) {
+  if (!desc || !out) return fail(LBX_ERR_ARG, "lbx_system_declare: null argument");
+  *out = nullptr;
+  const int K = family_K(desc->family);
+  if (K == 0) return fail(LBX_ERR_ARG, "lbx_system_declare: unknown family %d", desc->family);
+  auto* s = new lbx_system();
+  s->family = desc->family;
+  s->K = K;
+  s->NC = family_NC(desc->family);
+  s->D = family_D(desc->family);
+  memcpy(s->params, desc->params, sizeof(s->params));
+  memcpy(s->Q0, desc->Q0, sizeof(s->Q0));
+  if ((s->family == LBX_NSF_PRIM_TRACK || s->family == LBX_EULER || s->family == LBX_MHD_J_TRACK) &&
+      !(s->Q0[0] > 0.0)) {
+    delete s;
+    return fail(LBX_ERR_ARG, "lbx_system_declare: reference density Q0[0] must be > 0");
+  }
+  *out = s;
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_system_info(const lbx_system* s, int* K, int* n_cons, int* dim) {
+  if (!s) return fail(LBX_ERR_ARG, "lbx_system_info: null system");
+  if (K) *K = s->K;
+  if (n_cons) *n_cons = s->NC;
+  if (dim) *dim = s->D;
+  return LBX_OK;
+}
+
+extern "C" const char* lbx_component_name(const lbx_system* s, int k) {
+  if (!s || k < 0 || k >= s->K) return nullptr;
+  switch (s->family) {
+    case LBX_ADR_CASCADE: return NAMES_ADR[k];
+    case LBX_NSF_PRIM_TRACK: return NAMES_NSF[k];
+    case LBX_MHD_J_TRACK: return NAMES_MHD[k];
+    case LBX_BURGERS: return NAMES_BUR[k];
+    case LBX_EULER: return NAMES_EUL[k];
+    case LBX_MAXWELL_TM: return NAMES_MAX[k];
+  }
+  return nullptr;
+}
+
+extern "C" void lbx_system_destroy(lbx_system* s) { delete s; }
+
+// ------------------------------------------------------------------------- lattices
+template <class Lat>
+static void lat_table(int* q, int* c, double* w) {
+  *q = Lat::Q;
+  for (int i = 0; i < Lat::Q; ++i) {
+    if (c)
+      for (int d = 0; d < 3; ++d) c[3 * i + d] = Lat::c(i, d);
+    if (w) w[i] = Lat::w(i);
+  }
+}
+
+extern "C" lbx_status lbx_lattice_velocities(int lattice, int* q, int* c, double* w) {
+  if (!q) return fail(LBX_ERR_ARG, "lbx_lattice_velocities: null q");
+  switch (lattice) {
+    case LBX_D2Q5: lat_table<LatD2Q5>(q, c, w); return LBX_OK;
+    case LBX_D2Q9: lat_table<LatD2Q9>(q, c, w); return LBX_OK;
+    case LBX_D3Q7: lat_table<LatD3Q7>(q, c, w); return LBX_OK;
+    case LBX_D3Q19: lat_table<LatD3Q19>(q, c, w); return LBX_OK;
+  }
+  return fail(LBX_ERR_ARG, "lbx_lattice_velocities: unknown lattice %d", lattice);
+}
+
+int lbx::lattice_q(int lattice) {
+  switch (lattice) {
+    case LBX_D2Q5: return 5;
+    case LBX_D2Q9: return 9;
+    case LBX_D3Q7: return 7;
+    case LBX_D3Q19: return 19;
+  }
+  return 0;
+}
+static int lattice_D(int lattice) { return (lattice == LBX_D3Q7 || lattice == LBX_D3Q19) ? 3 : 2; }
+static double lattice_cs2(int lattice) { return lattice == LBX_D3Q7 ? 0.25 : 1.0 / 3.0; }
+static void lattice_c(int lattice, int i, int c[3]) {
+  int q, tab[19 * 3];
+  lbx_lattice_velocities(lattice, &q, tab, nullptr);
+  for (int d = 0; d < 3; ++d) c[d] = tab[3 * i + d];
+}
+static double lattice_w(int lattice, int i) {
+  int q;
+  double w[19];
+  lbx_lattice_velocities(lattice, &q, nullptr, w);
+  return w[i];
+}
+
+// ------------------------------------------------------------------------- schemes
+extern "C" lbx_status lbx_scheme_derive(const lbx_system* sys, const lbx_scheme_desc* d, lbx_scheme** out) {
+  if (!sys || !d || !out) return fail(LBX_ERR_ARG, "lbx_scheme_derive: null argument");
+  *out = nullptr;
+  const int q = lattice_q(d->lattice);
+  if (q == 0) return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown lattice %d", d->lattice);
+  if (lattice_D(d->lattice) != sys->D)
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: lattice dimension %d != system dimension %d",
+                lattice_D(d->lattice), sys->D);
+  const int64_t nx = d->extent[0], ny = d->extent[1], nz = sys->D == 3 ? d->extent[2] : 1;
+  if (nx < 2 || ny < 2 || nz < 1 || (sys->D == 3 && nz < 2))
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: extents must be >= 2");
+  if (nx > (1 << 20) || ny > 65535 || nz > 65535 || (double)nx * ny * nz >= 2147483647.0)
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: grid too large (%lld x %lld x %lld)", (long long)nx,
+                (long long)ny, (long long)nz);
+  if (d->scaling != LBX_ACOUSTIC && d->scaling != LBX_DIFFUSIVE)
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown scaling %d", d->scaling);
+  if (!(d->f > 0.0)) return fail(LBX_ERR_ARG, "lbx_scheme_derive: f must be > 0");
+  if (d->precision < LBX_FP64 || d->precision > LBX_FP16_SCALED)
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown precision %d", d->precision);
+  if (d->mms == LBX_MMS_ADR_SEPARABLE && (sys->family != LBX_ADR_CASCADE || sys->params[3] != 0.0))
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: ADR_SEPARABLE forcing needs the ADR cascade with R = 0");
+  if (d->mms != LBX_MMS_NONE && d->mms != LBX_MMS_ADR_SEPARABLE)
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown forcing %d", d->mms);
+  const bool has_trackers = sys->K > sys->NC;
+  if (has_trackers && !(d->g_tau > 0.0)) return fail(LBX_ERR_ARG, "lbx_scheme_derive: g_tau must be > 0");
+  auto* s = new lbx_scheme();
+  s->sys = *sys;
+  s->d = *d;
+  s->q = q;
+  s->nx = (int)nx;
+  s->ny = (int)ny;
+  s->nz = (int)nz;
+  s->ncell = nx * ny * nz;
+  s->dx = 1.0 / (double)nx;
+  s->dt = d->scaling == LBX_ACOUSTIC ? d->f * s->dx : d->f * s->dx * s->dx;
+  s->lam = s->dt / s->dx;
+  s->cs2 = lattice_cs2(d->lattice);
+  const double tc = d->tau_lb > 0.0 ? d->tau_lb : 0.5 + d->tau_R * s->dt;
+  if (!(tc > 0.5)) {
+    delete s;
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: conserved tau_LB = %g must exceed 1/2", tc);
+  }
+  for (int k = 0; k < sys->K; ++k) s->tau[k] = k < sys->NC ? tc : d->g_tau + 1.0;
+  *out = s;
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_scheme_info(const lbx_scheme* s, double* dx, double* dt, double* lam, double* tau, int* q) {
+  if (!s) return fail(LBX_ERR_ARG, "lbx_scheme_info: null scheme");
+  if (dx) *dx = s->dx;
+  if (dt) *dt = s->dt;
+  if (lam) *lam = s->lam;
+  if (tau)
+    for (int k = 0; k < s->sys.K; ++k) tau[k] = s->tau[k];
+  if (q) *q = s->q;
+  return LBX_OK;
+}
+
+extern "C" void lbx_scheme_destroy(lbx_scheme* s) { delete s; }
+
+size_t lbx::storage_size(int precision) {
+  return precision == LBX_FP64 ? 8 : (precision == LBX_FP32_SHIFT ? 4 : 2);
+}
+
+extern "C" size_t lbx_state_buffer_bytes(const lbx_scheme* s) {
+  if (!s) return 0;
+  return (size_t)s->sys.K * s->q * (size_t)s->ncell * storage_size(s->d.precision);
+}
+
+// Phi(Q0) in plain form (host, float64), for the unshifted storage mode and f^eq(Q0).
+static void background_flux(const lbx_scheme* s, double F0[KMAX][3]) {
+  const lbx_system& y = s->sys;
+  const double* Q = y.Q0;
+  const double* P = y.params;
+  const double itg = (y.K > y.NC) ? 1.0 / (s->d.g_tau * s->dt) : 0.0;
+  for (int k = 0; k < KMAX; ++k)
+    for (int d = 0; d < 3; ++d) F0[k][d] = 0.0;
+  switch (y.family) {
+    case LBX_ADR_CASCADE:
+      for (int d = 0; d < 2; ++d) F0[0][d] = P[d] * Q[0] - P[2] * Q[1 + d];
+      for (int b = 0; b < 2; ++b)
+        for (int c = 0; c < 2; ++c) F0[1 + b][c] = Q[1 + b] * P[c] - (b == c ? Q[0] * itg : 0.0);
+      break;
+    case LBX_NSF_PRIM_TRACK: {
+      const double g = P[0], R = P[1], mu = P[2], kap = P[3];
+      const double rho = Q[0], u[2] = {Q[1] / rho, Q[2] / rho};
+      const double p = (g - 1.0) * (Q[3] - 0.5 * (Q[1] * u[0] + Q[2] * u[1]));
+      const double T = p / (rho * R);
+      const double L[2][2] = {{Q[4], Q[5]}, {Q[6], Q[7]}};
+      const double dv = L[0][0] + L[1][1];
+      double tv[2][2];
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) tv[a][b] = mu * (L[a][b] + L[b][a] - (a == b ? 2.0 / 3.0 * dv : 0.0));
+      for (int b = 0; b < 2; ++b) {
+        F0[0][b] = Q[1 + b];
+        for (int a = 0; a < 2; ++a) F0[1 + a][b] = Q[1 + a] * u[b] + (a == b ? p : 0.0) - tv[a][b];
+        F0[3][b] = (Q[3] + p) * u[b] - (tv[b][0] * u[0] + tv[b][1] * u[1]) - kap * Q[8 + b];
+      }
+      const double V[3] = {u[0], u[1], T};
+      for (int v = 0; v < 3; ++v)
+        for (int b = 0; b < 2; ++b)
+          for (int c = 0; c < 2; ++c) F0[4 + 2 * v + b][c] = Q[4 + 2 * v + b] * u[c] - (b == c ? V[v] * itg : 0.0);
+      break;
+    }
+    case LBX_MHD_J_TRACK: {
+      const double g = P[0], eta = P[1];
+      const double rho = Q[0];
+      double u[3], B[3], j[3], ke = 0, b2 = 0, uB = 0;
+      for (int a = 0; a < 3; ++a) {
+        u[a] = Q[1 + a] / rho;
+        B[a] = Q[4 + a];
+        j[a] = Q[8 + a];
+      }
+      for (int a = 0; a < 3; ++a) {
+        ke += 0.5 * Q[1 + a] * u[a];
+        b2 += B[a] * B[a];
+        uB += u[a] * B[a];
+      }
+      const double p = (g - 1.0) * (Q[7] - ke - 0.5 * b2), pt = p + 0.5 * b2;
+      const double jxB[3] = {j[1] * B[2] - j[2] * B[1], j[2] * B[0] - j[0] * B[2], j[0] * B[1] - j[1] * B[0]};
+      for (int b = 0; b < 3; ++b) {
+        F0[0][b] = Q[1 + b];
+        F0[7][b] = (Q[7] + pt) * u[b] - B[b] * uB + eta * jxB[b];
+        for (int a = 0; a < 3; ++a) {
+          double ej = 0, eB = 0;
+          for (int c = 0; c < 3; ++c) {
+            const int e = SysMHD<double>::eps(a, b, c);
+            ej += e * j[c];
+            eB += e * B[c];
+          }
+          F0[1 + a][b] = Q[1 + a] * u[b] + (a == b ? pt : 0.0) - B[a] * B[b];
+          F0[4 + a][b] = B[a] * u[b] - u[a] * B[b] + eta * ej;
+          F0[8 + a][b] = j[a] * u[b] - eB * itg;
+        }
+      }
+      break;
+    }
+    case LBX_BURGERS:
+      F0[0][0] = F0[0][1] = 0.5 * Q[0] * Q[0];
+      break;
+    case LBX_EULER: {
+      const double g = P[0], rho = Q[0], u[2] = {Q[1] / rho, Q[2] / rho};
+      const double p = (g - 1.0) * (Q[3] - 0.5 * (Q[1] * u[0] + Q[2] * u[1]));
+      for (int b = 0; b < 2; ++b) {
+        F0[0][b] = Q[1 + b];
+        for (int a = 0; a < 2; ++a) F0[1 + a][b] = Q[1 + a] * u[b] + (a == b ? p : 0.0);
+        F0[3][b] = (Q[3] + p) * u[b];
+      }
+      break;
+    }
+    case LBX_MAXWELL_TM: {
+      const double c = P[0];
+      F0[0][0] = -c * Q[2];
+      F0[0][1] = c * Q[1];
+      F0[1][1] = c * Q[0];
+      F0[2][0] = -c * Q[0];
+      break;
+    }
+  }
+}
+
+// System parameter array in the layout systems.cuh documents (physical values).
+static void pack_prm(const lbx_scheme* s, double prm[NPRM]) {
+  for (int i = 0; i < NPRM; ++i) prm[i] = 0.0;
+  const lbx_system& y = s->sys;
+  const double* Q = y.Q0;
+  const double* P = y.params;
+  const double itg = (y.K > y.NC) ? 1.0 / (s->d.g_tau * s->dt) : 0.0;
+  switch (y.family) {
+    case LBX_ADR_CASCADE:
+      prm[0] = P[0]; prm[1] = P[1]; prm[2] = P[2]; prm[3] = P[3]; prm[4] = itg;
+      break;
+    case LBX_NSF_PRIM_TRACK: {
+      const double g = P[0], R = P[1], mu = P[2];
+      const double rho = Q[0], u0 = Q[1] / rho, u1 = Q[2] / rho;
+      const double p0 = (g - 1.0) * (Q[3] - 0.5 * (Q[1] * u0 + Q[2] * u1));
+      const double L00 = Q[4], L01 = Q[5], L10 = Q[6], L11 = Q[7], dv = 2.0 / 3.0 * (L00 + L11);
+      prm[0] = g - 1.0; prm[1] = R; prm[2] = mu; prm[3] = P[3]; prm[4] = itg;
+      prm[5] = u0; prm[6] = u1; prm[7] = Q[3] + p0; prm[8] = p0 / rho;
+      prm[9] = mu * (2 * L00 - dv); prm[10] = mu * (L01 + L10); prm[11] = mu * (2 * L11 - dv);
+      prm[12] = g;
+      break;
+    }
+    case LBX_MHD_J_TRACK: {
+      const double g = P[0], rho = Q[0];
+      double u[3], ke = 0, b2 = 0, uB = 0;
+      for (int a = 0; a < 3; ++a) u[a] = Q[1 + a] / rho;
+      for (int a = 0; a < 3; ++a) {
+        ke += 0.5 * Q[1 + a] * u[a];
+        b2 += Q[4 + a] * Q[4 + a];
+        uB += u[a] * Q[4 + a];
+      }
+      const double p0 = (g - 1.0) * (Q[7] - ke - 0.5 * b2);
+      prm[0] = g - 1.0; prm[1] = P[1]; prm[2] = itg;
+      prm[3] = u[0]; prm[4] = u[1]; prm[5] = u[2];
+      prm[6] = Q[7] + p0 + 0.5 * b2; prm[7] = uB; prm[8] = g;
+      break;
+    }
+    case LBX_BURGERS:
+      break;
+    case LBX_EULER: {
+      const double g = P[0], rho = Q[0], u0 = Q[1] / rho, u1 = Q[2] / rho;
+      const double p0 = (g - 1.0) * (Q[3] - 0.5 * (Q[1] * u0 + Q[2] * u1));
+      prm[0] = g - 1.0; prm[1] = u0; prm[2] = u1; prm[3] = Q[3] + p0; prm[4] = g;
+      break;
+    }
+    case LBX_MAXWELL_TM:
+      prm[0] = P[0];
+      break;
+  }
+}
+
+template <typename T>
+static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale) {
+  const lbx_scheme& s = st->sch;
+  memset(&p, 0, sizeof(p));
+  p.nx = s.nx;
+  p.ny = s.ny;
+  p.nz = s.nz;
+  p.ncell = s.ncell;
+  double F0[KMAX][3], prm[NPRM];
+  background_flux(&s, F0);
+  pack_prm(&s, prm);
+  const double lc = s.lam / s.cs2;
+  for (int k = 0; k < s.sys.K; ++k) {
+    p.Q0[k] = (T)s.sys.Q0[k];
+    for (int d = 0; d < 3; ++d) p.F0l[k][d] = (T)(lc * F0[k][d]);
+    p.omega[k] = (T)(1.0 / s.tau[k]);
+    p.scale[k] = (T)scale[k];
+    p.inv_scale[k] = (T)(1.0 / scale[k]);
+  }
+  for (int i = 0; i < NPRM; ++i) p.prm[i] = (T)prm[i];
+  p.lc = (T)lc;
+  p.dt = (T)s.dt;
+  p.step_ptr = st->d_step;
+  if (s.d.mms == LBX_MMS_ADR_SEPARABLE) {
+    const double A = s.d.mms_amp, nu = s.sys.params[2], tp = 2.0 * M_PI;
+    p.mms_c0 = (T)(A * (-1.0 + 2.0 * tp * tp * nu));
+    p.mms_cx = (T)(tp * A * s.sys.params[0]);
+    p.mms_cy = (T)(tp * A * s.sys.params[1]);
+    p.mms_tab = sizeof(T) == 8 ? (const T*)st->d_mms_tab64 : (const T*)st->d_mms_tab32;
+  }
+}
+
+// ------------------------------------------------------------------------ dispatch
+template <class Lat, template <typename> class SysT, class St>
+struct OpsImpl {
+  using C = typename St::C;
+  using S = typename St::S;
+  static constexpr int K = SysT<C>::K;
+  static constexpr bool REG = (size_t)K * Lat::Q * sizeof(C) <= 360;
+
+  static dim3 block(const lbx_scheme& s) {
+    int bx = s.nx >= 128 ? 128 : ((s.nx + 31) / 32) * 32;
+    return dim3(bx, 1, 1);
+  }
+  static dim3 grid(const lbx_scheme& s, dim3 b) { return dim3((s.nx + b.x - 1) / b.x, s.ny, s.nz); }
+
+  static cudaError_t step(const lbx_state* st, const void* A, void* B, int rel, cudaStream_t strm) {
+    KParams<C> p = st->pc<C>();
+    p.step_rel = rel;
+    dim3 b = block(st->sch), g = grid(st->sch, b);
+    k_step<Lat, SysT, St, REG><<<g, b, 0, strm>>>((const S*)A, (S*)B, p);
+    return cudaGetLastError();
+  }
+  static cudaError_t init(const lbx_state* st, const double* Q, void* A, unsigned long long* maxbits, int write) {
+    dim3 b = block(st->sch), g = grid(st->sch, b);
+    k_init<Lat, SysT, St><<<g, b, 0, st->stream>>>(Q, (S*)A, st->pd, st->d_feq0, maxbits, write);
+    return cudaGetLastError();
+  }
+  static cudaError_t gather(const lbx_state* st, const void* A, double* Qout, double* fout) {
+    dim3 b = block(st->sch), g = grid(st->sch, b);
+    k_gather<Lat, SysT, St><<<g, b, 0, st->stream>>>((const S*)A, st->pd, st->d_feq0, Qout, fout);
+    return cudaGetLastError();
+  }
+  static cudaError_t scatter(const lbx_state* st, const double* fin, void* A) {
+    dim3 b = block(st->sch), g = grid(st->sch, b);
+    k_scatter<Lat, SysT, St><<<g, b, 0, st->stream>>>(fin, (S*)A, st->pd, st->d_feq0);
+    return cudaGetLastError();
+  }
+  static cudaError_t reduce(const lbx_state* st, const void* A, const double* Qref, double* partials,
+                            int nblk, int mode) {
+    k_reduce<Lat, SysT, St><<<nblk, RED_THREADS, 0, st->stream>>>((const S*)A, st->pd, Qref, partials, mode);
+    return cudaGetLastError();
+  }
+  static const void* step_fn() { return (const void*)k_step<Lat, SysT, St, REG>; }
+};
+
+template <class Lat, template <typename> class SysT, class St>
+static Ops make_ops() {
+  using I = OpsImpl<Lat, SysT, St>;
+  return Ops{I::step, I::init, I::gather, I::scatter, I::reduce, I::step_fn, I::REG};
+}
+
+template <class Lat, template <typename> class SysT>
+static bool pick_store(int precision, Ops* o) {
+  switch (precision) {
+    case LBX_FP64: *o = make_ops<Lat, SysT, StoreF64>(); return true;
+    case LBX_FP32_SHIFT: *o = make_ops<Lat, SysT, StoreF32>(); return true;
+    case LBX_FP16_SCALED: *o = make_ops<Lat, SysT, StoreF16>(); return true;
+  }
+  return false;
+}
+
+bool lbx::find_ops(int family, int lattice, int precision, Ops* o) {
+  switch (family) {
+    case LBX_ADR_CASCADE:
+      if (lattice == LBX_D2Q5) return pick_store<LatD2Q5, SysADR>(precision, o);
+      if (lattice == LBX_D2Q9) return pick_store<LatD2Q9, SysADR>(precision, o);
+      return false;
+    case LBX_NSF_PRIM_TRACK:
+      if (lattice == LBX_D2Q5) return pick_store<LatD2Q5, SysNSF>(precision, o);
+      if (lattice == LBX_D2Q9) return pick_store<LatD2Q9, SysNSF>(precision, o);
+      return false;
+    case LBX_MHD_J_TRACK:
+      if (lattice == LBX_D3Q7) return pick_store<LatD3Q7, SysMHD>(precision, o);
+      if (lattice == LBX_D3Q19) return pick_store<LatD3Q19, SysMHD>(precision, o);
+      return false;
+    case LBX_BURGERS:
+      if (lattice == LBX_D2Q5) return pick_store<LatD2Q5, SysBurgers>(precision, o);
+      return false;
+    case LBX_EULER:
+      if (lattice == LBX_D2Q5) return pick_store<LatD2Q5, SysEuler>(precision, o);
+      return false;
+    case LBX_MAXWELL_TM:
+      if (lattice == LBX_D2Q5) return pick_store<LatD2Q5, SysMaxwell>(precision, o);
+      return false;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------------- states
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBX_ERR_OOM : LBX_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                                       \
+  } while (0)
+
+static void free_state(lbx_state* st) {
+  if (!st) return;
+  if (st->own_a && st->fa) cudaFree(st->fa);
+  if (st->own_b && st->fb) cudaFree(st->fb);
+  cudaFree(st->d_step);
+  cudaFree(st->d_feq0);
+  cudaFree(st->d_partials);
+  cudaFree(st->d_red_out);
+  cudaFree(st->d_mms_tab64);
+  cudaFree(st->d_mms_tab32);
+  delete st;
+}
+
+static void feq0_table(const lbx_scheme& s, double* out) {
+  double F0[KMAX][3];
+  background_flux(&s, F0);
+  const double lc = s.lam / s.cs2;
+  for (int k = 0; k < s.sys.K; ++k)
+    for (int i = 0; i < s.q; ++i) {
+      int c[3];
+      lattice_c(s.d.lattice, i, c);
+      double cph = 0.0;
+      for (int d = 0; d < 3; ++d) cph += c[d] * F0[k][d];
+      out[k * s.q + i] = lattice_w(s.d.lattice, i) * (s.sys.Q0[k] + lc * cph);
+    }
+}
+
+void lbx::refresh_params(lbx_state* st) {
+  fill_params<double>(st, st->pd, st->scale);
+  fill_params<float>(st, st->pf, st->scale);
+}
+
+lbx_status lbx::run_reduce(lbx_state* st, const double* Qref, int mode, double* host_out) {
+  const int K = st->sch.sys.K;
+  if (cudaError_t e = st->ops.reduce(st, st->cur(), Qref, st->d_partials, st->red_blocks, mode))
+    return fail(LBX_ERR_CUDA, "reduce launch: %s", cudaGetErrorString(e));
+  k_reduce_final<<<1, 64, 0, st->stream>>>(st->d_partials, st->red_blocks, K, mode, st->d_red_out);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(host_out, st->d_red_out, sizeof(double) * K * 4, cudaMemcpyDeviceToHost, st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_subchar_check(lbx_state* st, double* max_speed, double* bound_cs,
+                                        double* bound_monotone, int* ok) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_subchar_check: null state");
+  double out[KMAX * 4];
+  if (lbx_status s = run_reduce(st, nullptr, 2, out)) return s;
+  const double ms = st->sch.lam * out[2];
+  const double cs = std::sqrt(st->sch.cs2);
+  if (max_speed) *max_speed = ms;
+  if (bound_cs) *bound_cs = cs;
+  if (bound_monotone) *bound_monotone = st->sch.cs2;
+  if (ok) *ok = (ms <= cs) ? 1 : 0;
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_device, void* stream,
+                               void* f_buf_a, void* f_buf_b, lbx_state** out) {
+  if (!sch || !Q || !out) return fail(LBX_ERR_ARG, "lbx_init: null argument");
+  *out = nullptr;
+  if ((f_buf_a == nullptr) != (f_buf_b == nullptr))
+    return fail(LBX_ERR_ARG, "lbx_init: pass both population buffers or neither");
+  auto* st = new lbx_state();
+  st->sch = *sch;
+  st->stream = (cudaStream_t)stream;
+  if (!find_ops(sch->sys.family, sch->d.lattice, sch->d.precision, &st->ops)) {
+    delete st;
+    return fail(LBX_ERR_UNSUPPORTED, "lbx_init: family %d on lattice %d not compiled", sch->sys.family,
+                sch->d.lattice);
+  }
+  for (int k = 0; k < KMAX; ++k) st->scale[k] = 1.0;
+  lbx_status rc = LBX_OK;
+  double* dQ = nullptr;
+  const size_t bytes = lbx_state_buffer_bytes(sch);
+  const int K = sch->sys.K, q = sch->q;
+  auto bail = [&](lbx_status s) {
+    if (dQ && !q_on_device) cudaFree(dQ);
+    free_state(st);
+    return s;
+  };
+#define CKI(call)                                                                                    \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      return bail(fail(e_ == cudaErrorMemoryAllocation ? LBX_ERR_OOM : LBX_ERR_CUDA, "lbx_init: %s: %s", \
+                       #call, cudaGetErrorString(e_)));                                              \
+  } while (0)
+  if (f_buf_a) {
+    st->fa = f_buf_a;
+    st->fb = f_buf_b;
+  } else {
+    CKI(cudaMalloc(&st->fa, bytes));
+    st->own_a = true;
+    CKI(cudaMalloc(&st->fb, bytes));
+    st->own_b = true;
+  }
+  CKI(cudaMalloc(&st->d_step, sizeof(long long)));
+  CKI(cudaMemsetAsync(st->d_step, 0, sizeof(long long), st->stream));
+  CKI(cudaMalloc(&st->d_feq0, sizeof(double) * K * q));
+  {
+    std::vector<double> t(K * q);
+    feq0_table(*sch, t.data());
+    CKI(cudaMemcpyAsync(st->d_feq0, t.data(), sizeof(double) * K * q, cudaMemcpyHostToDevice, st->stream));
+    CKI(cudaStreamSynchronize(st->stream));
+  }
+  int dev = 0, nsm = 148;
+  CKI(cudaGetDevice(&dev));
+  CKI(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  st->red_blocks = 2 * nsm;
+  CKI(cudaMalloc(&st->d_partials, sizeof(double) * st->red_blocks * K * 4));
+  CKI(cudaMalloc(&st->d_red_out, sizeof(double) * K * 4));
+  if (sch->d.mms == LBX_MMS_ADR_SEPARABLE) {
+    const int nx = sch->nx, ny = sch->ny;
+    std::vector<double> t(2 * nx + 2 * ny);
+    std::vector<float> tf(t.size());
+    for (int i = 0; i < nx; ++i) {
+      t[i] = std::sin(2.0 * M_PI * i / nx);
+      t[nx + i] = std::cos(2.0 * M_PI * i / nx);
+    }
+    for (int j = 0; j < ny; ++j) {
+      t[2 * nx + j] = std::sin(2.0 * M_PI * j / ny);
+      t[2 * nx + ny + j] = std::cos(2.0 * M_PI * j / ny);
+    }
+    for (size_t i = 0; i < t.size(); ++i) tf[i] = (float)t[i];
+    CKI(cudaMalloc(&st->d_mms_tab64, sizeof(double) * t.size()));
+    CKI(cudaMalloc(&st->d_mms_tab32, sizeof(float) * t.size()));
+    CKI(cudaMemcpyAsync(st->d_mms_tab64, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, st->stream));
+    CKI(cudaMemcpyAsync(st->d_mms_tab32, tf.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice, st->stream));
+    CKI(cudaStreamSynchronize(st->stream));
+  }
+  refresh_params(st);
+  // fields on the device
+  const size_t qbytes = sizeof(double) * K * (size_t)sch->ncell;
+  if (q_on_device) {
+    dQ = const_cast<double*>(Q);
+  } else {
+    CKI(cudaMalloc(&dQ, qbytes));
+    CKI(cudaMemcpyAsync(dQ, Q, qbytes, cudaMemcpyHostToDevice, st->stream));
+  }
+  if (sch->d.precision == LBX_FP16_SCALED) {
+    unsigned long long* dmax = nullptr;
+    CKI(cudaMalloc(&dmax, sizeof(unsigned long long) * K));
+    cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long) * K, st->stream);
+    if (!e) e = st->ops.init(st, dQ, st->fa, dmax, 0);
+    unsigned long long hm[KMAX];
+    if (!e) e = cudaMemcpyAsync(hm, dmax, sizeof(unsigned long long) * K, cudaMemcpyDeviceToHost, st->stream);
+    if (!e) e = cudaStreamSynchronize(st->stream);
+    cudaFree(dmax);
+    CKI(e);
+    for (int k = 0; k < K; ++k) {
+      double m;
+      memcpy(&m, &hm[k], sizeof(double));
+      if (!std::isfinite(m)) return bail(fail(LBX_ERR_NONFINITE, "lbx_init: non-finite initial field"));
+      st->scale[k] = m > 0.0 ? std::ldexp(1.0, (int)std::ceil(std::log2(4.0 * m))) : 1.0;
+    }
+    refresh_params(st);
+  }
+  CKI(st->ops.init(st, dQ, st->fa, nullptr, 1));
+  CKI(cudaStreamSynchronize(st->stream));
+  if (!q_on_device) {
+    cudaFree(dQ);
+    dQ = nullptr;
+  }
+  st->cur_a = true;
+  {
+    double sums[KMAX * 4];
+    if ((rc = run_reduce(st, nullptr, 0, sums))) return bail(rc);
+    for (int k = 0; k < K; ++k)
+      if (sums[4 * k + 3] != 0.0) return bail(fail(LBX_ERR_NONFINITE, "lbx_init: non-finite initial field"));
+  }
+  if (!sch->d.allow_subchar_violation) {
+    double ms;
+    int ok;
+    if ((rc = lbx_subchar_check(st, &ms, nullptr, nullptr, &ok))) return bail(rc);
+    if (!ok)
+      return bail(fail(LBX_ERR_SUBCHAR, "lbx_init: sub-characteristic bound violated: (dt/dx) max speed %.6g > c_s %.6g",
+                       ms, std::sqrt(sch->cs2)));
+  }
+  *out = st;
+  return LBX_OK;
+#undef CKI
+}
+
+extern "C" lbx_status lbx_step(lbx_state* st, int64_t n) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_step: null state");
+  if (n < 0) return fail(LBX_ERR_ARG, "lbx_step: negative step count");
+  if (st->nonfinite) return fail(LBX_ERR_NONFINITE, "lbx_step: state holds non-finite values");
+  const bool forced = st->sch.d.mms != LBX_MMS_NONE;
+  int64_t done = 0;
+  while (done < n) {
+    const int64_t chunk = (n - done) < (int64_t(1) << 30) ? (n - done) : (int64_t(1) << 30);
+    for (int64_t r = 0; r < chunk; ++r) {
+      cudaError_t e = st->ops.step(st, st->cur(), st->nxt(), (int)r, st->stream);
+      if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_step: launch failed: %s", cudaGetErrorString(e));
+      st->cur_a = !st->cur_a;
+    }
+    if (forced) {
+      k_advance<<<1, 1, 0, st->stream>>>(st->d_step, chunk);
+      CK(cudaGetLastError());
+    } else {
+      st->step_dirty = true;
+    }
+    done += chunk;
+    st->step += chunk;
+  }
+  return LBX_OK;
+}
+
+// Keep the device step counter in line with the host one (steps taken without forcing).
+static lbx_status sync_step_counter(lbx_state* st) {
+  if (st->step_dirty) {
+    long long v = st->step;
+    CK(cudaMemcpyAsync(st->d_step, &v, sizeof(v), cudaMemcpyHostToDevice, st->stream));
+    CK(cudaStreamSynchronize(st->stream));
+    st->step_dirty = false;
+  }
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_moments(lbx_state* st, double* Q_out, int out_on_device) {
+  if (!st || !Q_out) return fail(LBX_ERR_ARG, "lbx_moments: null argument");
+  const size_t bytes = sizeof(double) * st->sch.sys.K * (size_t)st->sch.ncell;
+  if (out_on_device) {
+    if (cudaError_t e = st->ops.gather(st, st->cur(), Q_out, nullptr))
+      return fail(LBX_ERR_CUDA, "lbx_moments: %s", cudaGetErrorString(e));
+    return LBX_OK;
+  }
+  double* d = nullptr;
+  CK(cudaMalloc(&d, bytes));
+  cudaError_t e = st->ops.gather(st, st->cur(), d, nullptr);
+  if (!e) e = cudaMemcpyAsync(Q_out, d, bytes, cudaMemcpyDeviceToHost, st->stream);
+  if (!e) e = cudaStreamSynchronize(st->stream);
+  cudaFree(d);
+  CK(e);
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_conserved_sums(lbx_state* st, double* sums) {
+  if (!st || !sums) return fail(LBX_ERR_ARG, "lbx_conserved_sums: null argument");
+  double out[KMAX * 4];
+  if (lbx_status s = run_reduce(st, nullptr, 0, out)) return s;
+  for (int k = 0; k < st->sch.sys.K; ++k) sums[k] = out[4 * k];
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_check_finite(lbx_state* st, int* finite) {
+  if (!st || !finite) return fail(LBX_ERR_ARG, "lbx_check_finite: null argument");
+  double out[KMAX * 4];
+  if (lbx_status s = run_reduce(st, nullptr, 0, out)) return s;
+  int ok = 1;
+  for (int k = 0; k < st->sch.sys.K; ++k)
+    if (out[4 * k + 3] != 0.0) ok = 0;
+  *finite = ok;
+  if (!ok) st->nonfinite = true;
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_error_norms(lbx_state* st, const double* Q_ref, int ref_on_device, double* relL2,
+                                      double* relLinf) {
+  if (!st || !Q_ref) return fail(LBX_ERR_ARG, "lbx_error_norms: null argument");
+  const int K = st->sch.sys.K;
+  const size_t bytes = sizeof(double) * K * (size_t)st->sch.ncell;
+  const double* d = Q_ref;
+  double* tmp = nullptr;
+  if (!ref_on_device) {
+    CK(cudaMalloc(&tmp, bytes));
+    if (cudaError_t e = cudaMemcpyAsync(tmp, Q_ref, bytes, cudaMemcpyHostToDevice, st->stream)) {
+      cudaFree(tmp);
+      return fail(LBX_ERR_CUDA, "lbx_error_norms: %s", cudaGetErrorString(e));
+    }
+    d = tmp;
+  }
+  double out[KMAX * 4];
+  lbx_status s = run_reduce(st, d, 1, out);
+  if (tmp) cudaFree(tmp);
+  if (s) return s;
+  for (int k = 0; k < K; ++k) {
+    if (relL2) relL2[k] = out[4 * k + 1] > 0 ? std::sqrt(out[4 * k] / out[4 * k + 1]) : std::sqrt(out[4 * k]);
+    if (relLinf) relLinf[k] = out[4 * k + 3] > 0 ? out[4 * k + 2] / out[4 * k + 3] : out[4 * k + 2];
+  }
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_get_populations(lbx_state* st, double* f_out) {
+  if (!st || !f_out) return fail(LBX_ERR_ARG, "lbx_get_populations: null argument");
+  const size_t bytes = sizeof(double) * st->sch.sys.K * st->sch.q * (size_t)st->sch.ncell;
+  double* d = nullptr;
+  CK(cudaMalloc(&d, bytes));
+  cudaError_t e = st->ops.gather(st, st->cur(), nullptr, d);
+  if (!e) e = cudaMemcpyAsync(f_out, d, bytes, cudaMemcpyDeviceToHost, st->stream);
+  if (!e) e = cudaStreamSynchronize(st->stream);
+  cudaFree(d);
+  CK(e);
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_set_populations(lbx_state* st, const double* f_in) {
+  if (!st || !f_in) return fail(LBX_ERR_ARG, "lbx_set_populations: null argument");
+  const size_t bytes = sizeof(double) * st->sch.sys.K * st->sch.q * (size_t)st->sch.ncell;
+  double* d = nullptr;
+  CK(cudaMalloc(&d, bytes));
+  cudaError_t e = cudaMemcpyAsync(d, f_in, bytes, cudaMemcpyHostToDevice, st->stream);
+  if (!e) e = st->ops.scatter(st, d, st->cur());
+  if (!e) e = cudaStreamSynchronize(st->stream);
+  cudaFree(d);
+  CK(e);
+  st->nonfinite = false;
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_state_time(const lbx_state* st, int64_t* step, double* t) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_state_time: null state");
+  if (step) *step = st->step;
+  if (t) *t = (double)st->step * st->sch.dt;
+  return LBX_OK;
+}
+
+extern "C" void* lbx_state_populations(const lbx_state* st) { return st ? st->cur() : nullptr; }
+
+extern "C" lbx_status lbx_synchronize(lbx_state* st) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_synchronize: null state");
+  CK(cudaStreamSynchronize(st->stream));
+  if (lbx_status s = sync_step_counter(st)) return s;
+  return LBX_OK;
+}
+
+extern "C" void lbx_state_destroy(lbx_state* st) {
+  if (st) cudaStreamSynchronize(st->stream);
+  free_state(st);
+}
+
+lbx_status lbx::ensure_step_counter(lbx_state* st) { return sync_step_counter(st); }

@@ -1,0 +1,82 @@
+// Internal host-side structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbx.h"
+#include "kernels.cuh"
+
+struct lbx_system {
+  int family;
+  int K, NC, D;
+  double params[8];
+  double Q0[16];
+};
+
+struct lbx_scheme {
+  lbx_system sys;
+  lbx_scheme_desc d;
+  int q;
+  int nx, ny, nz;
+  long long ncell;
+  double dx, dt, lam, cs2;
+  double tau[lbx::KMAX];
+};
+
+namespace lbx {
+
+struct Ops {
+  cudaError_t (*step)(const lbx_state*, const void* A, void* B, int rel, cudaStream_t);
+  cudaError_t (*init)(const lbx_state*, const double* Q, void* A, unsigned long long* maxbits, int write);
+  cudaError_t (*gather)(const lbx_state*, const void* A, double* Qout, double* fout);
+  cudaError_t (*scatter)(const lbx_state*, const double* fin, void* A);
+  cudaError_t (*reduce)(const lbx_state*, const void* A, const double* Qref, double* partials, int nblk, int mode);
+  const void* (*step_fn)();
+  bool reg;
+};
+
+lbx_status fail(lbx_status s, const char* fmt, ...);
+bool find_ops(int family, int lattice, int precision, Ops* o);
+int lattice_q(int lattice);
+size_t storage_size(int precision);
+
+}  // namespace lbx
+
+struct lbx_state {
+  lbx_scheme sch;
+  cudaStream_t stream = nullptr;
+  lbx::Ops ops{};
+  void* fa = nullptr;
+  void* fb = nullptr;
+  bool own_a = false, own_b = false;
+  bool cur_a = true;            // current populations live in fa
+  long long step = 0;
+  bool step_dirty = false;      // host counter ahead of the device counter
+  bool nonfinite = false;
+  long long* d_step = nullptr;
+  double* d_feq0 = nullptr;     // f^eq(Q0) [K][q]
+  double* d_partials = nullptr; // reduction scratch [red_blocks][K][4]
+  double* d_red_out = nullptr;  // [K][4]
+  int red_blocks = 0;
+  double* d_mms_tab64 = nullptr;
+  float* d_mms_tab32 = nullptr;
+  double scale[lbx::KMAX];
+  lbx::KParams<double> pd;
+  lbx::KParams<float> pf;
+
+  void* cur() const { return cur_a ? fa : fb; }
+  void* nxt() const { return cur_a ? fb : fa; }
+  template <typename T>
+  const lbx::KParams<T>& pc() const;
+};
+
+template <>
+inline const lbx::KParams<double>& lbx_state::pc<double>() const { return pd; }
+template <>
+inline const lbx::KParams<float>& lbx_state::pc<float>() const { return pf; }
+
+namespace lbx {
+void refresh_params(lbx_state* st);
+lbx_status run_reduce(lbx_state* st, const double* Qref, int mode, double* host_out);
+lbx_status ensure_step_counter(lbx_state* st);
+}  // namespace lbx

@@ -1,0 +1,259 @@
+// Per-system flux and source of dQ/dt + div Phi(Q) = S(Q) (Eq. pde_target), evaluated
+// at one node in "delta form": given the background Q0 and the fluctuation dQ = Q - Q0,
+// eval() returns dPhi = Phi(Q0 + dQ) - Phi(Q0) (physical units, [K][D]) and the full
+// state source S(Q0 + dQ) ([K]).  Every difference is formed algebraically from the
+// fluctuations (e.g. u - u0 = (dm - u0 drho)/rho), never as a difference of two large
+// numbers, which is what lets the shifted float32/float16 kernels keep the fluctuation's
+// precision (Sec. 2.4.3).  Gradient trackers follow Eq. gradient_advection:
+// Phi_{G_{V,b}, c} = G_{V,b} u_c - delta_bc V / tau_grad, S_G = -G / tau_grad.
+//
+// max_speed() is a closed-form bound of the spectral radius of sum_a n_a dPhi_a/dQ over
+// unit n (Sec. 2.3.2, Eq. subchar_system), used by the sub-characteristic check.
+//
+// Parameters arrive as a T array `p` whose layout each system documents; the host fills
+// it (physical values plus derived background quantities).
+#pragma once
+
+namespace lbx {
+
+constexpr int KMAX = 11;
+constexpr int NPRM = 24;
+
+// ------------------------------------------------------------------------------ ADR
+// Sec. 3 (ADR) with the supplement's expanded form: Q = (u, G_x, G_y),
+// Phi_u = u a - nu G, Phi_{G_b,c} = G_b a_c - delta_bc u/tau_g, S_u = R u (1-u), S_G = -G/tau_g.
+// p: 0 a_x, 1 a_y, 2 nu, 3 R, 4 1/tau_grad
+template <typename T>
+struct SysADR {
+  static constexpr int K = 3, NC = 1, D = 2, FAMILY = 1;
+  __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
+    const T a[2] = {p[0], p[1]};
+    const T nu = p[2], R = p[3], itg = p[4];
+    const T du = dQ[0];
+    for (int d = 0; d < 2; ++d) dPhi[0][d] = a[d] * du - nu * dQ[1 + d];
+    for (int b = 0; b < 2; ++b)
+      for (int c = 0; c < 2; ++c) dPhi[1 + b][c] = a[c] * dQ[1 + b] - (b == c ? du * itg : T(0));
+    const T u = Q0[0] + du;
+    S[0] = R * u * (T(1) - u);
+    S[1] = -(Q0[1] + dQ[1]) * itg;
+    S[2] = -(Q0[2] + dQ[2]) * itg;
+  }
+  __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) {
+    return sqrt(p[0] * p[0] + p[1] * p[1]) + sqrt(p[2] * p[4]);
+  }
+};
+
+// ------------------------------------------------------------------------------ NSF
+// Compressible NSF (Sec. 3) with trackers of the primitives u, v, T:
+// Q = (rho, m_x, m_y, E, G_u(2), G_v(2), G_T(2)), u = m/rho, p = (gamma-1)(E - m.u/2),
+// T = p/(rho R), tau_v = mu (L + L^T - 2/3 tr L I) with L_ab = G_{u_a,b},
+// Phi_m = m u + p I - tau_v, Phi_E = (E+p) u - tau_v u - kappa G_T.
+// p: 0 gamma-1, 1 R, 2 mu, 3 kappa, 4 1/tau_grad, 5 u0x, 6 u0y, 7 E0+p0, 8 R T0,
+//    9 tau_v0_xx, 10 tau_v0_xy, 11 tau_v0_yy, 12 gamma
+template <typename T>
+struct SysNSF {
+  static constexpr int K = 10, NC = 4, D = 2, FAMILY = 2;
+  __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
+    const T gm1 = p[0], Rg = p[1], mu = p[2], kap = p[3], itg = p[4];
+    const T u0[2] = {p[5], p[6]};
+    const T EP0 = p[7], RT0 = p[8];
+    const T drho = dQ[0], rho = Q0[0] + drho, irho = T(1) / rho;
+    const T dm[2] = {dQ[1], dQ[2]};
+    const T m0[2] = {Q0[1], Q0[2]};
+    T du[2], u[2];
+    for (int a = 0; a < 2; ++a) {
+      du[a] = (dm[a] - u0[a] * drho) * irho;
+      u[a] = u0[a] + du[a];
+    }
+    const T dke = T(0.5) * (dm[0] * u[0] + dm[1] * u[1] + m0[0] * du[0] + m0[1] * du[1]);
+    const T dE = dQ[3];
+    const T dp = gm1 * (dE - dke);
+    const T dT = (dp - RT0 * drho) * irho / Rg;
+    // viscous stress of the tracker fluctuation (linear in G)
+    const T L00 = dQ[4], L01 = dQ[5], L10 = dQ[6], L11 = dQ[7];
+    const T dv = T(2.0 / 3.0) * (L00 + L11);
+    const T dt00 = mu * (T(2) * L00 - dv), dt11 = mu * (T(2) * L11 - dv), dt01 = mu * (L01 + L10);
+    const T t0[2][2] = {{p[9], p[10]}, {p[10], p[11]}};
+    const T dtv[2][2] = {{dt00, dt01}, {dt01, dt11}};
+    for (int b = 0; b < 2; ++b) dPhi[0][b] = dm[b];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        dPhi[1 + a][b] = dm[a] * u[b] + m0[a] * du[b] + (a == b ? dp : T(0)) - dtv[a][b];
+    for (int b = 0; b < 2; ++b) {
+      // (tau_v u) - (tau_v0 u0) = tau_v(dG) u + tau_v0 du
+      const T tu = dtv[b][0] * u[0] + dtv[b][1] * u[1] + t0[b][0] * du[0] + t0[b][1] * du[1];
+      dPhi[3][b] = (dE + dp) * u[b] + EP0 * du[b] - tu - kap * dQ[8 + b];
+    }
+    const T dV[3] = {du[0], du[1], dT};
+    for (int v = 0; v < 3; ++v)
+      for (int b = 0; b < 2; ++b) {
+        const int k = 4 + 2 * v + b;
+        for (int c = 0; c < 2; ++c)
+          dPhi[k][c] = dQ[k] * u[c] + Q0[k] * du[c] - (b == c ? dV[v] * itg : T(0));
+      }
+    for (int k = 0; k < 4; ++k) S[k] = T(0);
+    for (int k = 4; k < 10; ++k) S[k] = -(Q0[k] + dQ[k]) * itg;
+  }
+  // |u| + sqrt(c^2 + (4/3) mu/(rho tau_g) + (gamma-1) kappa/(rho R tau_g)): acoustic speed
+  // combined with the relaxation speeds of the viscous and thermal tracker couplings.
+  __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) {
+    const T rho = Q0[0] + dQ[0];
+    const T ux = (Q0[1] + dQ[1]) / rho, uy = (Q0[2] + dQ[2]) / rho;
+    const T pr = p[0] * ((Q0[3] + dQ[3]) - T(0.5) * rho * (ux * ux + uy * uy));
+    const T c2 = p[12] * pr / rho;
+    const T s2 = c2 + (T(4.0 / 3.0) * p[2] + p[0] * p[3] / p[1]) * p[4] / rho;
+    return sqrt(ux * ux + uy * uy) + sqrt(s2);
+  }
+};
+
+// ------------------------------------------------------------------------------ MHD
+// 3D resistive MHD (Sec. 3) with a current tracker j = curl B:
+// Q = (rho, m(3), B(3), E, j(3)), p = (gamma-1)(E - m.u/2 - |B|^2/2), p_t = p + |B|^2/2,
+// Phi_m = m u + p_t I - B B, Phi_B[a][b] = B_a u_b - u_a B_b + eta eps_abc j_c,
+// Phi_E = (E + p_t) u - B (u.B) + eta (j x B), Phi_j[a][b] = j_a u_b - eps_abc B_c/tau_g,
+// S_j = -j/tau_g.
+// p: 0 gamma-1, 1 eta, 2 1/tau_grad, 3..5 u0, 6 E0 + p_t0, 7 u0.B0, 8 gamma
+template <typename T>
+struct SysMHD {
+  static constexpr int K = 11, NC = 8, D = 3, FAMILY = 3;
+  __host__ __device__ static constexpr int eps(int a, int b, int c) {
+    return (a - b) * (b - c) * (c - a) / 2;
+  }
+  __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
+    const T gm1 = p[0], eta = p[1], itg = p[2];
+    const T u0[3] = {p[3], p[4], p[5]};
+    const T EP0 = p[6], uB0 = p[7];
+    const T drho = dQ[0], rho = Q0[0] + drho, irho = T(1) / rho;
+    T dm[3], m0[3], du[3], u[3], dB[3], B0[3], B[3], dj[3], j0[3], j[3];
+    for (int a = 0; a < 3; ++a) {
+      dm[a] = dQ[1 + a];
+      m0[a] = Q0[1 + a];
+      du[a] = (dm[a] - u0[a] * drho) * irho;
+      u[a] = u0[a] + du[a];
+      dB[a] = dQ[4 + a];
+      B0[a] = Q0[4 + a];
+      B[a] = B0[a] + dB[a];
+      dj[a] = dQ[8 + a];
+      j0[a] = Q0[8 + a];
+      j[a] = j0[a] + dj[a];
+    }
+    const T dE = dQ[7];
+    T dke = 0, dme = 0, duB = 0;
+    for (int a = 0; a < 3; ++a) {
+      dke += dm[a] * u[a] + m0[a] * du[a];
+      dme += dB[a] * (B[a] + B0[a]);
+      duB += du[a] * B[a] + u0[a] * dB[a];
+    }
+    dke *= T(0.5);
+    dme *= T(0.5);
+    const T dp = gm1 * (dE - dke - dme);
+    const T dpt = dp + dme;
+    const T uB = uB0 + duB;
+    for (int b = 0; b < 3; ++b) dPhi[0][b] = dm[b];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        dPhi[1 + a][b] = dm[a] * u[b] + m0[a] * du[b] + (a == b ? dpt : T(0)) - (dB[a] * B[b] + B0[a] * dB[b]);
+        T ej = 0, eB = 0;
+        for (int c = 0; c < 3; ++c) {
+          const int e = eps(a, b, c);
+          if (e != 0) {
+            ej += T(e) * dj[c];
+            eB += T(e) * dB[c];
+          }
+        }
+        dPhi[4 + a][b] = (dB[a] * u[b] + B0[a] * du[b]) - (du[a] * B[b] + u0[a] * dB[b]) + eta * ej;
+        dPhi[8 + a][b] = dj[a] * u[b] + j0[a] * du[b] - eB * itg;
+      }
+    // (j x B) - (j0 x B0) = dj x B + j0 x dB
+    const T jxB[3] = {dj[1] * B[2] - dj[2] * B[1] + j0[1] * dB[2] - j0[2] * dB[1],
+                      dj[2] * B[0] - dj[0] * B[2] + j0[2] * dB[0] - j0[0] * dB[2],
+                      dj[0] * B[1] - dj[1] * B[0] + j0[0] * dB[1] - j0[1] * dB[0]};
+    for (int b = 0; b < 3; ++b)
+      dPhi[7][b] = (dE + dpt) * u[b] + EP0 * du[b] - (dB[b] * uB + B0[b] * duB) + eta * jxB[b];
+    for (int k = 0; k < 8; ++k) S[k] = T(0);
+    for (int a = 0; a < 3; ++a) S[8 + a] = -j[a] * itg;
+  }
+  // |u| + sqrt(c^2 + |B|^2/rho + eta/tau_g): fast magnetosonic bound plus the
+  // relaxation speed of the resistive current coupling.
+  __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) {
+    const T rho = Q0[0] + dQ[0];
+    T u2 = 0, b2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      const T ua = (Q0[1 + a] + dQ[1 + a]) / rho, Ba = Q0[4 + a] + dQ[4 + a];
+      u2 += ua * ua;
+      b2 += Ba * Ba;
+    }
+    const T pr = p[0] * ((Q0[7] + dQ[7]) - T(0.5) * rho * u2 - T(0.5) * b2);
+    return sqrt(u2) + sqrt(p[8] * pr / rho + b2 / rho + p[1] * p[2]);
+  }
+};
+
+// -------------------------------------------------------------------------- Burgers
+// Sec. 3 (inviscid Burgers): Phi = (u^2/2, u^2/2).  No parameters.
+template <typename T>
+struct SysBurgers {
+  static constexpr int K = 1, NC = 1, D = 2, FAMILY = 4;
+  __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
+    const T h = T(0.5) * dQ[0] * (T(2) * Q0[0] + dQ[0]);
+    dPhi[0][0] = h;
+    dPhi[0][1] = h;
+    S[0] = T(0);
+  }
+  __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) {
+    return T(1.4142135623730951) * fabs(Q0[0] + dQ[0]);
+  }
+};
+
+// ---------------------------------------------------------------------------- Euler
+// Sec. 3 (compressible Euler).  p: 0 gamma-1, 1 u0x, 2 u0y, 3 E0+p0, 4 gamma
+template <typename T>
+struct SysEuler {
+  static constexpr int K = 4, NC = 4, D = 2, FAMILY = 5;
+  __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
+    const T gm1 = p[0];
+    const T u0[2] = {p[1], p[2]};
+    const T drho = dQ[0], irho = T(1) / (Q0[0] + drho);
+    const T dm[2] = {dQ[1], dQ[2]}, m0[2] = {Q0[1], Q0[2]};
+    T du[2], u[2];
+    for (int a = 0; a < 2; ++a) {
+      du[a] = (dm[a] - u0[a] * drho) * irho;
+      u[a] = u0[a] + du[a];
+    }
+    const T dke = T(0.5) * (dm[0] * u[0] + dm[1] * u[1] + m0[0] * du[0] + m0[1] * du[1]);
+    const T dE = dQ[3], dp = gm1 * (dE - dke);
+    for (int b = 0; b < 2; ++b) {
+      dPhi[0][b] = dm[b];
+      dPhi[1][b] = dm[0] * u[b] + m0[0] * du[b] + (b == 0 ? dp : T(0));
+      dPhi[2][b] = dm[1] * u[b] + m0[1] * du[b] + (b == 1 ? dp : T(0));
+      dPhi[3][b] = (dE + dp) * u[b] + p[3] * du[b];
+    }
+    for (int k = 0; k < 4; ++k) S[k] = T(0);
+  }
+  __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) {
+    const T rho = Q0[0] + dQ[0];
+    const T ux = (Q0[1] + dQ[1]) / rho, uy = (Q0[2] + dQ[2]) / rho;
+    const T pr = p[0] * ((Q0[3] + dQ[3]) - T(0.5) * rho * (ux * ux + uy * uy));
+    return sqrt(ux * ux + uy * uy) + sqrt(p[4] * pr / rho);
+  }
+};
+
+// ------------------------------------------------------------------------ Maxwell TM
+// Sec. 3 (Maxwell TM): Q = (E_z, H_x, H_y), Phi = c((-H_y, H_x), (0, E_z), (-E_z, 0)).
+// p: 0 c
+template <typename T>
+struct SysMaxwell {
+  static constexpr int K = 3, NC = 3, D = 2, FAMILY = 6;
+  __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
+    const T c = p[0];
+    dPhi[0][0] = -c * dQ[2];
+    dPhi[0][1] = c * dQ[1];
+    dPhi[1][0] = T(0);
+    dPhi[1][1] = c * dQ[0];
+    dPhi[2][0] = -c * dQ[0];
+    dPhi[2][1] = T(0);
+    S[0] = S[1] = S[2] = T(0);
+  }
+  __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) { return fabs(p[0]); }
+};
+
+}  // namespace lbx

@@ -1,0 +1,291 @@
+"""ctypes binding of liblbx.so (include/lbx.h).  Argument marshalling only: every step
+of the kinetic relaxation scheme runs in the library's CUDA kernels.  Importing this
+module fails if the library has not been built; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbx.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python {_HERE}/build.py`")
+_lib = C.CDLL(LIB_PATH)
+
+# ------------------------------------------------------------------------- constants
+ADR_CASCADE, NSF_PRIM_TRACK, MHD_J_TRACK, BURGERS, EULER, MAXWELL_TM = 1, 2, 3, 4, 5, 6
+D2Q5, D2Q9, D3Q7, D3Q19 = 1, 2, 3, 4
+ACOUSTIC, DIFFUSIVE = 1, 2
+FP64, FP32_SHIFT, FP16_SCALED = 1, 2, 3
+MMS_NONE, MMS_ADR_SEPARABLE = 0, 1
+
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_SUBCHAR", 5: "ERR_NONFINITE",
+          6: "ERR_TIMEOUT", 7: "ERR_STATE", 8: "ERR_IO", 9: "ERR_UNSUPPORTED"}
+
+
+class LbxError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [("family", C.c_int), ("params", C.c_double * 8), ("Q0", C.c_double * 16)]
+
+
+class SchemeDesc(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("extent", C.c_int64 * 3), ("scaling", C.c_int),
+                ("f", C.c_double), ("tau_lb", C.c_double), ("tau_R", C.c_double),
+                ("g_tau", C.c_double), ("precision", C.c_int), ("mms", C.c_int),
+                ("mms_amp", C.c_double), ("allow_subchar_violation", C.c_int)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+def _sig(name, res, args):
+    fn = getattr(_lib, name)
+    fn.restype = res
+    fn.argtypes = args
+    return fn
+
+
+_sig("lbx_last_error", C.c_char_p, [])
+_sig("lbx_version", C.c_int, [])
+_sig("lbx_system_declare", C.c_int, [C.POINTER(SystemDesc), C.POINTER(_P)])
+_sig("lbx_system_info", C.c_int, [_P, _I, _I, _I])
+_sig("lbx_component_name", C.c_char_p, [_P, C.c_int])
+_sig("lbx_system_destroy", None, [_P])
+_sig("lbx_scheme_derive", C.c_int, [_P, C.POINTER(SchemeDesc), C.POINTER(_P)])
+_sig("lbx_scheme_info", C.c_int, [_P, _D, _D, _D, _D, _I])
+_sig("lbx_scheme_destroy", None, [_P])
+_sig("lbx_lattice_velocities", C.c_int, [C.c_int, _I, _I, _D])
+_sig("lbx_init", C.c_int, [_P, _P, C.c_int, _P, _P, _P, C.POINTER(_P)])
+_sig("lbx_state_buffer_bytes", C.c_size_t, [_P])
+_sig("lbx_step", C.c_int, [_P, C.c_int64])
+_sig("lbx_moments", C.c_int, [_P, _P, C.c_int])
+_sig("lbx_conserved_sums", C.c_int, [_P, _D])
+_sig("lbx_error_norms", C.c_int, [_P, _P, C.c_int, _D, _D])
+_sig("lbx_check_finite", C.c_int, [_P, _I])
+_sig("lbx_subchar_check", C.c_int, [_P, _D, _D, _D, _I])
+_sig("lbx_get_populations", C.c_int, [_P, _P])
+_sig("lbx_set_populations", C.c_int, [_P, _P])
+_sig("lbx_state_time", C.c_int, [_P, C.POINTER(C.c_int64), _D])
+_sig("lbx_state_populations", _P, [_P])
+_sig("lbx_synchronize", C.c_int, [_P])
+_sig("lbx_save", C.c_int, [_P, C.c_char_p])
+_sig("lbx_load", C.c_int, [_P, C.c_char_p])
+_sig("lbx_state_destroy", None, [_P])
+_sig("lbx_probe_peaks", C.c_int, [C.c_size_t, _P, _D, _D, _D])
+
+
+def lib():
+    """The loaded ctypes library (for callers that need a raw entry point)."""
+    return _lib
+
+
+def check(rc):
+    if rc != 0:
+        raise LbxError(rc, _lib.lbx_last_error().decode())
+
+
+def _dbl(n):
+    return (C.c_double * n)()
+
+
+def _host_f64(a):
+    """Contiguous float64 numpy view of a CPU tensor or array (kept alive by caller)."""
+    if isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def lattice_velocities(lattice):
+    """(c [q, 3] int, w [q] float64) in the library's population order."""
+    q = C.c_int()
+    check(_lib.lbx_lattice_velocities(lattice, C.byref(q), None, None))
+    c = (C.c_int * (3 * q.value))()
+    w = _dbl(q.value)
+    check(_lib.lbx_lattice_velocities(lattice, C.byref(q), c, w))
+    return np.array(c[:], dtype=np.int64).reshape(q.value, 3), np.array(w[:])
+
+
+def probe_peaks(nbytes=4 << 30, stream=None, copy=True, fp64=True, fp32=True):
+    g, d, s = C.c_double(), C.c_double(), C.c_double()
+    check(_lib.lbx_probe_peaks(nbytes, _stream_handle(stream), C.byref(g) if copy else None,
+                               C.byref(d) if fp64 else None, C.byref(s) if fp32 else None))
+    return {"copy_gbs": g.value if copy else None, "fp64_gflops": d.value if fp64 else None,
+            "fp32_gflops": s.value if fp32 else None}
+
+
+class System:
+    """lbx_system_declare: a system family with physical parameters and background Q0."""
+
+    def __init__(self, family, params=(), Q0=()):
+        d = SystemDesc()
+        d.family = family
+        for i, v in enumerate(params):
+            d.params[i] = float(v)
+        for i, v in enumerate(Q0):
+            d.Q0[i] = float(v)
+        h = _P()
+        check(_lib.lbx_system_declare(C.byref(d), C.byref(h)))
+        self._h = h
+        K, nc, dim = C.c_int(), C.c_int(), C.c_int()
+        check(_lib.lbx_system_info(h, C.byref(K), C.byref(nc), C.byref(dim)))
+        self.K, self.n_cons, self.dim = K.value, nc.value, dim.value
+        self.names = [_lib.lbx_component_name(h, k).decode() for k in range(self.K)]
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.lbx_system_destroy(self._h)
+            self._h = None
+
+
+class Scheme:
+    """lbx_scheme_derive: lattice, extents, refinement law and relaxation slots."""
+
+    def __init__(self, system: System, lattice, extent, scaling, f, tau_lb=0.0, tau_R=0.0,
+                 g_tau=0.0, precision=FP64, mms=MMS_NONE, mms_amp=0.0,
+                 allow_subchar_violation=False):
+        d = SchemeDesc()
+        d.lattice = lattice
+        ext = list(extent) + [1] * (3 - len(extent))
+        for i in range(3):
+            d.extent[i] = int(ext[i])
+        d.scaling, d.f, d.tau_lb, d.tau_R, d.g_tau = scaling, float(f), float(tau_lb), float(tau_R), float(g_tau)
+        d.precision, d.mms, d.mms_amp = precision, mms, float(mms_amp)
+        d.allow_subchar_violation = int(bool(allow_subchar_violation))
+        h = _P()
+        check(_lib.lbx_scheme_derive(system._h, C.byref(d), C.byref(h)))
+        self._h = h
+        self.system = system
+        self.lattice = lattice
+        self.precision = precision
+        self.extent = tuple(int(e) for e in extent)
+        dx, dt, lam = C.c_double(), C.c_double(), C.c_double()
+        tau = _dbl(system.K)
+        q = C.c_int()
+        check(_lib.lbx_scheme_info(h, C.byref(dx), C.byref(dt), C.byref(lam), tau, C.byref(q)))
+        self.dx, self.dt, self.lam, self.q = dx.value, dt.value, lam.value, q.value
+        self.tau = list(tau[:])
+        self.grid = tuple(reversed(self.extent))          # (nz,) ny, nx
+        self.buffer_bytes = _lib.lbx_state_buffer_bytes(h)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.lbx_scheme_destroy(self._h)
+            self._h = None
+
+
+class State:
+    """lbx_init ... lbx_state_destroy.  Q: float64 [K, *grid] (CPU or CUDA tensor, or numpy)."""
+
+    def __init__(self, scheme: Scheme, Q, stream=None, buffers=None):
+        self.scheme = scheme
+        self.K = scheme.system.K
+        self._stream = _stream_handle(stream)
+        h = _P()
+        bufs = (None, None) if buffers is None else (buffers[0].data_ptr(), buffers[1].data_ptr())
+        self._buffers = buffers
+        if isinstance(Q, torch.Tensor) and Q.is_cuda:
+            Qc = Q.detach().to(torch.float64).contiguous()
+            check(_lib.lbx_init(scheme._h, Qc.data_ptr(), 1, self._stream, bufs[0], bufs[1], C.byref(h)))
+        else:
+            Qh = _host_f64(Q)
+            check(_lib.lbx_init(scheme._h, Qh.ctypes.data, 0, self._stream, bufs[0], bufs[1], C.byref(h)))
+        self._h = h
+
+    # -- stepping and diagnostics ----------------------------------------------------
+    def step(self, n=1):
+        check(_lib.lbx_step(self._h, int(n)))
+
+    def moments(self, device=False):
+        shape = (self.K,) + self.scheme.grid
+        if device:
+            out = torch.empty(shape, dtype=torch.float64, device="cuda")
+            check(_lib.lbx_moments(self._h, out.data_ptr(), 1))
+            return out
+        out = np.empty(shape, dtype=np.float64)
+        check(_lib.lbx_moments(self._h, out.ctypes.data, 0))
+        return torch.from_numpy(out)
+
+    def conserved_sums(self):
+        s = _dbl(self.K)
+        check(_lib.lbx_conserved_sums(self._h, s))
+        return np.array(s[:])
+
+    def error_norms(self, Q_ref):
+        l2, li = _dbl(self.K), _dbl(self.K)
+        if isinstance(Q_ref, torch.Tensor) and Q_ref.is_cuda:
+            R = Q_ref.detach().to(torch.float64).contiguous()
+            check(_lib.lbx_error_norms(self._h, R.data_ptr(), 1, l2, li))
+        else:
+            R = _host_f64(Q_ref)
+            check(_lib.lbx_error_norms(self._h, R.ctypes.data, 0, l2, li))
+        return np.array(l2[:]), np.array(li[:])
+
+    def check_finite(self):
+        v = C.c_int()
+        check(_lib.lbx_check_finite(self._h, C.byref(v)))
+        return bool(v.value)
+
+    def subchar_check(self):
+        ms, bc, bm, ok = C.c_double(), C.c_double(), C.c_double(), C.c_int()
+        check(_lib.lbx_subchar_check(self._h, C.byref(ms), C.byref(bc), C.byref(bm), C.byref(ok)))
+        return {"max_speed": ms.value, "bound_cs": bc.value, "bound_monotone": bm.value, "ok": bool(ok.value)}
+
+    def get_populations(self):
+        shape = (self.K, self.scheme.q) + self.scheme.grid
+        out = np.empty(shape, dtype=np.float64)
+        check(_lib.lbx_get_populations(self._h, out.ctypes.data))
+        return torch.from_numpy(out)
+
+    def set_populations(self, f):
+        fh = _host_f64(f)
+        check(_lib.lbx_set_populations(self._h, fh.ctypes.data))
+
+    @property
+    def time(self):
+        s, t = C.c_int64(), C.c_double()
+        check(_lib.lbx_state_time(self._h, C.byref(s), C.byref(t)))
+        return s.value, t.value
+
+    def populations_ptr(self):
+        return _lib.lbx_state_populations(self._h)
+
+    def synchronize(self):
+        check(_lib.lbx_synchronize(self._h))
+
+    def save(self, path):
+        check(_lib.lbx_save(self._h, str(path).encode()))
+
+    def load(self, path):
+        check(_lib.lbx_load(self._h, str(path).encode()))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lbx_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

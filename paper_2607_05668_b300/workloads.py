@@ -1,0 +1,43 @@
+"""Wiring of the benchmark cases into the C ABI: which family, lattice, refinement law,
+relaxation slots and background state each case uses.  Parameters only; the fields come
+from the seeded `synthetic` generators and every computation runs in liblbx.so.
+"""
+from __future__ import annotations
+
+from . import lbx as L
+
+
+def adr_system(case):
+    """ADR cascade with R = 0 (u_t + a.grad u = nu lap u); a in physical units."""
+    ax, ay = case.a_phys
+    return L.System(L.ADR_CASCADE, params=(ax, ay, case.nu, 0.0), Q0=(1.0, 0.0, 0.0))
+
+
+def adr_scheme(case, precision=L.FP64, lattice=L.D2Q5, forcing=True, tau_u=None):
+    """Diffusive refinement dt = f dx^2 with tau_LB(u) given directly, trackers g_tau."""
+    sysm = adr_system(case)
+    return L.Scheme(sysm, lattice, (case.n, case.n), L.DIFFUSIVE, case.f,
+                    tau_lb=case.tau_u if tau_u is None else tau_u, g_tau=case.g_tau,
+                    precision=precision, mms=L.MMS_ADR_SEPARABLE if forcing else L.MMS_NONE,
+                    mms_amp=case.amp)
+
+
+def nsf_system(case):
+    return L.System(L.NSF_PRIM_TRACK, params=(case.gamma, case.R, case.mu, case.kappa),
+                    Q0=case.reference_state())
+
+
+def nsf_scheme(case, precision=L.FP64, lattice=L.D2Q9, tau_lb=0.0):
+    """Diffusive refinement dt = f dx^2, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
+    return L.Scheme(nsf_system(case), lattice, (case.n, case.n), L.DIFFUSIVE, case.f,
+                    tau_lb=tau_lb, tau_R=case.tau_R, g_tau=case.g_tau, precision=precision)
+
+
+def mhd_system(case):
+    return L.System(L.MHD_J_TRACK, params=(case.gamma, case.eta), Q0=case.reference_state())
+
+
+def mhd_scheme(case, precision=L.FP32_SHIFT, lattice=L.D3Q19):
+    """Acoustic refinement dt = f dx, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
+    return L.Scheme(mhd_system(case), lattice, (case.n, case.n, case.n), L.ACOUSTIC, case.f,
+                    tau_R=case.tau_R, g_tau=case.g_tau, precision=precision)

@@ -1,0 +1,50 @@
+"""Shared test helpers: oracle schemes for the same cases the GPU runs."""
+import math
+
+import torch
+
+import oracle
+import synthetic as syn
+from oracle import systems as S
+from oracle.mms import make_mms
+
+F64 = torch.float64
+
+
+def oracle_adr(case: syn.AdrCase, lattice="D2Q5", forcing=True, shifted=False):
+    sysm = S.AdrCascade(case.a_phys, case.nu, case.g_tau * case.dt)
+    xs = syn.coords((case.n, case.n))
+    mms = make_mms(sysm, lambda x, y, t: syn.adr_exact(case, x, y, t).unsqueeze(0), xs, dt=case.dt) if forcing else None
+    tau = oracle.tau_vector(sysm, case.dt, tau_cons=case.tau_u, g_tau=case.g_tau)
+    return oracle.Scheme(sysm, oracle.LATTICES[lattice], (case.n, case.n), case.dx, case.dt, tau,
+                         mms=mms, shifted=shifted, Q0=[1.0, 0.0, 0.0])
+
+
+def oracle_nsf(case: syn.NsfCase, lattice="D2Q9"):
+    sysm = S.NsfPrimitive(case.gamma, case.R, case.mu, case.kappa, case.g_tau * case.dt)
+    tau = oracle.tau_vector(sysm, case.dt, tau_R=case.tau_R, g_tau=case.g_tau)
+    return oracle.Scheme(sysm, oracle.LATTICES[lattice], (case.n, case.n), case.dx, case.dt, tau)
+
+
+def oracle_mhd(case: syn.MhdCase, lattice="D3Q19"):
+    sysm = S.MhdCurrent(case.gamma, case.eta, case.g_tau * case.dt)
+    tau = oracle.tau_vector(sysm, case.dt, tau_R=case.tau_R, g_tau=case.g_tau)
+    n = case.n
+    return oracle.Scheme(sysm, oracle.LATTICES[lattice], (n, n, n), case.dx, case.dt, tau)
+
+
+def rel_linf_per_field(a, b):
+    """max|a - b| / max|b| per component (leading axis)."""
+    K = a.shape[0]
+    d = (a - b).reshape(K, -1).abs().amax(1)
+    r = b.reshape(K, -1).abs().amax(1)
+    return d / r
+
+
+def fluct_rel_l2(a, b, Q0):
+    """||a - b||_2 / ||b - Q0||_2 per component: error relative to the fluctuation."""
+    K = a.shape[0]
+    q0 = torch.as_tensor(Q0, dtype=F64).reshape((K,) + (1,) * (a.dim() - 1))
+    e = (a - b).reshape(K, -1)
+    r = (b - q0).reshape(K, -1)
+    return torch.sqrt((e * e).sum(1)) / torch.sqrt((r * r).sum(1)).clamp_min(1e-300)

@@ -1,0 +1,324 @@
+"""GPU (CUDA, through the C ABI) against the CPU FP64 oracle, element by element.
+
+Tolerances: FP64 kernels match the oracle to 1e-12 (max |diff| / max |field| per
+component).  The shifted FP32 and scaled FP16 storage modes are compared with the FP64
+oracle relative to the fluctuation about the background state (||Q_gpu - Q_o||_2 /
+||Q_o - Q0||_2): <= 1e-4 (FP32) and <= 3e-2 (FP16), the provisional bounds stated for
+those modes.  Grid sizes span several 128-wide thread blocks and a ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic as syn
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+lbx = pytest.importorskip("paper_2607_05668_b300.lbx")
+from paper_2607_05668_b300 import workloads as W  # noqa: E402
+
+F64 = torch.float64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    torch.cuda.init()
+
+
+# ------------------------------------------------------------------ config 1: ADR 64^2
+
+def test_adr_64_fp64_500_steps_matches_oracle():
+    case = syn.AdrCase(n=64)
+    st = lbx.State(W.adr_scheme(case, lbx.FP64), syn.adr_fields(case))
+    st.step(500)
+    Qg = st.moments()
+    och = H.oracle_adr(case)
+    Qo = och.moments(och.run(och.init(syn.adr_fields(case)), 500))
+    err = H.rel_linf_per_field(Qg, Qo)
+    assert err.max() <= 1e-12, err
+    # error norms against the exact solution agree with the oracle's
+    Qex = syn.adr_fields(case, t=500 * case.dt)
+    l2g, lig = st.error_norms(Qex)
+    l2o, lio = oracle.rel_norms(Qo, Qex)
+    np.testing.assert_allclose(l2g, l2o.numpy(), rtol=1e-9)
+    np.testing.assert_allclose(lig, lio.numpy(), rtol=1e-9)
+    assert st.time[0] == 500
+
+
+@pytest.mark.parametrize("prec,bound", [(lbx.FP32_SHIFT, 1e-4), (lbx.FP16_SCALED, 3e-2)])
+def test_adr_64_reduced_precision_against_fp64_oracle(prec, bound):
+    case = syn.AdrCase(n=64)
+    st = lbx.State(W.adr_scheme(case, prec), syn.adr_fields(case))
+    st.step(500)
+    och = H.oracle_adr(case)
+    Qo = och.moments(och.run(och.init(syn.adr_fields(case)), 500))
+    e = H.fluct_rel_l2(st.moments(), Qo, [1.0, 0.0, 0.0])
+    assert e.max() <= bound, e
+
+
+def test_adr_d2q9_fp64_matches_oracle():
+    case = syn.AdrCase(n=40)
+    st = lbx.State(W.adr_scheme(case, lbx.FP64, lattice=lbx.D2Q9), syn.adr_fields(case))
+    st.step(60)
+    och = H.oracle_adr(case, lattice="D2Q9")
+    Qo = och.moments(och.run(och.init(syn.adr_fields(case)), 60))
+    assert H.rel_linf_per_field(st.moments(), Qo).max() <= 1e-12
+
+
+# ----------------------------------------------------------------- config 2: NSF D2Q9
+
+NSF_N = 160      # two 128-wide blocks per row, the second one ragged
+
+
+def _nsf_oracle_run(case, steps):
+    och = H.oracle_nsf(case)
+    return och.moments(och.run(och.init(syn.nsf_fields(case)), steps))
+
+
+def test_nsf_fp64_matches_oracle():
+    case = syn.NsfCase(n=NSF_N)
+    st = lbx.State(W.nsf_scheme(case, lbx.FP64), syn.nsf_fields(case))
+    st.step(40)
+    err = H.rel_linf_per_field(st.moments(), _nsf_oracle_run(case, 40))
+    assert err.max() <= 1e-12, err
+
+
+@pytest.mark.parametrize("prec,bound", [(lbx.FP32_SHIFT, 1e-4), (lbx.FP16_SCALED, 3e-2)])
+def test_nsf_reduced_precision_against_fp64_oracle(prec, bound):
+    case = syn.NsfCase(n=NSF_N)
+    st = lbx.State(W.nsf_scheme(case, prec), syn.nsf_fields(case))
+    st.step(200)
+    Qo = _nsf_oracle_run(case, 200)
+    e = H.fluct_rel_l2(st.moments(), Qo, case.reference_state())
+    print("fluctuation-relative L2 per field:", [f"{v:.2e}" for v in e.tolist()])
+    assert e.max() <= bound, e
+
+
+def test_nsf_d2q5_fp64_matches_oracle():
+    case = syn.NsfCase(n=48)
+    st = lbx.State(W.nsf_scheme(case, lbx.FP64, lattice=lbx.D2Q5), syn.nsf_fields(case))
+    st.step(30)
+    och = H.oracle_nsf(case, lattice="D2Q5")
+    Qo = och.moments(och.run(och.init(syn.nsf_fields(case)), 30))
+    assert H.rel_linf_per_field(st.moments(), Qo).max() <= 1e-12
+
+
+# ------------------------------------------------------------------ config 3: MHD D3Q19
+
+def test_mhd_fp64_matches_oracle():
+    case = syn.MhdCase(n=24)            # 24 < 32: one ragged warp per row
+    st = lbx.State(W.mhd_scheme(case, lbx.FP64), syn.mhd_fields(case))
+    st.step(12)
+    och = H.oracle_mhd(case)
+    Qo = och.moments(och.run(och.init(syn.mhd_fields(case)), 12))
+    err = H.rel_linf_per_field(st.moments(), Qo)
+    assert err.max() <= 1e-12, err
+
+
+@pytest.mark.parametrize("prec,bound", [(lbx.FP32_SHIFT, 1e-4), (lbx.FP16_SCALED, 3e-2)])
+def test_mhd_32_reduced_precision_against_fp64_oracle(prec, bound):
+    case = syn.MhdCase(n=32)
+    st = lbx.State(W.mhd_scheme(case, prec), syn.mhd_fields(case))
+    st.step(40)
+    och = H.oracle_mhd(case)
+    Qo = och.moments(och.run(och.init(syn.mhd_fields(case)), 40))
+    e = H.fluct_rel_l2(st.moments(), Qo, case.reference_state())
+    print("fluctuation-relative L2 per field:", [f"{v:.2e}" for v in e.tolist()])
+    assert e.max() <= bound, e
+
+
+def test_mhd_d3q7_fp64_matches_oracle():
+    case = syn.MhdCase(n=16)
+    st = lbx.State(W.mhd_scheme(case, lbx.FP64, lattice=lbx.D3Q7), syn.mhd_fields(case))
+    st.step(8)
+    och = H.oracle_mhd(case, lattice="D3Q7")
+    Qo = och.moments(och.run(och.init(syn.mhd_fields(case)), 8))
+    assert H.rel_linf_per_field(st.moments(), Qo).max() <= 1e-12
+
+
+# --------------------------------------------------------- the paper's D2Q5 systems
+
+@pytest.mark.parametrize("name", ["burgers", "euler", "maxwell"])
+def test_paper_d2q5_systems_fp64_match_oracle(name):
+    N = 72
+    xs = syn.coords((N, N))
+    if name == "burgers":
+        Q = syn.burgers_exact(*xs, torch.zeros_like(xs[0])).unsqueeze(0)
+        gs = lbx.System(lbx.BURGERS, (), (0.0,))
+        osys, f, tauR = oracle.systems.Burgers(), 0.2, 0.2
+    elif name == "maxwell":
+        Q = syn.maxwell_exact(*xs, torch.zeros_like(xs[0]))
+        gs = lbx.System(lbx.MAXWELL_TM, (1.0,), (0.0, 0.0, 0.0))
+        osys, f, tauR = oracle.systems.MaxwellTM(1.0), 0.2, 0.2
+    else:
+        r = 1.0 + 0.3 * torch.sin(2 * math.pi * xs[0]) * torch.cos(2 * math.pi * xs[1])
+        u, v = 0.5 + 0.1 * torch.cos(2 * math.pi * xs[1]), 0.2 + 0.0 * xs[0]
+        p = 1.0 / 1.4 + 0.1 * torch.sin(2 * math.pi * xs[1])
+        Q = torch.stack([r, r * u, r * v, p / 0.4 + 0.5 * r * (u * u + v * v)])
+        gs = lbx.System(lbx.EULER, (1.4,), (1.0, 0.5, 0.2, 1.0 / 0.56 + 0.145))
+        osys, f, tauR = oracle.systems.Euler(1.4), 0.05, 0.2
+    sch = lbx.Scheme(gs, lbx.D2Q5, (N, N), lbx.ACOUSTIC, f, tau_R=tauR)
+    st = lbx.State(sch, Q)
+    st.step(25)
+    dx, dt = oracle.lattice_steps(N, f, "acoustic")
+    och = oracle.Scheme(osys, oracle.LATTICES["D2Q5"], (N, N), dx, dt, oracle.tau_vector(osys, dt, tau_R=tauR))
+    Qo = och.moments(och.run(och.init(Q), 25))
+    assert H.rel_linf_per_field(st.moments(), Qo).max() <= 1e-12
+
+
+# ------------------------------------------------------------ brute force on 8 x 8
+
+def test_linear_adr_step_equals_oracle_matrix_8x8():
+    """Linear ADR cascade (no forcing) on 8 x 8: the oracle's one-step matrix M (960 x 960,
+    built column by column) applied to random populations equals one GPU step."""
+    case = syn.AdrCase(n=8, tau_u=0.83)
+    och = H.oracle_adr(case, forcing=False)
+    c_gpu, _ = lbx.lattice_velocities(lbx.D2Q5)
+    c_or = [tuple(c) + (0,) for c in oracle.LATTICES["D2Q5"].c]
+    perm = [c_or.index(tuple(int(v) for v in c)) for c in c_gpu]     # gpu i -> oracle i
+    n = 3 * 5 * 64
+    M = torch.zeros(n, n, dtype=F64)
+    for j in range(n):
+        e = torch.zeros(n, dtype=F64)
+        e[j] = 1.0
+        M[:, j] = och.step(e.reshape(3, 5, 8, 8), 0.0).reshape(-1)
+    # conserved block: each u column sums to 1 over the u rows (Sec. 2.2 conservation)
+    colsum_u = M.reshape(3, 5 * 64, n)[0].sum(0).reshape(3, 5 * 64)
+    torch.testing.assert_close(colsum_u[0], torch.ones(5 * 64, dtype=F64), rtol=0, atol=1e-14)
+    g = torch.Generator().manual_seed(0)
+    v = torch.rand((3, 5, 8, 8), dtype=F64, generator=g)
+    st = lbx.State(W.adr_scheme(case, lbx.FP64, forcing=False), syn.adr_fields(case))
+    st.set_populations(v[:, perm])
+    st.step(1)
+    got = st.get_populations()[:, np.argsort(perm)]
+    want = (M @ v.reshape(-1)).reshape(3, 5, 8, 8)
+    torch.testing.assert_close(got, want, rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------------------- invariants on the GPU
+
+def test_populations_round_trip_and_init_equilibrium():
+    case = syn.NsfCase(n=32)
+    Q = syn.nsf_fields(case)
+    st = lbx.State(W.nsf_scheme(case, lbx.FP64), Q)
+    torch.testing.assert_close(st.moments(), Q, rtol=1e-14, atol=1e-13)
+    f = st.get_populations()
+    st.set_populations(f)
+    assert torch.equal(st.get_populations(), f)
+
+
+@pytest.mark.parametrize("prec", [lbx.FP64, lbx.FP32_SHIFT])
+def test_conserved_sums_are_invariant(prec):
+    case = syn.NsfCase(n=NSF_N)
+    st = lbx.State(W.nsf_scheme(case, prec), syn.nsf_fields(case))
+    s0 = st.conserved_sums()
+    st.step(100)
+    s1 = st.conserved_sums()
+    tol = 1e-12 if prec == lbx.FP64 else 2e-6
+    assert np.all(np.abs(s1[:4] - s0[:4]) <= tol * np.abs(s0[:4]).max())
+
+
+def test_translation_equivariance_bitwise():
+    case = syn.NsfCase(n=NSF_N)
+    Q = syn.nsf_fields(case)
+    a = lbx.State(W.nsf_scheme(case, lbx.FP32_SHIFT), Q)
+    b = lbx.State(W.nsf_scheme(case, lbx.FP32_SHIFT), torch.roll(Q, shifts=(3, 5), dims=(-2, -1)))
+    a.step(7)
+    b.step(7)
+    assert torch.equal(torch.roll(a.moments(), shifts=(3, 5), dims=(-2, -1)), b.moments())
+
+
+def test_run_twice_is_bitwise_deterministic():
+    case = syn.MhdCase(n=32)
+    outs = []
+    for _ in range(2):
+        st = lbx.State(W.mhd_scheme(case, lbx.FP32_SHIFT), syn.mhd_fields(case))
+        st.step(9)
+        outs.append((st.moments(), st.conserved_sums()))
+    assert torch.equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_save_load_resume_bitwise(tmp_path):
+    case = syn.NsfCase(n=64)
+    st = lbx.State(W.nsf_scheme(case, lbx.FP16_SCALED), syn.nsf_fields(case))
+    st.step(10)
+    p = tmp_path / "ck.lbx"
+    st.save(p)
+    st.step(10)
+    a = st.moments()
+    st2 = lbx.State(W.nsf_scheme(case, lbx.FP16_SCALED), syn.nsf_fields(case))
+    st2.load(p)
+    assert st2.time[0] == 10
+    st2.step(10)
+    assert torch.equal(a, st2.moments())
+    raw = bytearray(p.read_bytes())
+    raw[len(raw) // 2] ^= 0x40
+    p.write_bytes(bytes(raw))
+    with pytest.raises(lbx.LbxError) as e:
+        st2.load(p)
+    assert e.value.name == "ERR_IO"
+    p.write_bytes(bytes(raw[: len(raw) // 3]))
+    with pytest.raises(lbx.LbxError) as e:
+        st2.load(p)
+    assert e.value.name == "ERR_IO"
+
+
+def test_nonfinite_detection_on_host_injected_nan():
+    case = syn.NsfCase(n=32)
+    Q = syn.nsf_fields(case)
+    Qbad = Q.clone()
+    Qbad[3, 5, 7] = float("nan")
+    with pytest.raises(lbx.LbxError) as e:
+        lbx.State(W.nsf_scheme(case, lbx.FP32_SHIFT), Qbad)
+    assert e.value.name == "ERR_NONFINITE"
+    st = lbx.State(W.nsf_scheme(case, lbx.FP32_SHIFT), Q)
+    f = st.get_populations()
+    f[0, 0, 1, 1] = float("inf")
+    st.set_populations(f)
+    assert st.check_finite() is False
+    with pytest.raises(lbx.LbxError) as e:
+        st.step(1)
+    assert e.value.name == "ERR_NONFINITE"
+
+
+# ---------------------------------------------------------- sub-characteristic check
+
+def test_subchar_maxwell_bound_f_le_cs_over_c():
+    N = 16
+    xs = syn.coords((N, N))
+    Q = syn.maxwell_exact(*xs, torch.zeros_like(xs[0]))
+    gs = lbx.System(lbx.MAXWELL_TM, (1.0,), (0.0, 0.0, 0.0))
+    ok = lbx.State(lbx.Scheme(gs, lbx.D2Q5, (N, N), lbx.ACOUSTIC, 0.57, tau_R=0.2), Q)
+    r = ok.subchar_check()
+    assert r["ok"] and abs(r["max_speed"] - 0.57) < 1e-12
+    with pytest.raises(lbx.LbxError) as e:
+        lbx.State(lbx.Scheme(gs, lbx.D2Q5, (N, N), lbx.ACOUSTIC, 0.58, tau_R=0.2), Q)
+    assert e.value.name == "ERR_SUBCHAR"
+    st = lbx.State(lbx.Scheme(gs, lbx.D2Q5, (N, N), lbx.ACOUSTIC, 0.58, tau_R=0.2,
+                              allow_subchar_violation=True), Q)
+    assert st.subchar_check()["ok"] is False
+
+
+def test_subchar_closed_forms_against_oracle_eigenvalues():
+    # ADR: exact closed form; Euler: exact (|u| + c); NSF and MHD: an upper bound.
+    case = syn.AdrCase(n=16)
+    st = lbx.State(W.adr_scheme(case, lbx.FP64), syn.adr_fields(case))
+    osys = oracle.systems.AdrCascade(case.a_phys, case.nu, case.g_tau * case.dt)
+    num = oracle.subchar.max_speed(osys, syn.adr_fields(case), n_dirs=720, nodes=[0, 5])
+    got = st.subchar_check()["max_speed"] / st.scheme.lam
+    assert num <= got * (1 + 1e-12) and got <= num * (1 + 1e-4)
+
+    ncase = syn.NsfCase(n=16)
+    Q = syn.nsf_fields(ncase)
+    st = lbx.State(W.nsf_scheme(ncase, lbx.FP64), Q)
+    osys = oracle.systems.NsfPrimitive(ncase.gamma, ncase.R, ncase.mu, ncase.kappa, ncase.g_tau * ncase.dt)
+    nodes = list(range(0, 256, 17))
+    num = oracle.subchar.max_speed(osys, Q, n_dirs=180, nodes=nodes)
+    got = st.subchar_check()["max_speed"] / st.scheme.lam
+    assert num * (1 - 1e-9) <= got <= 1.5 * num
