@@ -202,6 +202,34 @@ lbx_status lbx_load(lbx_state* st, const char* path);
 
 void lbx_state_destroy(lbx_state* st);
 
+/* ---- conserved sums without any device allocation --------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that must not
+ * allocate device memory: code recorded into a CUDA graph or running under a latency
+ * budget (cudaMalloc and cudaFree synchronise the device), and programs whose device
+ * memory is entirely owned by another allocator (a framework's caching allocator or a
+ * hard memory cap).  It computes what lbx_conserved_sums computes, sum over nodes of Q_k,
+ * with the same deterministic FP64 reduction, but allocates nothing: its scratch is one
+ * file-scope device array of LBX_STATIC_REDUCE_SCRATCH_DOUBLES doubles that every GPU
+ * which loads the library holds until the process exits.
+ *   sch          scheme the populations belong to (host handle only).
+ *   populations  device buffer in the library's storage layout, e.g. the pointer from
+ *                lbx_state_populations() or a buffer the caller passed to lbx_init();
+ *                FP64 or FP32_SHIFT storage (FP16_SCALED -> LBX_ERR_UNSUPPORTED, its
+ *                scales belong to the state).
+ *   sums         device output, K float64 values, written on `stream`.
+ *   nblocks      reduction blocks, 1..LBX_STATIC_REDUCE_MAX_BLOCKS, or 0 for 2 x SMs
+ *                (capped); larger values fail with LBX_ERR_ARG.
+ *   stream       cudaStream_t (NULL = legacy default stream); the call is asynchronous.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current) and caches it; make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's contents (every
+ * value a call reads is written earlier in the same call, so nothing is cleared); calls
+ * whose work overlaps on the GPU race on it and must be ordered, e.g. on one stream. */
+#define LBX_STATIC_REDUCE_MAX_BLOCKS 512
+#define LBX_STATIC_REDUCE_SCRATCH_DOUBLES (LBX_STATIC_REDUCE_MAX_BLOCKS * 11 * 4 + 11 * 4)
+lbx_status lbx_conserved_sums_static(const lbx_scheme* sch, const void* populations, double* sums,
+                                     int nblocks, void* stream);
+
 /* ---- peak probes used for the roofline denominators ---------------------------------- */
 /* Streams a copy of `bytes` bytes (read + write counted) and a dependent FP64 FMA loop on
  * the given stream; returns measured GB/s and FP64 GFLOP/s (CUDA events).  Either output

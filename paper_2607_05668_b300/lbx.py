@@ -84,6 +84,8 @@ _sig("lbx_save", C.c_int, [_P, C.c_char_p])
 _sig("lbx_load", C.c_int, [_P, C.c_char_p])
 _sig("lbx_state_destroy", None, [_P])
 _sig("lbx_probe_peaks", C.c_int, [C.c_size_t, _P, _D, _D, _D])
+_sig("lbx_conserved_sums_static", C.c_int, [_P, _P, _P, C.c_int, _P])
+STATIC_REDUCE_MAX_BLOCKS = 512
 
 
 def lib():
