@@ -162,6 +162,103 @@ def cells(workload, case):
     return case.n ** (3 if workload == "mhd" else 2)
 
 
+
+# ------------------------------------------------------------------ measurements
+def _timed_steps(obj, stream, steps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    obj.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=False):
+    """Time one grid workload; returns a dict of rate, ms per step and GB/s."""
+    case = make_case(workload, n)
+    K, q = kq(workload)
+    ncell = cells(workload, case)
+    st = L.State(scheme(W, L, workload, case, precision), fields(workload, case).cuda(), stream=stream)
+    if graph:
+        st.use_graph(True)
+    st.step(warmup)
+    st.synchronize()
+    ms = _timed_steps(st, stream, steps)
+    nbytes = 2 * K * q * STORE_BYTES[precision] * ncell
+    out = {"lup_s": ncell / (ms * 1e-3), "ms_per_step": ms, "gbs": nbytes / (ms * 1e-3) / 1e9,
+           "bytes_per_launch": nbytes, "finite": st.check_finite(), "graph": graph}
+    return out, st
+
+
+def fluct_err(Qa, Qb, Q0):
+    """||Qa - Qb||_2 / ||Qb - Q0||_2 per component (device tensors)."""
+    K = Qa.shape[0]
+    q0 = torch.tensor(Q0, dtype=torch.float64, device=Qa.device).reshape((K,) + (1,) * (Qa.dim() - 1))
+    e = (Qa - Qb).reshape(K, -1).norm(dim=1)
+    r = (Qb - q0).reshape(K, -1).norm(dim=1)
+    return (e / r).tolist()
+
+
+def measure_precision_errors(L, W, workload, n, steps, stream):
+    """FP32-shift and FP16-scaled against the FP64 kernel (itself pinned to the CPU oracle
+    to 1e-12) after `steps` steps at full size."""
+    case = make_case(workload, n)
+    Q = fields(workload, case).cuda()
+    ref = L.State(scheme(W, L, workload, case, "fp64"), Q, stream=stream)
+    ref.step(steps)
+    R = ref.moments(device=True)
+    ref.synchronize()
+    ref.close()
+    out = {}
+    for prec in ("fp32", "fp16"):
+        st = L.State(scheme(W, L, workload, case, prec), Q, stream=stream)
+        st.step(steps)
+        Qp = st.moments(device=True)
+        st.synchronize()
+        out[prec] = [float(f"{v:.3e}") for v in fluct_err(Qp, R, case.reference_state())]
+        st.close()
+    del R
+    torch.cuda.empty_cache()
+    return {"steps": steps, "grid": case.n, "fluct_rel_l2_vs_fp64": out}
+
+
+def measure_batch(L, W, steps, warmup, stream, n_inst=512, seed=0, trials=5):
+    cases = syn.adr_batch_draws(n_inst, seed=seed)
+    schemes = [W.adr_scheme(c, L.FP32_SHIFT) for c in cases]
+    b = L.Batch(schemes, [syn.adr_fields(c) for c in cases], stream=stream)
+    rep = b.tune(trials=trials)
+    b.step(warmup)
+    b.synchronize()
+    ms = _timed_steps(b, stream, steps)
+    nbytes = 2 * 3 * 5 * 4 * b.total_cells
+    out = {"instances": n_inst, "total_cells": b.total_cells, "lup_s": b.total_cells / (ms * 1e-3),
+           "ms_per_step": ms, "gbs": nbytes / (ms * 1e-3) / 1e9, "bytes_per_launch": nbytes,
+           "tuned": rep["best"], "graph": True}
+    b.close()
+    return out
+
+
+def run_variants(L, W, args, stream, peak):
+    v = {}
+    t0 = time.perf_counter()
+    for wl, prec, n, steps in (("nsf", "fp64", 1024, 100), ("nsf", "fp16", 1024, 1000),
+                               ("mhd", "fp32", 256, 50), ("mhd", "fp16", 256, 50),
+                               ("adr", "fp64", 64, 500)):
+        # the 64^2 case is launch-latency bound: its 500 steps replay as one CUDA graph
+        r, st = measure_grid(L, W, wl, prec, n, steps, 5 if wl != "adr" else 500, stream, graph=(wl == "adr"))
+        st.close()
+        r["frac_of_hbm_peak"] = r["gbs"] / peak
+        v[f"{wl}_{prec}_{n}"] = r
+        torch.cuda.empty_cache()
+    r = measure_batch(L, W, 200, 5, stream)
+    r["frac_of_hbm_peak"] = r["gbs"] / peak
+    v["adr_batch512_fp32"] = r
+    v["precision_errors"] = {"nsf_1024": measure_precision_errors(L, W, "nsf", 1024, 2000, stream),
+                             "mhd_128": measure_precision_errors(L, W, "mhd", 128, 500, stream)}
+    v["seconds"] = time.perf_counter() - t0
+    return v
+
 # --------------------------------------------------------------------- our arm
 def run_ours(args):
     ws, rank, local = dist_env()
@@ -247,9 +344,10 @@ def run_ours(args):
         "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "finite": finite,
         "clocks": clk.summary(),
     }
-    if args.precision == "fp64" or args.probe:
-        pk = L.probe_peaks(2 << 30, stream=stream)
-        result["probe"] = pk
+    if args.precision == "fp64" or args.probe or not args.no_variants:
+        result["probe"] = L.probe_peaks(2 << 30, stream=stream)
+    if not args.no_variants and args.workload == "nsf" and args.precision == "fp32":
+        result["variants"] = run_variants(L, W, args, stream, peak)
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args, case)
     if rank == 0:
@@ -351,6 +449,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="grid size override")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--probe", action="store_true", help="also run the copy / FMA peak probes")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other precisions and workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -154,9 +154,13 @@ lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_device, voi
 /* Bytes of one population buffer for this scheme (K*q*cells*storage size). */
 size_t lbx_state_buffer_bytes(const lbx_scheme* sch);
 
-/* Advance n >= 0 steps of Eq. lbe_update (fused pull collide-and-stream), asynchronous.
- * Fails with LBX_ERR_NONFINITE without stepping if a previous check found a NaN/Inf. */
+/* Advance 0 <= n <= 2^30 steps of Eq. lbe_update (fused pull collide-and-stream),
+ * asynchronous.  Fails with LBX_ERR_NONFINITE without stepping if a previous check found
+ * a NaN/Inf.  With graph replay enabled, the n launches are recorded into a CUDA graph
+ * the first time this (n, buffer parity) occurs and replayed afterwards. */
 lbx_status lbx_step(lbx_state* st, int64_t n);
+/* Enable (1) or disable (0) graph replay in lbx_step; needs a non-default stream. */
+lbx_status lbx_state_use_graph(lbx_state* st, int enable);
 
 /* Q_k = sum_i f_{k,i} (Eq. moments) at the current time, float64 [K][cells] into host
  * (out_on_device = 0, synchronous) or device memory (1, asynchronous). */
@@ -201,6 +205,39 @@ lbx_status lbx_save(lbx_state* st, const char* path);
 lbx_status lbx_load(lbx_state* st, const char* path);
 
 void lbx_state_destroy(lbx_state* st);
+
+/* ---- batched states: many independent grids, one persistent launch per step ---------
+ * n 2D schemes of the same family, lattice, storage (FP64 or FP32_SHIFT) and forcing,
+ * each with its own extents, parameters and relaxation times, share two population
+ * buffers (instance j at its own 256-byte aligned offset).  One launch of a persistent
+ * kernel advances every instance by one step of Eq. lbe_update: blocks walk a list of
+ * tiles of `block` consecutive cells with a grid-size stride (grid = SMs x ctas_per_sm).
+ * lbx_batch_step records the n launches (plus the step-counter advance) into a CUDA graph
+ * on first use and replays it afterwards (use_graph = 1).
+ * Q[j]: host float64 [K][cells_j].  stream: NULL = a private non-blocking stream.  */
+typedef struct {
+    int block;             /* threads per block and cells per tile (multiple of 32)      */
+    int ctas_per_sm;       /* persistent grid = SM count x ctas_per_sm                    */
+    int steps_per_launch;  /* 1: a step needs every neighbour's previous step             */
+    int use_graph;         /* nonzero: lbx_batch_step replays a captured CUDA graph       */
+} lbx_batch_config;
+
+lbx_status lbx_batch_create(const lbx_scheme* const* schemes, int n, const double* const* Q,
+                            void* stream, lbx_batch** out);
+lbx_status lbx_batch_info(const lbx_batch* b, int* n, int64_t* total_cells, size_t* buffer_bytes);
+/* Advance every instance by n steps (asynchronous on the batch's stream). */
+lbx_status lbx_batch_step(lbx_batch* b, int64_t n);
+lbx_status lbx_batch_synchronize(lbx_batch* b);
+/* Moments of instance j, float64 [K][cells_j] host array (synchronous). */
+lbx_status lbx_batch_moments(lbx_batch* b, int j, double* Q_out);
+lbx_status lbx_batch_get_config(const lbx_batch* b, lbx_batch_config* cfg);
+lbx_status lbx_batch_set_config(lbx_batch* b, const lbx_batch_config* cfg);
+/* Autotuner: times `trials` launches of every (block, ctas_per_sm) candidate with CUDA
+ * events (each launch reads the current buffer and writes the other one without
+ * swapping, so the state does not advance), keeps the fastest and writes a JSON report
+ * of all trials into `report` (may be NULL). */
+lbx_status lbx_batch_tune(lbx_batch* b, int trials, char* report, size_t report_len);
+void lbx_batch_destroy(lbx_batch* b);
 
 /* ---- conserved sums without any device allocation --------------------------------------
  * The paper has no counterpart to this call; it exists for callers that must not

@@ -5,4 +5,4 @@
 Importing the package fails when the CUDA library has not been built.
 """
 from . import lbx  # noqa: F401  (raises ImportError if liblbx.so is missing)
-from .lbx import LbxError, System, Scheme, State, lattice_velocities, probe_peaks  # noqa: F401
+from .lbx import LbxError, System, Scheme, State, Batch, lattice_velocities, probe_peaks  # noqa: F401

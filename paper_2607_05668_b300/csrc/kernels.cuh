@@ -109,8 +109,7 @@ struct PullIdx {
 // ADR manufactured forcing S_MMS(x, t + dt/2) for u_ex = 1 + A sin(2pi x)cos(2pi y)e^-t:
 // e^{-t}[A(-1 + 8 pi^2 nu) s_x c_y + 2 pi A (a_x c_x c_y - a_y s_x s_y)].
 template <typename T>
-__device__ __forceinline__ T adr_mms(const KParams<T>& p, int x, int y) {
-  const long long step = *p.step_ptr + p.step_rel;
+__device__ __forceinline__ T adr_mms(const KParams<T>& p, int x, int y, long long step) {
   const T th = (T(step) + T(0.5)) * p.dt;
   const T e = exp(-th);
   const T* tb = p.mms_tab;
@@ -119,16 +118,16 @@ __device__ __forceinline__ T adr_mms(const KParams<T>& p, int x, int y) {
 }
 
 // --------------------------------------------------------------------------- the step
+// One node of one grid: pull, moments, flux/source, equilibrium, BGK, store.  `step` is
+// the index of the step being taken (only the manufactured forcing uses it).
 template <class Lat, template <typename> class SysT, class St, bool REG>
-__global__ void k_step(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
-                       const KParams<typename St::C> p) {
+__device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
+                                          const KParams<typename St::C>& p, int x, int y, int z,
+                                          long long step) {
   using T = typename St::C;
   using S = typename St::S;
   using Sys = SysT<T>;
   constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= p.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
   const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
   const size_t plane = (size_t)p.ncell;
   const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
@@ -156,7 +155,7 @@ __global__ void k_step(const typename St::S* __restrict__ A, typename St::S* __r
   for (int k = 0; k < K; ++k) dQ[k] = St::SHIFT ? X[k] : X[k] - p.Q0[k];
   T Phi[K][D], Src[K];
   Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
-  if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y);
+  if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y, step);
 
   // a4 + a5 + a6: equilibrium (Eq. feq), BGK with source (Eq. lbe_update), store
 #pragma unroll
@@ -186,6 +185,43 @@ __global__ void k_step(const typename St::S* __restrict__ A, typename St::S* __r
       T out = fma(om, feq - f, f) + wi * sdt;
       if (St::SCALE) out *= p.inv_scale[k];
       st_out(B + ((size_t)k * Q + i) * plane + cell, out);
+    }
+  }
+}
+
+// One grid, one thread per node, blocks of 128 along x.
+template <class Lat, template <typename> class SysT, class St, bool REG>
+__global__ void k_step(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
+                       const KParams<typename St::C> p) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const long long step = p.mms_tab != nullptr ? *p.step_ptr + p.step_rel : 0;
+  step_node<Lat, SysT, St, REG>(A, B, p, x, blockIdx.y, blockIdx.z, step);
+}
+
+// Many independent 2D grids in one persistent launch.  Instance j's populations start at
+// element offset off[j] of the shared buffers; the work list holds tiles of blockDim.x
+// consecutive cells (row-major, so a tile of a narrow grid spans several rows), and each
+// block walks the list with a grid-size stride.
+template <typename T>
+struct BatchInst {
+  KParams<T> p;
+  long long off;
+};
+
+template <class Lat, template <typename> class SysT, class St, bool REG>
+__global__ void k_step_batch(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
+                             const BatchInst<typename St::C>* __restrict__ insts, const int2* __restrict__ tiles,
+                             int ntiles, const long long* __restrict__ step_ptr, int step_rel) {
+  const long long step = *step_ptr + step_rel;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int2 tl = tiles[t];
+    const KParams<typename St::C> p = insts[tl.x].p;
+    const long long off = insts[tl.x].off;
+    const int c = tl.y + (int)threadIdx.x;
+    if (c < p.ncell) {
+      const int y = c / p.nx;
+      step_node<Lat, SysT, St, REG>(A + off, B + off, p, c - y * p.nx, y, 0, step);
     }
   }
 }

@@ -438,12 +438,22 @@ struct OpsImpl {
     return cudaGetLastError();
   }
   static const void* step_fn() { return (const void*)k_step<Lat, SysT, St, REG>; }
+  static cudaError_t batch_step(const void* A, void* B, const void* insts, const int2* tiles, int ntiles,
+                                const long long* step_ptr, int step_rel, int grid, int block, cudaStream_t strm) {
+    k_step_batch<Lat, SysT, St, REG><<<grid, block, 0, strm>>>((const S*)A, (S*)B, (const BatchInst<C>*)insts,
+                                                                tiles, ntiles, step_ptr, step_rel);
+    return cudaGetLastError();
+  }
+  static const void* batch_fn() { return (const void*)k_step_batch<Lat, SysT, St, REG>; }
 };
 
 template <class Lat, template <typename> class SysT, class St>
 static Ops make_ops() {
   using I = OpsImpl<Lat, SysT, St>;
-  return Ops{I::step, I::init, I::gather, I::scatter, I::reduce, I::step_fn, I::REG};
+  return Ops{I::step,       I::init,     I::gather,
+             I::scatter,    I::reduce,   I::step_fn,
+             I::REG,        I::batch_step, I::batch_fn,
+             sizeof(BatchInst<typename St::C>), sizeof(typename St::S)};
 }
 
 template <class Lat, template <typename> class SysT>
@@ -494,6 +504,7 @@ bool lbx::find_ops(int family, int lattice, int precision, Ops* o) {
 
 static void free_state(lbx_state* st) {
   if (!st) return;
+  for (auto& g : st->graphs) cudaGraphExecDestroy(g.second);
   if (st->own_a && st->fa) cudaFree(st->fa);
   if (st->own_b && st->fb) cudaFree(st->fb);
   cudaFree(st->d_step);
@@ -505,7 +516,7 @@ static void free_state(lbx_state* st) {
   delete st;
 }
 
-static void feq0_table(const lbx_scheme& s, double* out) {
+void lbx::feq0_table(const lbx_scheme& s, double* out) {
   double F0[KMAX][3];
   background_flux(&s, F0);
   const double lc = s.lam / s.cs2;
@@ -676,28 +687,58 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
 #undef CKI
 }
 
+// Enqueue n steps (ping-pong from the current buffer) and, with forcing, the device
+// step-counter advance; does not touch the host-side bookkeeping.
+static cudaError_t enqueue_steps(lbx_state* st, int64_t n, bool start_a) {
+  bool a = start_a;
+  for (int64_t r = 0; r < n; ++r) {
+    cudaError_t e = st->ops.step(st, a ? st->fa : st->fb, a ? st->fb : st->fa, (int)r, st->stream);
+    if (e != cudaSuccess) return e;
+    a = !a;
+  }
+  if (st->sch.d.mms != LBX_MMS_NONE) return launch_advance(st->d_step, n, st->stream);
+  return cudaSuccess;
+}
+
+extern "C" lbx_status lbx_state_use_graph(lbx_state* st, int enable) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_state_use_graph: null state");
+  if (enable && st->stream == nullptr)
+    return fail(LBX_ERR_STATE, "lbx_state_use_graph: graph capture needs a stream other than the legacy default");
+  st->use_graph = enable != 0;
+  return LBX_OK;
+}
+
 extern "C" lbx_status lbx_step(lbx_state* st, int64_t n) {
   if (!st) return fail(LBX_ERR_ARG, "lbx_step: null state");
-  if (n < 0) return fail(LBX_ERR_ARG, "lbx_step: negative step count");
+  if (n < 0 || n > (int64_t(1) << 30)) return fail(LBX_ERR_ARG, "lbx_step: step count out of range");
   if (st->nonfinite) return fail(LBX_ERR_NONFINITE, "lbx_step: state holds non-finite values");
-  const bool forced = st->sch.d.mms != LBX_MMS_NONE;
-  int64_t done = 0;
-  while (done < n) {
-    const int64_t chunk = (n - done) < (int64_t(1) << 30) ? (n - done) : (int64_t(1) << 30);
-    for (int64_t r = 0; r < chunk; ++r) {
-      cudaError_t e = st->ops.step(st, st->cur(), st->nxt(), (int)r, st->stream);
-      if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_step: launch failed: %s", cudaGetErrorString(e));
-      st->cur_a = !st->cur_a;
+  if (n == 0) return LBX_OK;
+  if (st->use_graph) {
+    const auto key = std::make_pair((long long)n, st->cur_a ? 1 : 0);
+    auto it = st->graphs.find(key);
+    if (it == st->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(st->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_steps(st, n, st->cur_a);
+      cudaError_t e2 = cudaStreamEndCapture(st->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(LBX_ERR_CUDA, "lbx_step: graph capture failed: %s", cudaGetErrorString(e ? e : e2));
+      }
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_step: graph instantiate: %s", cudaGetErrorString(e));
+      it = st->graphs.emplace(key, ex).first;
     }
-    if (forced) {
-      k_advance<<<1, 1, 0, st->stream>>>(st->d_step, chunk);
-      CK(cudaGetLastError());
-    } else {
-      st->step_dirty = true;
-    }
-    done += chunk;
-    st->step += chunk;
+    CK(cudaGraphLaunch(it->second, st->stream));
+  } else {
+    cudaError_t e = enqueue_steps(st, n, st->cur_a);
+    if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_step: launch failed: %s", cudaGetErrorString(e));
   }
+  if (st->sch.d.mms == LBX_MMS_NONE) st->step_dirty = true;
+  if (n & 1) st->cur_a = !st->cur_a;
+  st->step += n;
   return LBX_OK;
 }
 
@@ -825,3 +866,8 @@ extern "C" void lbx_state_destroy(lbx_state* st) {
 }
 
 lbx_status lbx::ensure_step_counter(lbx_state* st) { return sync_step_counter(st); }
+
+cudaError_t lbx::launch_advance(long long* step, long long n, cudaStream_t s) {
+  k_advance<<<1, 1, 0, s>>>(step, n);
+  return cudaGetLastError();
+}

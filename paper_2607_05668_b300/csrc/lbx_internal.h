@@ -3,6 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
+#include <utility>
+
 #include "lbx.h"
 #include "kernels.cuh"
 
@@ -33,6 +36,12 @@ struct Ops {
   cudaError_t (*reduce)(const lbx_state*, const void* A, const double* Qref, double* partials, int nblk, int mode);
   const void* (*step_fn)();
   bool reg;
+  // batched persistent step: insts = BatchInst<C>[n] on the device
+  cudaError_t (*batch_step)(const void* A, void* B, const void* insts, const int2* tiles, int ntiles,
+                            const long long* step_ptr, int step_rel, int grid, int block, cudaStream_t);
+  const void* (*batch_fn)();
+  size_t inst_bytes;   // sizeof(BatchInst<C>)
+  size_t elem_bytes;   // storage bytes per population value
 };
 
 lbx_status fail(lbx_status s, const char* fmt, ...);
@@ -63,6 +72,8 @@ struct lbx_state {
   double scale[lbx::KMAX];
   lbx::KParams<double> pd;
   lbx::KParams<float> pf;
+  bool use_graph = false;       // lbx_step replays captured graphs
+  std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
 
   void* cur() const { return cur_a ? fa : fb; }
   void* nxt() const { return cur_a ? fb : fa; }
@@ -79,4 +90,6 @@ namespace lbx {
 void refresh_params(lbx_state* st);
 lbx_status run_reduce(lbx_state* st, const double* Qref, int mode, double* host_out);
 lbx_status ensure_step_counter(lbx_state* st);
+void feq0_table(const lbx_scheme& s, double* out);                 // f^eq(Q0) [K][q]
+cudaError_t launch_advance(long long* step, long long n, cudaStream_t s);
 }  // namespace lbx

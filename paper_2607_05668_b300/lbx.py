@@ -70,6 +70,7 @@ _sig("lbx_lattice_velocities", C.c_int, [C.c_int, _I, _I, _D])
 _sig("lbx_init", C.c_int, [_P, _P, C.c_int, _P, _P, _P, C.POINTER(_P)])
 _sig("lbx_state_buffer_bytes", C.c_size_t, [_P])
 _sig("lbx_step", C.c_int, [_P, C.c_int64])
+_sig("lbx_state_use_graph", C.c_int, [_P, C.c_int])
 _sig("lbx_moments", C.c_int, [_P, _P, C.c_int])
 _sig("lbx_conserved_sums", C.c_int, [_P, _D])
 _sig("lbx_error_norms", C.c_int, [_P, _P, C.c_int, _D, _D])
@@ -217,7 +218,13 @@ class State:
     def step(self, n=1):
         check(_lib.lbx_step(self._h, int(n)))
 
+    def use_graph(self, enable=True):
+        """Replay lbx_step's launches from captured CUDA graphs (needs a non-default stream)."""
+        check(_lib.lbx_state_use_graph(self._h, int(bool(enable))))
+
     def moments(self, device=False):
+        """Q [K, *grid] float64.  device=True returns a CUDA tensor written asynchronously on
+        the state's stream (synchronize before reading it from another stream)."""
         shape = (self.K,) + self.scheme.grid
         if device:
             out = torch.empty(shape, dtype=torch.float64, device="cuda")
@@ -287,6 +294,80 @@ class State:
     def close(self):
         if getattr(self, "_h", None):
             _lib.lbx_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+# --------------------------------------------------------------------------- batches
+class BatchConfig(C.Structure):
+    _fields_ = [("block", C.c_int), ("ctas_per_sm", C.c_int), ("steps_per_launch", C.c_int),
+                ("use_graph", C.c_int)]
+
+
+_sig("lbx_batch_create", C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P), _P, C.POINTER(_P)])
+_sig("lbx_batch_info", C.c_int, [_P, _I, C.POINTER(C.c_int64), C.POINTER(C.c_size_t)])
+_sig("lbx_batch_step", C.c_int, [_P, C.c_int64])
+_sig("lbx_batch_synchronize", C.c_int, [_P])
+_sig("lbx_batch_moments", C.c_int, [_P, C.c_int, _P])
+_sig("lbx_batch_get_config", C.c_int, [_P, C.POINTER(BatchConfig)])
+_sig("lbx_batch_set_config", C.c_int, [_P, C.POINTER(BatchConfig)])
+_sig("lbx_batch_tune", C.c_int, [_P, C.c_int, C.c_char_p, C.c_size_t])
+_sig("lbx_batch_destroy", None, [_P])
+
+
+class Batch:
+    """lbx_batch_create ... lbx_batch_destroy: independent 2D grids advanced together."""
+
+    def __init__(self, schemes, fields, stream=None):
+        self.schemes = list(schemes)
+        n = len(self.schemes)
+        arr = (_P * n)(*[s._h for s in self.schemes])
+        host = [_host_f64(Q) for Q in fields]
+        qp = (_P * n)(*[h.ctypes.data for h in host])
+        h = _P()
+        check(_lib.lbx_batch_create(arr, n, qp, None if stream is None else _stream_handle(stream), C.byref(h)))
+        self._h = h
+        nn, cells, nbytes = C.c_int(), C.c_int64(), C.c_size_t()
+        check(_lib.lbx_batch_info(h, C.byref(nn), C.byref(cells), C.byref(nbytes)))
+        self.n, self.total_cells, self.buffer_bytes = nn.value, cells.value, nbytes.value
+
+    def step(self, n=1):
+        check(_lib.lbx_batch_step(self._h, int(n)))
+
+    def synchronize(self):
+        check(_lib.lbx_batch_synchronize(self._h))
+
+    def moments(self, j):
+        s = self.schemes[j]
+        out = np.empty((s.system.K,) + s.grid, dtype=np.float64)
+        check(_lib.lbx_batch_moments(self._h, j, out.ctypes.data))
+        return torch.from_numpy(out)
+
+    @property
+    def config(self):
+        c = BatchConfig()
+        check(_lib.lbx_batch_get_config(self._h, C.byref(c)))
+        return {"block": c.block, "ctas_per_sm": c.ctas_per_sm, "steps_per_launch": c.steps_per_launch,
+                "use_graph": bool(c.use_graph)}
+
+    def set_config(self, block=None, ctas_per_sm=None, use_graph=None, steps_per_launch=None):
+        cur = self.config
+        c = BatchConfig(block or cur["block"], ctas_per_sm or cur["ctas_per_sm"],
+                        steps_per_launch or cur["steps_per_launch"],
+                        int(cur["use_graph"] if use_graph is None else use_graph))
+        check(_lib.lbx_batch_set_config(self._h, C.byref(c)))
+
+    def tune(self, trials=5):
+        buf = C.create_string_buffer(1 << 15)
+        check(_lib.lbx_batch_tune(self._h, int(trials), buf, len(buf)))
+        import json
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lbx_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

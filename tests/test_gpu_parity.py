@@ -322,3 +322,21 @@ def test_subchar_closed_forms_against_oracle_eigenvalues():
     num = oracle.subchar.max_speed(osys, Q, n_dirs=180, nodes=nodes)
     got = st.subchar_check()["max_speed"] / st.scheme.lam
     assert num * (1 - 1e-9) <= got <= 1.5 * num
+
+
+def test_graph_replay_matches_plain_launches_with_forcing():
+    """lbx_step with graph replay (forcing needs the device step counter advanced inside the
+    graph) equals plain launches bitwise, for repeated and odd step counts."""
+    case = syn.AdrCase(n=64)
+    s = torch.cuda.Stream()
+    g = lbx.State(W.adr_scheme(case, lbx.FP64), syn.adr_fields(case), stream=s)
+    p = lbx.State(W.adr_scheme(case, lbx.FP64), syn.adr_fields(case), stream=s)
+    g.use_graph(True)
+    for n in (7, 7, 4, 1, 7):
+        g.step(n)
+        p.step(n)
+    assert g.time == p.time == (26, 26 * case.dt)
+    assert torch.equal(g.moments(), p.moments())
+    with pytest.raises(lbx.LbxError) as e:
+        lbx.State(W.adr_scheme(case, lbx.FP64), syn.adr_fields(case), stream=0).use_graph(True)
+    assert e.value.name == "ERR_STATE"
