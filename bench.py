@@ -239,6 +239,25 @@ def measure_batch(L, W, steps, warmup, stream, n_inst=512, seed=0, trials=5):
     return out
 
 
+def measure_adjoint(L, W, n=256, steps=2000, ckpt=64):
+    """Config 5: gradient of the final density misfit for NSF D2Q9 FP32-shift, checkpoint
+    every `ckpt` steps.  Bytes per node-step: forward 2 K q s twice (sweep + recompute) plus
+    the reverse step (Lam in and out, forward state in) 3 K q s."""
+    case = syn.NsfCase(n=n)
+    sch = W.nsf_scheme(case, L.FP32_SHIFT)
+    Q, tgt = syn.nsf_fields(case), syn.density_target(n)
+    L.adjoint(sch, Q, 64, 16, tgt)        # warm-up (module load, allocations)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, g, gt = L.adjoint(sch, Q, steps, ckpt, tgt)
+    sec = time.perf_counter() - t0
+    K, q = 10, 9
+    nbytes = (2 * 2 * K * q * 4 + 3 * K * q * 4) * case.n * case.n * steps
+    return {"grid": n, "steps": steps, "ckpt_every": ckpt, "seconds_per_gradient": sec,
+            "effective_gbs": nbytes / sec / 1e9, "J": J, "dJ_dtau": gt,
+            "note": "wall time of lbx_adjoint incl. allocation, host copies and the FP64 reductions"}
+
+
 def run_variants(L, W, args, stream, peak):
     v = {}
     t0 = time.perf_counter()
@@ -254,6 +273,7 @@ def run_variants(L, W, args, stream, peak):
     r = measure_batch(L, W, 200, 5, stream)
     r["frac_of_hbm_peak"] = r["gbs"] / peak
     v["adr_batch512_fp32"] = r
+    v["adjoint_nsf256_fp32"] = measure_adjoint(L, W)
     v["precision_errors"] = {"nsf_1024": measure_precision_errors(L, W, "nsf", 1024, 2000, stream),
                              "mhd_128": measure_precision_errors(L, W, "mhd", 128, 500, stream)}
     v["seconds"] = time.perf_counter() - t0

@@ -239,6 +239,22 @@ lbx_status lbx_batch_set_config(lbx_batch* b, const lbx_batch_config* cfg);
 lbx_status lbx_batch_tune(lbx_batch* b, int trials, char* report, size_t report_len);
 void lbx_batch_destroy(lbx_batch* b);
 
+/* ---- adjoint: gradient of a final-time density misfit -------------------------------
+ * J = 1/2 sum_x (rho(x, T) - rho*(x))^2 after n_steps steps from populations at the
+ * (shifted) equilibrium of Q_init.  Computes J, dJ/dQ_init (float64 [K][cells], every
+ * component of the initial fields, trackers included) and dJ/dtau, tau the tau_LB
+ * shared by the conserved fields.  The discrete adjoint of Eq. lbe_update runs on the
+ * GPU (reverse pull along -c_i with the node-local flux and source Jacobians taken by
+ * forward-mode dual numbers); the forward state is checkpointed every ckpt_every steps
+ * and each segment is recomputed bitwise before its reverse sweep, so device memory
+ * holds about (n_steps/ckpt_every + ckpt_every) population buffers.  The relaxation-time
+ * term is accumulated per node in float64.  Storage FP64 or FP32_SHIFT (the adjoint runs
+ * in the same arithmetic).  Q_init and rho_target are host arrays; outputs are host
+ * pointers (any may be NULL); synchronous. */
+lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, int64_t n_steps, int ckpt_every,
+                       const double* rho_target, void* stream, double* J, double* dJ_dQ0,
+                       double* dJ_dtau);
+
 /* ---- conserved sums without any device allocation --------------------------------------
  * The paper has no counterpart to this call; it exists for callers that must not
  * allocate device memory: code recorded into a CUDA graph or running under a latency

@@ -1,0 +1,203 @@
+// Gradient of a final-time density misfit by the discrete adjoint of the scheme, with
+// checkpoint-and-recompute (see adjoint.cuh for the per-step derivation).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "adjoint.cuh"
+#include "lbx.h"
+#include "lbx_internal.h"
+
+using namespace lbx;
+
+namespace {
+
+struct AdjOps {
+  cudaError_t (*step)(const void* An, const void* Lnext, void* Lout, const lbx_state* st, double* tau_acc);
+  cudaError_t (*seed)(const void* AN, const double* target, void* L, const lbx_state* st);
+  cudaError_t (*init)(const void* L0, const double* Qinit, const lbx_state* st, double* dJdQ);
+  size_t lam_bytes;
+};
+
+template <class Lat, template <typename> class SysT, class St>
+struct AdjImpl {
+  using C = typename St::C;
+  using S = typename St::S;
+  static dim3 block(const lbx_scheme& s) { return dim3(s.nx >= 128 ? 128 : ((s.nx + 31) / 32) * 32, 1, 1); }
+  static dim3 grid(const lbx_scheme& s) {
+    dim3 b = block(s);
+    return dim3((s.nx + b.x - 1) / b.x, s.ny, s.nz);
+  }
+  static cudaError_t step(const void* An, const void* Lnext, void* Lout, const lbx_state* st, double* tau_acc) {
+    k_adj_step<Lat, SysT, St><<<grid(st->sch), block(st->sch), 0, st->stream>>>(
+        (const S*)An, (const C*)Lnext, (C*)Lout, st->pc<C>(), tau_acc);
+    return cudaGetLastError();
+  }
+  static cudaError_t seed(const void* AN, const double* target, void* L, const lbx_state* st) {
+    k_adj_seed<Lat, SysT, St><<<grid(st->sch), block(st->sch), 0, st->stream>>>((const S*)AN, target, (C*)L, st->pd);
+    return cudaGetLastError();
+  }
+  static cudaError_t init(const void* L0, const double* Qinit, const lbx_state* st, double* dJdQ) {
+    k_adj_init<Lat, SysT, St><<<grid(st->sch), block(st->sch), 0, st->stream>>>((const C*)L0, Qinit, st->pd, dJdQ);
+    return cudaGetLastError();
+  }
+};
+
+template <class Lat, template <typename> class SysT>
+bool pick(int precision, AdjOps* o) {
+  if (precision == LBX_FP64) {
+    using I = AdjImpl<Lat, SysT, StoreF64>;
+    *o = AdjOps{I::step, I::seed, I::init, sizeof(double)};
+    return true;
+  }
+  if (precision == LBX_FP32_SHIFT) {
+    using I = AdjImpl<Lat, SysT, StoreF32>;
+    *o = AdjOps{I::step, I::seed, I::init, sizeof(float)};
+    return true;
+  }
+  return false;
+}
+
+bool find_adj(int family, int lattice, int precision, AdjOps* o) {
+  switch (family) {
+    case LBX_ADR_CASCADE:
+      if (lattice == LBX_D2Q5) return pick<LatD2Q5, SysADR>(precision, o);
+      if (lattice == LBX_D2Q9) return pick<LatD2Q9, SysADR>(precision, o);
+      return false;
+    case LBX_NSF_PRIM_TRACK:
+      if (lattice == LBX_D2Q5) return pick<LatD2Q5, SysNSF>(precision, o);
+      if (lattice == LBX_D2Q9) return pick<LatD2Q9, SysNSF>(precision, o);
+      return false;
+    case LBX_MHD_J_TRACK:
+      if (lattice == LBX_D3Q19) return pick<LatD3Q19, SysMHD>(precision, o);
+      return false;
+    case LBX_EULER:
+      if (lattice == LBX_D2Q5) return pick<LatD2Q5, SysEuler>(precision, o);
+      return false;
+    case LBX_BURGERS:
+      if (lattice == LBX_D2Q5) return pick<LatD2Q5, SysBurgers>(precision, o);
+      return false;
+    case LBX_MAXWELL_TM:
+      if (lattice == LBX_D2Q5) return pick<LatD2Q5, SysMaxwell>(precision, o);
+      return false;
+  }
+  return false;
+}
+
+// Deterministic float64 sum of n values by one block (fixed thread strides, fixed tree).
+__global__ void k_sum_f64(const double* __restrict__ v, long long n, double* __restrict__ out) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
+}  // namespace
+
+extern "C" lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, int64_t n_steps, int ckpt_every,
+                                  const double* rho_target, void* stream, double* J, double* dJ_dQ0,
+                                  double* dJ_dtau) {
+  if (!sch || !Q_init || !rho_target) return fail(LBX_ERR_ARG, "lbx_adjoint: null argument");
+  if (n_steps < 0 || n_steps > (int64_t(1) << 30)) return fail(LBX_ERR_ARG, "lbx_adjoint: step count out of range");
+  if (ckpt_every < 1) return fail(LBX_ERR_ARG, "lbx_adjoint: ckpt_every must be >= 1");
+  AdjOps adj;
+  if (!find_adj(sch->sys.family, sch->d.lattice, sch->d.precision, &adj))
+    return fail(LBX_ERR_UNSUPPORTED, "lbx_adjoint: FP64 or FP32_SHIFT storage of a compiled family needed");
+  lbx_state* st = nullptr;
+  if (lbx_status s = lbx_init(sch, Q_init, 0, stream, nullptr, nullptr, &st)) return s;
+  const int K = sch->sys.K, q = sch->q;
+  const long long ncell = sch->ncell;
+  const size_t bytes = lbx_state_buffer_bytes(sch);
+  const size_t lam_bytes = (size_t)K * q * ncell * adj.lam_bytes;
+  const long long k = std::min<long long>(ckpt_every, std::max<long long>(n_steps, 1));
+  const long long nck = n_steps == 0 ? 0 : (n_steps + k - 1) / k;
+  char *ckpt = nullptr, *seg = nullptr;
+  void *La = nullptr, *Lb = nullptr;
+  double *tau_acc = nullptr, *d_tgt = nullptr, *d_Qref = nullptr, *d_Q = nullptr, *d_grad = nullptr, *d_sum = nullptr;
+  lbx_status rc = LBX_OK;
+  cudaError_t e = cudaSuccess;
+  auto cleanup = [&]() {
+    cudaFree(ckpt); cudaFree(seg); cudaFree(La); cudaFree(Lb); cudaFree(tau_acc); cudaFree(d_tgt);
+    cudaFree(d_Qref); cudaFree(d_Q); cudaFree(d_grad); cudaFree(d_sum);
+    lbx_state_destroy(st);
+  };
+#define STEP(call)                                                                                   \
+  do {                                                                                               \
+    e = (call);                                                                                      \
+    if (e != cudaSuccess) {                                                                          \
+      rc = fail(e == cudaErrorMemoryAllocation ? LBX_ERR_OOM : LBX_ERR_CUDA, "lbx_adjoint: %s: %s", #call, \
+                cudaGetErrorString(e));                                                              \
+      cleanup();                                                                                     \
+      return rc;                                                                                     \
+    }                                                                                                \
+  } while (0)
+  const cudaStream_t s = st->stream;
+  if (nck > 0) STEP(cudaMalloc((void**)&ckpt, bytes * nck));
+  if (nck > 0) STEP(cudaMalloc((void**)&seg, bytes * k));
+  STEP(cudaMalloc(&La, lam_bytes));
+  STEP(cudaMalloc(&Lb, lam_bytes));
+  STEP(cudaMalloc((void**)&tau_acc, sizeof(double) * ncell));
+  STEP(cudaMemsetAsync(tau_acc, 0, sizeof(double) * ncell, s));
+  STEP(cudaMalloc((void**)&d_tgt, sizeof(double) * ncell));
+  STEP(cudaMemcpyAsync(d_tgt, rho_target, sizeof(double) * ncell, cudaMemcpyHostToDevice, s));
+  STEP(cudaMalloc((void**)&d_Qref, sizeof(double) * K * ncell));
+  STEP(cudaMemsetAsync(d_Qref, 0, sizeof(double) * K * ncell, s));
+  STEP(cudaMemcpyAsync(d_Qref, d_tgt, sizeof(double) * ncell, cudaMemcpyDeviceToDevice, s));
+  STEP(cudaMalloc((void**)&d_Q, sizeof(double) * K * ncell));
+  STEP(cudaMemcpyAsync(d_Q, Q_init, sizeof(double) * K * ncell, cudaMemcpyHostToDevice, s));
+  STEP(cudaMalloc((void**)&d_grad, sizeof(double) * K * ncell));
+  STEP(cudaMalloc((void**)&d_sum, sizeof(double)));
+  // forward sweep, keeping the state at the start of every segment
+  for (long long c = 0; c < nck; ++c) {
+    STEP(cudaMemcpyAsync(ckpt + bytes * c, st->cur(), bytes, cudaMemcpyDeviceToDevice, s));
+    const long long len = std::min(k, n_steps - c * k);
+    if ((rc = lbx_step(st, len))) {
+      cleanup();
+      return rc;
+    }
+  }
+  // misfit J = 1/2 sum (rho - rho*)^2 (deterministic float64 reduction)
+  {
+    double out[KMAX * 4];
+    if ((rc = run_reduce(st, d_Qref, 1, out))) {
+      cleanup();
+      return rc;
+    }
+    if (J) *J = 0.5 * out[0];
+  }
+  STEP(adj.seed(st->cur(), d_tgt, La, st));
+  // reverse sweep: recompute each segment from its checkpoint, then step the adjoint back
+  void* Lnext = La;
+  void* Lout = Lb;
+  for (long long c = nck - 1; c >= 0; --c) {
+    const long long len = std::min(k, n_steps - c * k);
+    STEP(cudaMemcpyAsync(seg, ckpt + bytes * c, bytes, cudaMemcpyDeviceToDevice, s));
+    long long base = c * k;
+    STEP(cudaMemcpyAsync(st->d_step, &base, sizeof(base), cudaMemcpyHostToDevice, s));
+    STEP(cudaStreamSynchronize(s));   // `base` lives on this stack frame
+    for (long long m = 0; m + 1 < len; ++m) STEP(st->ops.step(st, seg + bytes * m, seg + bytes * (m + 1), (int)m, s));
+    for (long long m = len - 1; m >= 0; --m) {
+      STEP(adj.step(seg + bytes * m, Lnext, Lout, st, tau_acc));
+      std::swap(Lnext, Lout);
+    }
+  }
+  STEP(adj.init(Lnext, d_Q, st, d_grad));
+  if (dJ_dQ0) STEP(cudaMemcpyAsync(dJ_dQ0, d_grad, sizeof(double) * K * ncell, cudaMemcpyDeviceToHost, s));
+  k_sum_f64<<<1, 256, 0, s>>>(tau_acc, ncell, d_sum);
+  STEP(cudaGetLastError());
+  double tsum = 0.0;
+  STEP(cudaMemcpyAsync(&tsum, d_sum, sizeof(double), cudaMemcpyDeviceToHost, s));
+  STEP(cudaStreamSynchronize(s));
+  const double tau = sch->tau[0];
+  if (dJ_dtau) *dJ_dtau = tsum / (tau * tau);
+  cleanup();
+  return LBX_OK;
+#undef STEP
+}

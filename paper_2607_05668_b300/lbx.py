@@ -86,6 +86,7 @@ _sig("lbx_load", C.c_int, [_P, C.c_char_p])
 _sig("lbx_state_destroy", None, [_P])
 _sig("lbx_probe_peaks", C.c_int, [C.c_size_t, _P, _D, _D, _D])
 _sig("lbx_conserved_sums_static", C.c_int, [_P, _P, _P, C.c_int, _P])
+_sig("lbx_adjoint", C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, _D, _P, _D])
 STATIC_REDUCE_MAX_BLOCKS = 512
 
 
@@ -372,3 +373,14 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+def adjoint(scheme: Scheme, Q_init, n_steps, ckpt_every, rho_target, stream=None):
+    """lbx_adjoint: (J, dJ/dQ_init [K, *grid] float64 tensor, dJ/dtau)."""
+    Qh = _host_f64(Q_init)
+    th = _host_f64(rho_target)
+    J, gt = C.c_double(), C.c_double()
+    g = np.empty((scheme.system.K,) + scheme.grid, dtype=np.float64)
+    check(_lib.lbx_adjoint(scheme._h, Qh.ctypes.data, int(n_steps), int(ckpt_every), th.ctypes.data,
+                           _stream_handle(stream), C.byref(J), g.ctypes.data, C.byref(gt)))
+    return J.value, torch.from_numpy(g), gt.value
