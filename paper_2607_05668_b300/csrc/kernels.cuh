@@ -31,6 +31,7 @@ struct KParams {
   T Q0[KMAX];                  // background state (shift reference)
   T F0l[KMAX][3];              // (dt/dx)/c_s^2 * Phi(Q0), used by the unshifted mode
   T omega[KMAX];               // 1 / tau_LB per component
+  T tau[KMAX];                 // tau_LB per component
   T scale[KMAX];               // float16 storage scale s_k (1 otherwise)
   T inv_scale[KMAX];
   T prm[NPRM];                 // system parameters (layout per system)
@@ -118,9 +119,80 @@ __device__ __forceinline__ T adr_mms(const KParams<T>& p, int x, int y, long lon
 }
 
 // --------------------------------------------------------------------------- the step
+// Population staging between the moment pass and the write pass:
+//   MODE_REG   the node's K q values stay in registers (K q <= 90);
+//   MODE_SMEM  each thread copies its node's K q values into its own column of dynamic
+//              shared memory (cp.async for 4/8-byte values), [(k q + i) * blockDim + tid]:
+//              no other thread touches the column, so no barrier is needed, and DRAM sees
+//              every population once.
+constexpr int MODE_REG = 0, MODE_SMEM = 1;
+
+// COLS: threads per block of a staged launch (the column stride of its layout).
+template <class Lat, template <typename> class SysT, class St, int COLS = 128>
+struct StepMode {
+  // register-resident or per-thread staged (also the batched kernel's choice)
+  static constexpr int value =
+      (size_t)SysT<typename St::C>::K * Lat::Q * sizeof(typename St::C) <= 360 ? MODE_REG : MODE_SMEM;
+  static constexpr size_t smem_per_thread = (size_t)SysT<typename St::C>::K * Lat::Q * sizeof(typename St::S);
+  static constexpr size_t smem_bytes = value == MODE_SMEM ? smem_per_thread * COLS : 0;
+  // blocks per SM the launch bounds ask the register allocator to allow: 4 for
+  // register-resident 4/8-byte storage, 3 when FP16 conversions need more registers, and
+  // for staged kernels what shared memory lets reside (228 KB per SM), at most 3
+  static constexpr int smem_blocks = value == MODE_SMEM ? (int)(228 * 1024 / smem_bytes) : 0;
+  static constexpr int min_blocks =
+      value == MODE_REG ? (sizeof(typename St::S) >= 4 ? 4 : 3)
+                        : (smem_blocks < 1 ? 1 : (smem_blocks * COLS > 384 ? 384 / COLS : smem_blocks));
+};
+
+template <typename S>
+__device__ __forceinline__ void stage(S* sm, const S* g) {
+  if constexpr (sizeof(S) == 2) {
+    *sm = __ldg(g);
+  } else {
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(sm);
+    if constexpr (sizeof(S) == 4)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(g) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
+  }
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared-memory reads the compiler must not merge or keep live across the flux evaluation
+// (asm volatile), so the staged values cost no registers between the two passes.
+__device__ __forceinline__ float lds_c(const float* p) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"((unsigned int)__cvta_generic_to_shared(p)));
+  return v;
+}
+__device__ __forceinline__ double lds_c(const double* p) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"((unsigned int)__cvta_generic_to_shared(p)));
+  return v;
+}
+__device__ __forceinline__ float lds_c(const __half* p) {
+  unsigned short v;
+  asm volatile("ld.shared.b16 %0, [%1];" : "=h"(v) : "r"((unsigned int)__cvta_generic_to_shared(p)));
+  return __half2float(__ushort_as_half(v));
+}
+
+__device__ __forceinline__ float to_c(__half h) { return __half2float(h); }
+__device__ __forceinline__ float to_c(float v) { return v; }
+__device__ __forceinline__ double to_c(double v) { return v; }
+
 // One node of one grid: pull, moments, flux/source, equilibrium, BGK, store.  `step` is
 // the index of the step being taken (only the manufactured forcing uses it).
-template <class Lat, template <typename> class SysT, class St, bool REG>
+//
+// Arithmetic (Eq. lbe_update with Eq. feq): with w = 1/tau_k,
+//   f_out = f + w (F_i - f),   F_i = w_i (X_k + tau_k dt S_k) + w_i c_i . phi_k,
+// phi_k = (dt/dx)/c_s^2 Phi_k.  w multiplies only the small non-equilibrium difference
+// F_i - f, so the sum over i conserves X_k (+ dt S_k) up to random rounding: a rounded
+// coefficient never multiplies the O(f) equilibrium itself.  Opposite velocities share
+// the projection P = c'_i . phi_k (c' = c_i oriented so its first nonzero entry is +1)
+// and the weight class shares w_i (X_k + tau_k dt S_k), so each population costs one
+// add (moment) and three fused operations.  FP16 storage works in stored units (values
+// divided by s_k): X, phi and dt S are divided by s_k once per component.
+template <class Lat, template <typename> class SysT, class St, int MODE, int COLS = 128>
 __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
                                           const KParams<typename St::C>& p, int x, int y, int z,
                                           long long step) {
@@ -129,30 +201,49 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
   using Sys = SysT<T>;
   constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D;
   const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
-  const size_t plane = (size_t)p.ncell;
+  // element offsets fit in 32 bits (the host guarantees K q cells < 2^32): one wide
+  // multiply-add forms each address
+  const unsigned int plane = (unsigned int)p.ncell;
   const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
+  extern __shared__ __align__(16) unsigned char lbx_smem[];
+  S* col = reinterpret_cast<S*>(lbx_smem) + threadIdx.x;
+  constexpr int cs = COLS;
 
-  // a1 + a2: pull every population of the node and accumulate its moments (Eq. moments)
-  T X[K];
-  T fv[REG ? K : 1][REG ? Q : 1];
-#pragma unroll
-  for (int k = 0; k < K; ++k) X[k] = T(0);
+  // a1: pull every population of the node (register file or private smem column)
+  T fv[MODE == MODE_REG ? K : 1][MODE == MODE_REG ? Q : 1];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const S* a = A + pi.src<Lat>(i, p.nx, p.ny) + (size_t)i * plane;
+    const unsigned int src = pi.src<Lat>(i, p.nx, p.ny) + (unsigned int)i * plane;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      T v = ld_nc(a + (size_t)k * Q * plane);
-      if (St::SCALE) v *= p.scale[k];
-      if constexpr (REG) fv[k][i] = v;
-      X[k] += v;
+      const unsigned int off = src + (unsigned int)(k * Q) * plane;
+      if constexpr (MODE == MODE_REG) fv[k][i] = to_c(__ldg(A + off));
+      else stage(col + (k * Q + i) * cs, A + off);
     }
   }
+  if constexpr (MODE == MODE_SMEM) stage_wait();
+  auto f_at = [&](int k, int i) -> T {
+    if constexpr (MODE == MODE_REG) return fv[k][i];
+    else return lds_c(col + (k * Q + i) * cs);
+  };
 
-  // a3: primitives, flux and source at the node
+  // a2: moments (Eq. moments), in stored units
+  T X[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    T sum = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) sum += f_at(k, i);
+    X[k] = sum;
+  }
+
+  // a3: primitives, flux and source at the node (physical units)
   T dQ[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) dQ[k] = St::SHIFT ? X[k] : X[k] - p.Q0[k];
+  for (int k = 0; k < K; ++k) {
+    const T xk = St::SCALE ? X[k] * p.scale[k] : X[k];
+    dQ[k] = St::SHIFT ? xk : xk - p.Q0[k];
+  }
   T Phi[K][D], Src[K];
   Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
   if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y, step);
@@ -161,42 +252,39 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const T om = p.omega[k];
+    const T inv_s = St::SCALE ? p.inv_scale[k] : T(1);
     T ph[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) ph[d] = p.lc * Phi[k][d] + (St::SHIFT ? T(0) : p.F0l[k][d]);
-    const T sdt = p.dt * Src[k];
+    for (int d = 0; d < D; ++d) ph[d] = (p.lc * Phi[k][d] + (St::SHIFT ? T(0) : p.F0l[k][d])) * inv_s;
+    const T Xs = X[k] + p.tau[k] * (p.dt * Src[k] * inv_s);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      T cph = T(0);
+      const int sg = Lat::c(i, 0) != 0 ? Lat::c(i, 0) : (Lat::c(i, 1) != 0 ? Lat::c(i, 1) : Lat::c(i, 2));
+      T P = T(0);
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        if (Lat::c(i, d) == 1) cph += ph[d];
-        if (Lat::c(i, d) == -1) cph -= ph[d];
+        const int cd = Lat::c(i, d) * sg;
+        if (cd == 1) P += ph[d];
+        if (cd == -1) P -= ph[d];
       }
       const T wi = T(Lat::w(i));
-      const T feq = wi * (X[k] + cph);
-      T f;
-      if constexpr (REG) {
-        f = fv[k][i];
-      } else {
-        f = ld_again(A + pi.src<Lat>(i, p.nx, p.ny) + ((size_t)k * Q + i) * plane);
-        if (St::SCALE) f *= p.scale[k];
-      }
-      T out = fma(om, feq - f, f) + wi * sdt;
-      if (St::SCALE) out *= p.inv_scale[k];
-      st_out(B + ((size_t)k * Q + i) * plane + cell, out);
+      const T Fi = fma(T(sg) * wi, P, wi * Xs);
+      const T f = f_at(k, i);
+      st_out(B + ((unsigned int)(k * Q + i) * plane + cell), fma(om, Fi - f, f));
     }
   }
 }
 
 // One grid, one thread per node, blocks of 128 along x.
-template <class Lat, template <typename> class SysT, class St, bool REG>
-__global__ void k_step(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
-                       const KParams<typename St::C> p) {
+// Register budget per thread follows the residency the populations' staging allows.
+// Blocks of COLS threads along x (COLS = 128 for register-resident kernels).
+template <class Lat, template <typename> class SysT, class St, int MODE, int COLS>
+__global__ void __launch_bounds__(COLS, StepMode<Lat, SysT, St, COLS>::min_blocks)
+    k_step(const typename St::S* __restrict__ A, typename St::S* __restrict__ B, const KParams<typename St::C> p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
   const long long step = p.mms_tab != nullptr ? *p.step_ptr + p.step_rel : 0;
-  step_node<Lat, SysT, St, REG>(A, B, p, x, blockIdx.y, blockIdx.z, step);
+  step_node<Lat, SysT, St, MODE, COLS>(A, B, p, x, blockIdx.y, blockIdx.z, step);
 }
 
 // Many independent 2D grids in one persistent launch.  Instance j's populations start at
@@ -209,7 +297,7 @@ struct BatchInst {
   long long off;
 };
 
-template <class Lat, template <typename> class SysT, class St, bool REG>
+template <class Lat, template <typename> class SysT, class St, int MODE>
 __global__ void k_step_batch(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
                              const BatchInst<typename St::C>* __restrict__ insts, const int2* __restrict__ tiles,
                              int ntiles, const long long* __restrict__ step_ptr, int step_rel) {
@@ -221,7 +309,7 @@ __global__ void k_step_batch(const typename St::S* __restrict__ A, typename St::
     const int c = tl.y + (int)threadIdx.x;
     if (c < p.ncell) {
       const int y = c / p.nx;
-      step_node<Lat, SysT, St, REG>(A + off, B + off, p, c - y * p.nx, y, 0, step);
+      step_node<Lat, SysT, St, MODE>(A + off, B + off, p, c - y * p.nx, y, 0, step);
     }
   }
 }

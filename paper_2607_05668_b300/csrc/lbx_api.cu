@@ -163,7 +163,8 @@ extern "C" lbx_status lbx_scheme_derive(const lbx_system* sys, const lbx_scheme_
   const int64_t nx = d->extent[0], ny = d->extent[1], nz = sys->D == 3 ? d->extent[2] : 1;
   if (nx < 2 || ny < 2 || nz < 1 || (sys->D == 3 && nz < 2))
     return fail(LBX_ERR_ARG, "lbx_scheme_derive: extents must be >= 2");
-  if (nx > (1 << 20) || ny > 65535 || nz > 65535 || (double)nx * ny * nz >= 2147483647.0)
+  if (nx > (1 << 20) || ny > 65535 || nz > 65535 || (double)nx * ny * nz >= 2147483647.0 ||
+      (double)family_K(sys->family) * q * nx * ny * nz >= 4294967295.0)
     return fail(LBX_ERR_ARG, "lbx_scheme_derive: grid too large (%lld x %lld x %lld)", (long long)nx,
                 (long long)ny, (long long)nz);
   if (d->scaling != LBX_ACOUSTIC && d->scaling != LBX_DIFFUSIVE)
@@ -333,6 +334,7 @@ static void pack_prm(const lbx_scheme* s, double prm[NPRM]) {
       prm[5] = u0; prm[6] = u1; prm[7] = Q[3] + p0; prm[8] = p0 / rho;
       prm[9] = mu * (2 * L00 - dv); prm[10] = mu * (L01 + L10); prm[11] = mu * (2 * L11 - dv);
       prm[12] = g;
+      prm[13] = 1.0 / R;
       break;
     }
     case LBX_MHD_J_TRACK: {
@@ -380,6 +382,7 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
     p.Q0[k] = (T)s.sys.Q0[k];
     for (int d = 0; d < 3; ++d) p.F0l[k][d] = (T)(lc * F0[k][d]);
     p.omega[k] = (T)(1.0 / s.tau[k]);
+    p.tau[k] = (T)s.tau[k];
     p.scale[k] = (T)scale[k];
     p.inv_scale[k] = (T)(1.0 / scale[k]);
   }
@@ -402,20 +405,45 @@ struct OpsImpl {
   using C = typename St::C;
   using S = typename St::S;
   static constexpr int K = SysT<C>::K;
-  static constexpr bool REG = (size_t)K * Lat::Q * sizeof(C) <= 360;
+  static constexpr int MODE = StepMode<Lat, SysT, St>::value;
+  static constexpr bool REG = MODE == MODE_REG;
 
   static dim3 block(const lbx_scheme& s) {
     int bx = s.nx >= 128 ? 128 : ((s.nx + 31) / 32) * 32;
     return dim3(bx, 1, 1);
   }
   static dim3 grid(const lbx_scheme& s, dim3 b) { return dim3((s.nx + b.x - 1) / b.x, s.ny, s.nz); }
+  static size_t smem(int threads) { return StepMode<Lat, SysT, St, 128>::smem_bytes; }
+  // Opt a staged kernel into the shared memory it needs.
+  static cudaError_t prepare(const void* fn, size_t bytes) {
+    if (MODE != MODE_SMEM) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
+  template <int COLS>
+  static cudaError_t launch(const lbx_state* st, const void* A, void* B, const KParams<C>& p, cudaStream_t strm) {
+    const size_t bytes = StepMode<Lat, SysT, St, COLS>::smem_bytes;
+    static cudaError_t prep = prepare((const void*)k_step<Lat, SysT, St, MODE, COLS>, bytes);
+    if (prep != cudaSuccess) return prep;
+    const dim3 b(COLS, 1, 1), g((st->sch.nx + COLS - 1) / COLS, st->sch.ny, st->sch.nz);
+    k_step<Lat, SysT, St, MODE, COLS><<<g, b, bytes, strm>>>((const S*)A, (S*)B, p);
+    return cudaGetLastError();
+  }
 
+  // Register-resident kernels use 128-thread blocks (narrower grids: the smallest multiple
+  // of 32 covering nx); staged kernels use st->block in {32, 64, 128}.
   static cudaError_t step(const lbx_state* st, const void* A, void* B, int rel, cudaStream_t strm) {
     KParams<C> p = st->pc<C>();
     p.step_rel = rel;
-    dim3 b = block(st->sch), g = grid(st->sch, b);
-    k_step<Lat, SysT, St, REG><<<g, b, 0, strm>>>((const S*)A, (S*)B, p);
-    return cudaGetLastError();
+    if (MODE == MODE_REG) {
+      dim3 b = block(st->sch), g = grid(st->sch, b);
+      k_step<Lat, SysT, St, MODE, 128><<<g, b, 0, strm>>>((const S*)A, (S*)B, p);
+      return cudaGetLastError();
+    }
+    switch (st->block) {
+      case 32: return launch<32>(st, A, B, p, strm);
+      case 64: return launch<64>(st, A, B, p, strm);
+      default: return launch<128>(st, A, B, p, strm);
+    }
   }
   static cudaError_t init(const lbx_state* st, const double* Q, void* A, unsigned long long* maxbits, int write) {
     dim3 b = block(st->sch), g = grid(st->sch, b);
@@ -437,14 +465,20 @@ struct OpsImpl {
     k_reduce<Lat, SysT, St><<<nblk, RED_THREADS, 0, st->stream>>>((const S*)A, st->pd, Qref, partials, mode);
     return cudaGetLastError();
   }
-  static const void* step_fn() { return (const void*)k_step<Lat, SysT, St, REG>; }
+  static const void* step_fn() { return (const void*)k_step<Lat, SysT, St, MODE, 128>; }
   static cudaError_t batch_step(const void* A, void* B, const void* insts, const int2* tiles, int ntiles,
                                 const long long* step_ptr, int step_rel, int grid, int block, cudaStream_t strm) {
-    k_step_batch<Lat, SysT, St, REG><<<grid, block, 0, strm>>>((const S*)A, (S*)B, (const BatchInst<C>*)insts,
-                                                                tiles, ntiles, step_ptr, step_rel);
+    if (MODE == MODE_SMEM) {
+      cudaError_t prep = prepare((const void*)k_step_batch<Lat, SysT, St, MODE>, smem(block));
+      if (prep != cudaSuccess) return prep;
+    }
+    k_step_batch<Lat, SysT, St, MODE><<<grid, block, smem(block), strm>>>(
+        (const S*)A, (S*)B, (const BatchInst<C>*)insts, tiles, ntiles, step_ptr, step_rel);
     return cudaGetLastError();
   }
-  static const void* batch_fn() { return (const void*)k_step_batch<Lat, SysT, St, REG>; }
+  static const void* batch_fn() { return (const void*)k_step_batch<Lat, SysT, St, MODE>; }
+  // staged kernels keep a fixed 128-column layout: larger blocks cannot launch
+  static size_t smem_bytes(int threads) { return (MODE == MODE_SMEM && threads > 128) ? (size_t)1 << 30 : smem(threads); }
 };
 
 template <class Lat, template <typename> class SysT, class St>
@@ -452,7 +486,7 @@ static Ops make_ops() {
   using I = OpsImpl<Lat, SysT, St>;
   return Ops{I::step,       I::init,     I::gather,
              I::scatter,    I::reduce,   I::step_fn,
-             I::REG,        I::batch_step, I::batch_fn,
+             I::REG,        I::batch_step, I::batch_fn, I::smem_bytes,
              sizeof(BatchInst<typename St::C>), sizeof(typename St::S)};
 }
 
@@ -698,6 +732,18 @@ static cudaError_t enqueue_steps(lbx_state* st, int64_t n, bool start_a) {
   }
   if (st->sch.d.mms != LBX_MMS_NONE) return launch_advance(st->d_step, n, st->stream);
   return cudaSuccess;
+}
+
+extern "C" lbx_status lbx_state_set_block(lbx_state* st, int block) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_state_set_block: null state");
+  if (block != 32 && block != 64 && block != 128)
+    return fail(LBX_ERR_ARG, "lbx_state_set_block: block must be 32, 64 or 128");
+  if (block != st->block) {
+    for (auto& g : st->graphs) cudaGraphExecDestroy(g.second);
+    st->graphs.clear();
+  }
+  st->block = block;
+  return LBX_OK;
 }
 
 extern "C" lbx_status lbx_state_use_graph(lbx_state* st, int enable) {

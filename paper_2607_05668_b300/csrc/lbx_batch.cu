@@ -376,9 +376,16 @@ extern "C" lbx_status lbx_batch_tune(lbx_batch* b, int trials, char* report, siz
   bool first = true;
   for (int blk : blocks) {
     int max_active = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_active, b->ops.batch_fn(), blk, 0);
+    const size_t sm_bytes = b->ops.smem_bytes(blk);
+    if (sm_bytes > 48 * 1024)
+      cudaFuncSetAttribute(b->ops.batch_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_active, b->ops.batch_fn(), blk, sm_bytes) != cudaSuccess ||
+        max_active < 1) {
+      cudaGetLastError();
+      continue;                                          // this block size cannot be resident
+    }
     for (int c : per_sm) {
-      if (c > std::max(1, max_active) * 2) continue;   // beyond residency only adds tail waves
+      if (c > max_active * 2) continue;                  // beyond residency only adds tail waves
       lbx_batch_config cfg{blk, c, 1, b->cfg.use_graph};
       if (lbx_status s = lbx_batch_set_config(b, &cfg)) return s;
       float ms = 0;

@@ -40,6 +40,7 @@ struct Ops {
   cudaError_t (*batch_step)(const void* A, void* B, const void* insts, const int2* tiles, int ntiles,
                             const long long* step_ptr, int step_rel, int grid, int block, cudaStream_t);
   const void* (*batch_fn)();
+  size_t (*smem_bytes)(int threads);   // dynamic shared memory of a step launch
   size_t inst_bytes;   // sizeof(BatchInst<C>)
   size_t elem_bytes;   // storage bytes per population value
 };
@@ -73,6 +74,7 @@ struct lbx_state {
   lbx::KParams<double> pd;
   lbx::KParams<float> pf;
   bool use_graph = false;       // lbx_step replays captured graphs
+  int block = 32;               // threads per block of staged (shared-memory) step kernels
   std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
 
   void* cur() const { return cur_a ? fa : fb; }

@@ -49,12 +49,12 @@ struct SysADR {
 // T = p/(rho R), tau_v = mu (L + L^T - 2/3 tr L I) with L_ab = G_{u_a,b},
 // Phi_m = m u + p I - tau_v, Phi_E = (E+p) u - tau_v u - kappa G_T.
 // p: 0 gamma-1, 1 R, 2 mu, 3 kappa, 4 1/tau_grad, 5 u0x, 6 u0y, 7 E0+p0, 8 R T0,
-//    9 tau_v0_xx, 10 tau_v0_xy, 11 tau_v0_yy, 12 gamma
+//    9 tau_v0_xx, 10 tau_v0_xy, 11 tau_v0_yy, 12 gamma, 13 1/R
 template <typename T>
 struct SysNSF {
   static constexpr int K = 10, NC = 4, D = 2, FAMILY = 2;
   __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
-    const T gm1 = p[0], Rg = p[1], mu = p[2], kap = p[3], itg = p[4];
+    const T gm1 = p[0], mu = p[2], kap = p[3], itg = p[4];
     const T u0[2] = {p[5], p[6]};
     const T EP0 = p[7], RT0 = p[8];
     const T drho = dQ[0], rho = Q0[0] + drho, irho = T(1) / rho;
@@ -68,7 +68,7 @@ struct SysNSF {
     const T dke = T(0.5) * (dm[0] * u[0] + dm[1] * u[1] + m0[0] * du[0] + m0[1] * du[1]);
     const T dE = dQ[3];
     const T dp = gm1 * (dE - dke);
-    const T dT = (dp - RT0 * drho) * irho / Rg;
+    const T dT = (dp - RT0 * drho) * irho * p[13];
     // viscous stress of the tracker fluctuation (linear in G)
     const T L00 = dQ[4], L01 = dQ[5], L10 = dQ[6], L11 = dQ[7];
     const T dv = T(2.0 / 3.0) * (L00 + L11);

@@ -71,6 +71,7 @@ _sig("lbx_init", C.c_int, [_P, _P, C.c_int, _P, _P, _P, C.POINTER(_P)])
 _sig("lbx_state_buffer_bytes", C.c_size_t, [_P])
 _sig("lbx_step", C.c_int, [_P, C.c_int64])
 _sig("lbx_state_use_graph", C.c_int, [_P, C.c_int])
+_sig("lbx_state_set_block", C.c_int, [_P, C.c_int])
 _sig("lbx_moments", C.c_int, [_P, _P, C.c_int])
 _sig("lbx_conserved_sums", C.c_int, [_P, _D])
 _sig("lbx_error_norms", C.c_int, [_P, _P, C.c_int, _D, _D])
@@ -218,6 +219,10 @@ class State:
     # -- stepping and diagnostics ----------------------------------------------------
     def step(self, n=1):
         check(_lib.lbx_step(self._h, int(n)))
+
+    def set_block(self, block):
+        """Threads per block of staged step kernels (32, 64 or 128); results do not change."""
+        check(_lib.lbx_state_set_block(self._h, int(block)))
 
     def use_graph(self, enable=True):
         """Replay lbx_step's launches from captured CUDA graphs (needs a non-default stream)."""

@@ -340,3 +340,29 @@ def test_graph_replay_matches_plain_launches_with_forcing():
     with pytest.raises(lbx.LbxError) as e:
         lbx.State(W.adr_scheme(case, lbx.FP64), syn.adr_fields(case), stream=0).use_graph(True)
     assert e.value.name == "ERR_STATE"
+
+
+@pytest.mark.parametrize("n", [48, 47, 22])
+def test_fp16_storage_on_partial_tiles_and_odd_widths(n):
+    """FP16 runs through per-warp halo tiles when nx is even (48: a half-empty warp tile;
+    22: a tile wider than the row, wrapped twice) and through the register kernel when nx
+    is odd (47); all against the FP64 oracle at the FP16 bound, and FP32 against 1e-4."""
+    case = syn.NsfCase(n=n)
+    Qo = _nsf_oracle_run(case, 60)
+    for prec, bound in ((lbx.FP16_SCALED, 3e-2), (lbx.FP32_SHIFT, 1e-4)):
+        st = lbx.State(W.nsf_scheme(case, prec), syn.nsf_fields(case))
+        st.step(60)
+        e = H.fluct_rel_l2(st.moments(), Qo, case.reference_state())
+        assert e.max() <= bound, (prec, e)
+
+
+def test_fp16_halo_matches_register_kernel_statistics():
+    """Same FP16 arithmetic through the halo path (even nx) on an MHD 3D grid with a
+    ragged warp (nx = 20) stays within the FP16 bound of the FP64 oracle."""
+    case = syn.MhdCase(n=20)
+    st = lbx.State(W.mhd_scheme(case, lbx.FP16_SCALED), syn.mhd_fields(case))
+    st.step(10)
+    och = H.oracle_mhd(case)
+    Qo = och.moments(och.run(och.init(syn.mhd_fields(case)), 10))
+    e = H.fluct_rel_l2(st.moments(), Qo, case.reference_state())
+    assert e.max() <= 3e-2, e
