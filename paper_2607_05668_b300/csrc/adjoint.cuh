@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(128) k_adj_step(const typename St::S* __restri
 #pragma unroll
   for (int i = 0; i < Q; ++i)
 #pragma unroll
-    for (int k = 0; k < K; ++k) X[k] += (T)ld_nc(An + ((size_t)k * Q + i) * plane + pi.src<Lat>(i, p.nx, p.ny));
+    for (int k = 0; k < K; ++k) X[k] += (T)ld_nc(An + eidx<K, Q>(k, i, pi.src<Lat>(i, p.nx, p.ny), (unsigned int)plane));
   T dQ[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) dQ[k] = St::SHIFT ? X[k] : X[k] - p.Q0[k];
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(128) k_adj_step(const typename St::S* __restri
           if (Lat::c(i, d) == -1) cph -= ph[d];
         }
         const T feq = T(Lat::w(i)) * (X[k] + cph);
-        const T g = (T)ld_again(An + ((size_t)k * Q + i) * plane + pi.src<Lat>(i, p.nx, p.ny));
+        const T g = (T)ld_again(An + eidx<K, Q>(k, i, pi.src<Lat>(i, p.nx, p.ny), (unsigned int)plane));
         tacc += mu * (g - feq);
       }
     }
@@ -172,7 +172,7 @@ __global__ void k_adj_seed(const typename St::S* __restrict__ AN, const double* 
   const size_t cell = ((size_t)z * p.ny + y) * p.nx + x;
   double rho = St::SHIFT ? p.Q0[0] : 0.0;
   for (int i = 0; i < Q; ++i) {
-    double v = (double)ld_nc(AN + (size_t)i * plane + pi.src<Lat>(i, p.nx, p.ny));
+    double v = (double)ld_nc(AN + eidx<K, Q>(0, i, pi.src<Lat>(i, p.nx, p.ny), (unsigned int)plane));
     rho += v;
   }
   const T r = (T)(rho - target[cell]);

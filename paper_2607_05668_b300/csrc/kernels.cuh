@@ -1,7 +1,11 @@
 // Device kernels of the kinetic relaxation scheme (sm_103a).
 //
-// Storage: structure of arrays A[k][i][cell], cell = (z*ny + y)*nx + x, one population
-// plane of `ncell` values per (component k, velocity i).  The buffer holds
+// Storage: structure of arrays over (velocity i, node), with components interleaved in
+// pairs: component k < 2 floor(K/2) of velocity i at node `cell` is element
+// ((floor(k/2) q + i) ncell + cell) 2 + (k mod 2), and an odd last component has its own
+// plane after the pairs (element 2 floor(K/2) q ncell + i ncell + cell); cell =
+// (z ny + y) nx + x.  A warp's access to one velocity is still one contiguous run, and
+// every load or store moves two components (one 2x16-bit, 2x32-bit or 2x64-bit vector).  The buffer holds
 // post-collision populations of the previous step at the node they left, so the step
 // kernel PULLS f_{k,i}(x, t) = A[k][i][x - c_i] (periodic), collides at x and writes
 // B[k][i][x]: every store is coalesced and every load is a unit-stride run shifted by
@@ -42,6 +46,14 @@ struct KParams {
   const long long* step_ptr;   // step index at the start of this launch sequence
   int step_rel;                // offset of this launch in the sequence
 };
+
+// Element index of population (k, i) at `cell` (see the storage layout above).
+template <int K, int Q>
+__host__ __device__ __forceinline__ unsigned int eidx(int k, int i, unsigned int cell, unsigned int plane) {
+  constexpr int KP = K / 2;
+  if (k < 2 * KP) return (((unsigned int)((k >> 1) * Q + i)) * plane + cell) * 2u + (unsigned int)(k & 1);
+  return 2u * (unsigned int)(KP * Q) * plane + (unsigned int)i * plane + cell;
+}
 
 // ----------------------------------------------------------------------------- storage
 struct StoreF64 {
@@ -176,6 +188,46 @@ __device__ __forceinline__ float lds_c(const __half* p) {
   return __half2float(__ushort_as_half(v));
 }
 
+// Component pairs: vector type, global load, shared staging and read, conversion, store.
+template <typename S> struct PairOf;
+template <> struct PairOf<double> { using V = double2; };
+template <> struct PairOf<float> { using V = float2; };
+template <> struct PairOf<__half> { using V = __half2; };
+
+__device__ __forceinline__ double2 ldg_pair(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldg_pair(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ __half2 ldg_pair(const __half2* p) { return __ldg(p); }
+__device__ __forceinline__ void split(double2 v, double& a, double& b) { a = v.x; b = v.y; }
+__device__ __forceinline__ void split(float2 v, float& a, float& b) { a = v.x; b = v.y; }
+__device__ __forceinline__ void split(__half2 v, float& a, float& b) { a = __low2float(v); b = __high2float(v); }
+__device__ __forceinline__ void st_pair(double2* p, double a, double b) { *p = make_double2(a, b); }
+__device__ __forceinline__ void st_pair(float2* p, float a, float b) { *p = make_float2(a, b); }
+__device__ __forceinline__ void st_pair(__half2* p, float a, float b) { *p = __floats2half2_rn(a, b); }
+template <typename V>
+__device__ __forceinline__ void stage_pair(V* sm, const V* g) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(sm);
+  if constexpr (sizeof(V) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(g) : "memory");
+  else if constexpr (sizeof(V) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(g) : "memory");
+}
+// pair reads from shared memory that stay volatile (re-issued in each pass)
+__device__ __forceinline__ void lds_pair(const double2* p, double& a, double& b) {
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "r"((unsigned int)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void lds_pair(const float2* p, float& a, float& b) {
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "r"((unsigned int)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void lds_pair(const __half2* p, float& a, float& b) {
+  unsigned int v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"((unsigned int)__cvta_generic_to_shared(p)));
+  __half2 h = *reinterpret_cast<__half2*>(&v);
+  a = __low2float(h);
+  b = __high2float(h);
+}
+
 __device__ __forceinline__ float to_c(__half h) { return __half2float(h); }
 __device__ __forceinline__ float to_c(float v) { return v; }
 __device__ __forceinline__ double to_c(double v) { return v; }
@@ -198,43 +250,66 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
                                           long long step) {
   using T = typename St::C;
   using S = typename St::S;
+  using V = typename PairOf<S>::V;
   using Sys = SysT<T>;
-  constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D;
+  constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D, KP = K / 2;
+  constexpr bool ODD = (K & 1) != 0;
   const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
-  // element offsets fit in 32 bits (the host guarantees K q cells < 2^32): one wide
-  // multiply-add forms each address
+  // element offsets fit in 32 bits (the host guarantees K q cells < 2^32)
   const unsigned int plane = (unsigned int)p.ncell;
   const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
+  // staged layout: pairs [KP q][COLS] of V, then the odd component [q][COLS] of S
   extern __shared__ __align__(16) unsigned char lbx_smem[];
-  S* col = reinterpret_cast<S*>(lbx_smem) + threadIdx.x;
-  constexpr int cs = COLS;
+  V* colv = reinterpret_cast<V*>(lbx_smem) + threadIdx.x;
+  S* colo = reinterpret_cast<S*>(reinterpret_cast<V*>(lbx_smem) + KP * Q * COLS) + threadIdx.x;
 
-  // a1: pull every population of the node (register file or private smem column)
+  // a1: pull every population of the node, two components per access
   T fv[MODE == MODE_REG ? K : 1][MODE == MODE_REG ? Q : 1];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const unsigned int src = pi.src<Lat>(i, p.nx, p.ny) + (unsigned int)i * plane;
+    const unsigned int src = pi.src<Lat>(i, p.nx, p.ny);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const unsigned int off = src + (unsigned int)(k * Q) * plane;
-      if constexpr (MODE == MODE_REG) fv[k][i] = to_c(__ldg(A + off));
-      else stage(col + (k * Q + i) * cs, A + off);
+    for (int kp = 0; kp < KP; ++kp) {
+      const V* g = reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, plane));
+      if constexpr (MODE == MODE_REG) split(ldg_pair(g), fv[2 * kp][i], fv[2 * kp + 1][i]);
+      else stage_pair(colv + (kp * Q + i) * COLS, g);
+    }
+    if constexpr (ODD) {
+      const S* g = A + eidx<K, Q>(K - 1, i, src, plane);
+      if constexpr (MODE == MODE_REG) fv[K - 1][i] = to_c(__ldg(g));
+      else stage(colo + i * COLS, g);
     }
   }
   if constexpr (MODE == MODE_SMEM) stage_wait();
-  auto f_at = [&](int k, int i) -> T {
-    if constexpr (MODE == MODE_REG) return fv[k][i];
-    else return lds_c(col + (k * Q + i) * cs);
+  auto get_pair = [&](int kp, int i, T& a, T& b) {
+    if constexpr (MODE == MODE_REG) {
+      a = fv[2 * kp][i];
+      b = fv[2 * kp + 1][i];
+    } else {
+      lds_pair(colv + (kp * Q + i) * COLS, a, b);
+    }
+  };
+  auto get_odd = [&](int i) -> T {
+    if constexpr (MODE == MODE_REG) return fv[K - 1][i];
+    else return lds_c(colo + i * COLS);
   };
 
   // a2: moments (Eq. moments), in stored units
   T X[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    T sum = T(0);
+  for (int k = 0; k < K; ++k) X[k] = T(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) sum += f_at(k, i);
-    X[k] = sum;
+  for (int kp = 0; kp < KP; ++kp)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      T a, b;
+      get_pair(kp, i, a, b);
+      X[2 * kp] += a;
+      X[2 * kp + 1] += b;
+    }
+  if constexpr (ODD) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) X[K - 1] += get_odd(i);
   }
 
   // a3: primitives, flux and source at the node (physical units)
@@ -249,33 +324,36 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
   if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y, step);
 
   // a4 + a5 + a6: equilibrium (Eq. feq), BGK with source (Eq. lbe_update), store
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const T om = p.omega[k];
+  auto out_of = [&](int k, int i, T f) -> T {
     const T inv_s = St::SCALE ? p.inv_scale[k] : T(1);
-    T ph[D];
+    const int sg = Lat::c(i, 0) != 0 ? Lat::c(i, 0) : (Lat::c(i, 1) != 0 ? Lat::c(i, 1) : Lat::c(i, 2));
+    T P = T(0);
 #pragma unroll
-    for (int d = 0; d < D; ++d) ph[d] = (p.lc * Phi[k][d] + (St::SHIFT ? T(0) : p.F0l[k][d])) * inv_s;
+    for (int d = 0; d < D; ++d) {
+      const int cd = Lat::c(i, d) * sg;
+      const T phd = (p.lc * Phi[k][d] + (St::SHIFT ? T(0) : p.F0l[k][d])) * inv_s;
+      if (cd == 1) P += phd;
+      if (cd == -1) P -= phd;
+    }
     const T Xs = X[k] + p.tau[k] * (p.dt * Src[k] * inv_s);
+    const T wi = T(Lat::w(i));
+    const T Fi = fma(T(sg) * wi, P, wi * Xs);
+    return fma(p.omega[k], Fi - f, f);
+  };
+#pragma unroll
+  for (int kp = 0; kp < KP; ++kp)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int sg = Lat::c(i, 0) != 0 ? Lat::c(i, 0) : (Lat::c(i, 1) != 0 ? Lat::c(i, 1) : Lat::c(i, 2));
-      T P = T(0);
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const int cd = Lat::c(i, d) * sg;
-        if (cd == 1) P += ph[d];
-        if (cd == -1) P -= ph[d];
-      }
-      const T wi = T(Lat::w(i));
-      const T Fi = fma(T(sg) * wi, P, wi * Xs);
-      const T f = f_at(k, i);
-      st_out(B + ((unsigned int)(k * Q + i) * plane + cell), fma(om, Fi - f, f));
+      T a, b;
+      get_pair(kp, i, a, b);
+      st_pair(reinterpret_cast<V*>(B + eidx<K, Q>(2 * kp, i, cell, plane)), out_of(2 * kp, i, a), out_of(2 * kp + 1, i, b));
     }
+  if constexpr (ODD) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_out(B + eidx<K, Q>(K - 1, i, cell, plane), out_of(K - 1, i, get_odd(i)));
   }
 }
 
-// One grid, one thread per node, blocks of 128 along x.
 // Register budget per thread follows the residency the populations' staging allows.
 // Blocks of COLS threads along x (COLS = 128 for register-resident kernels).
 template <class Lat, template <typename> class SysT, class St, int MODE, int COLS>
@@ -348,7 +426,7 @@ __global__ void k_init(const double* __restrict__ Qf, typename St::S* __restrict
       if (write) {
         const size_t dst = ((size_t)dzs[Lat::c(i, 2) + 1] * p.ny + dys[Lat::c(i, 1) + 1]) * p.nx +
                            dxs[Lat::c(i, 0) + 1];
-        typename St::S* o = A + ((size_t)k * Q + i) * plane + dst;
+        typename St::S* o = A + eidx<K, Q>(k, i, (unsigned int)dst, (unsigned int)plane);
         if (St::SCALE) v *= p.inv_scale[k];
         store_f64(o, v);
       }
@@ -373,7 +451,7 @@ __global__ void k_gather(const typename St::S* __restrict__ A, const KParams<dou
   for (int k = 0; k < K; ++k) {
     double s = 0.0;
     for (int i = 0; i < Q; ++i) {
-      double v = (double)ld_nc(A + ((size_t)k * Q + i) * plane + pi.src<Lat>(i, p.nx, p.ny));
+      double v = (double)ld_nc(A + eidx<K, Q>(k, i, pi.src<Lat>(i, p.nx, p.ny), (unsigned int)plane));
       if (St::SCALE) v *= p.scale[k];
       s += v;
       if (fout) fout[((size_t)k * Q + i) * plane + cell] = v + (St::SHIFT ? feq0[k * Q + i] : 0.0);
@@ -398,7 +476,7 @@ __global__ void k_scatter(const double* __restrict__ fin, typename St::S* __rest
     for (int i = 0; i < Q; ++i) {
       double v = fin[((size_t)k * Q + i) * plane + cell] - (St::SHIFT ? feq0[k * Q + i] : 0.0);
       if (St::SCALE) v *= p.inv_scale[k];
-      typename St::S* o = A + ((size_t)k * Q + i) * plane + pi.src<Lat>(i, p.nx, p.ny);
+      typename St::S* o = A + eidx<K, Q>(k, i, pi.src<Lat>(i, p.nx, p.ny), (unsigned int)plane);
       store_f64(o, v);
     }
 }
@@ -441,7 +519,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename St::S* __
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
       for (int i = 0; i < Q; ++i) {
-        double v = (double)ld_nc(A + ((size_t)k * Q + i) * plane + pi.src<Lat>(i, p.nx, p.ny));
+        double v = (double)ld_nc(A + eidx<K, Q>(k, i, pi.src<Lat>(i, p.nx, p.ny), (unsigned int)plane));
         if (St::SCALE) v *= p.scale[k];
         s += v;
       }
