@@ -159,7 +159,7 @@ size_t lbx_state_buffer_bytes(const lbx_scheme* sch);
  * a NaN/Inf.  With graph replay enabled, the n launches are recorded into a CUDA graph
  * the first time this (n, buffer parity) occurs and replayed afterwards. */
 lbx_status lbx_step(lbx_state* st, int64_t n);
-/* Threads per block (32, 64 or 128; default 32) of the step kernels that stage a node's
+/* Threads per block (32, 64 or 128; default 128) of the step kernels that stage a node's
  * populations in shared memory (K q s > 360 bytes: MHD on D3Q19, FP64 NSF); the other
  * kernels always use 128.  Only speed changes, never results. */
 lbx_status lbx_state_set_block(lbx_state* st, int block);

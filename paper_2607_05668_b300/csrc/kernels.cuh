@@ -152,7 +152,7 @@ struct StepMode {
   // for staged kernels what shared memory lets reside (228 KB per SM), at most 3
   static constexpr int smem_blocks = value == MODE_SMEM ? (int)(228 * 1024 / smem_bytes) : 0;
   static constexpr int min_blocks =
-      value == MODE_REG ? (sizeof(typename St::S) >= 4 ? 4 : 3)
+      value == MODE_REG ? 4
                         : (smem_blocks < 1 ? 1 : (smem_blocks * COLS > 384 ? 384 / COLS : smem_blocks));
 };
 

@@ -74,7 +74,7 @@ struct lbx_state {
   lbx::KParams<double> pd;
   lbx::KParams<float> pf;
   bool use_graph = false;       // lbx_step replays captured graphs
-  int block = 32;               // threads per block of staged (shared-memory) step kernels
+  int block = 128;              // threads per block of staged (shared-memory) step kernels
   std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
 
   void* cur() const { return cur_a ? fa : fb; }
