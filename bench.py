@@ -53,16 +53,28 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def profile_traffic(workload_key):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
-    when the summary is missing or was taken on other kernel sources."""
+def profile_entry(key):
+    """Entry of the committed ncu summary (profiles/ncu_traffic.json), or None when it is
+    missing or was taken on other kernel sources."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(workload_key)
+    d = json.load(open(p)).get(key)
     if not d or d.get("source_sha") != kernel_source_sha():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d
+
+
+def profile_traffic(workload_key, cells=None):
+    """DRAM bytes per launch of the step kernel (scaled by node count when the capture ran
+    on a smaller grid of the same kernel), or None."""
+    d = profile_entry(workload_key)
+    if not d:
+        return None
+    b = d.get("dram_bytes_per_launch")
+    if b is not None and cells and d.get("cells") and d["cells"] != cells:
+        b = b * cells / d["cells"]
+    return b
 
 
 class ClockSampler:
@@ -258,7 +270,7 @@ def measure_adjoint(L, W, n=256, steps=2000, ckpt=64):
             "note": "wall time of lbx_adjoint incl. allocation, host copies and the FP64 reductions"}
 
 
-def run_variants(L, W, args, stream, peak):
+def run_variants(L, W, args, stream, peak, probe_fp64=None):
     v = {}
     t0 = time.perf_counter()
     for wl, prec, n, steps in (("nsf", "fp64", 1024, 100), ("nsf", "fp16", 1024, 1000),
@@ -268,6 +280,15 @@ def run_variants(L, W, args, stream, peak):
         r, st = measure_grid(L, W, wl, prec, n, steps, 5 if wl != "adr" else 500, stream, graph=(wl == "adr"))
         st.close()
         r["frac_of_hbm_peak"] = r["gbs"] / peak
+        ncell = n ** (3 if wl == "mhd" else 2)
+        r["traffic_per_launch"] = profile_traffic(f"{wl}_{prec}", ncell)
+        if prec == "fp64":
+            fl = profile_entry(f"{wl}_fp64_flops")
+            if fl:
+                ach = fl["fp64_flops_per_node"] * r["lup_s"] / 1e9
+                r["alu_roofline"] = {"bound": "alu", "achieved": ach, "unit": "GFLOP/s",
+                                     "fp64_flops_per_node": fl["fp64_flops_per_node"],
+                                     "peak_probe": probe_fp64, "frac": ach / probe_fp64 if probe_fp64 else None}
         v[f"{wl}_{prec}_{n}"] = r
         torch.cuda.empty_cache()
     r = measure_batch(L, W, 200, 5, stream)
@@ -326,8 +347,7 @@ def run_ours(args):
     bytes_launch = 2 * K * q * STORE_BYTES[args.precision] * ncell
     peak, peak_kind = measured_peaks()
     achieved = bytes_launch / (ms_step * 1e-3) / 1e9
-    key = f"{args.workload}_{args.precision}_{case.n}"
-    traffic = profile_traffic(key)
+    traffic = profile_traffic(f"{args.workload}_{args.precision}", ncell)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch}
     if args.precision == "fp64":
@@ -367,7 +387,7 @@ def run_ours(args):
     if args.precision == "fp64" or args.probe or not args.no_variants:
         result["probe"] = L.probe_peaks(2 << 30, stream=stream)
     if not args.no_variants and args.workload == "nsf" and args.precision == "fp32":
-        result["variants"] = run_variants(L, W, args, stream, peak)
+        result["variants"] = run_variants(L, W, args, stream, peak, result["probe"]["fp64_gflops"])
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args, case)
     if rank == 0:

@@ -244,55 +244,18 @@ __device__ __forceinline__ double to_c(double v) { return v; }
 // and the weight class shares w_i (X_k + tau_k dt S_k), so each population costs one
 // add (moment) and three fused operations.  FP16 storage works in stored units (values
 // divided by s_k): X, phi and dt S are divided by s_k once per component.
-template <class Lat, template <typename> class SysT, class St, int MODE, int COLS = 128>
-__device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
-                                          const KParams<typename St::C>& p, int x, int y, int z,
-                                          long long step) {
+// Moments, flux and source, equilibrium, BGK and store for one node whose populations
+// are available through get_pair(kp, i, a, b) / get_odd(i) (registers or a staged column).
+template <class Lat, template <typename> class SysT, class St, class GetPair, class GetOdd>
+__device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, const KParams<typename St::C>& p,
+                                            int x, int y, unsigned int cell, long long step, bool active,
+                                            GetPair get_pair, GetOdd get_odd) {
   using T = typename St::C;
-  using S = typename St::S;
-  using V = typename PairOf<S>::V;
+  using V = typename PairOf<typename St::S>::V;
   using Sys = SysT<T>;
   constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D, KP = K / 2;
   constexpr bool ODD = (K & 1) != 0;
-  const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
-  // element offsets fit in 32 bits (the host guarantees K q cells < 2^32)
   const unsigned int plane = (unsigned int)p.ncell;
-  const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
-  // staged layout: pairs [KP q][COLS] of V, then the odd component [q][COLS] of S
-  extern __shared__ __align__(16) unsigned char lbx_smem[];
-  V* colv = reinterpret_cast<V*>(lbx_smem) + threadIdx.x;
-  S* colo = reinterpret_cast<S*>(reinterpret_cast<V*>(lbx_smem) + KP * Q * COLS) + threadIdx.x;
-
-  // a1: pull every population of the node, two components per access
-  T fv[MODE == MODE_REG ? K : 1][MODE == MODE_REG ? Q : 1];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const unsigned int src = pi.src<Lat>(i, p.nx, p.ny);
-#pragma unroll
-    for (int kp = 0; kp < KP; ++kp) {
-      const V* g = reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, plane));
-      if constexpr (MODE == MODE_REG) split(ldg_pair(g), fv[2 * kp][i], fv[2 * kp + 1][i]);
-      else stage_pair(colv + (kp * Q + i) * COLS, g);
-    }
-    if constexpr (ODD) {
-      const S* g = A + eidx<K, Q>(K - 1, i, src, plane);
-      if constexpr (MODE == MODE_REG) fv[K - 1][i] = to_c(__ldg(g));
-      else stage(colo + i * COLS, g);
-    }
-  }
-  if constexpr (MODE == MODE_SMEM) stage_wait();
-  auto get_pair = [&](int kp, int i, T& a, T& b) {
-    if constexpr (MODE == MODE_REG) {
-      a = fv[2 * kp][i];
-      b = fv[2 * kp + 1][i];
-    } else {
-      lds_pair(colv + (kp * Q + i) * COLS, a, b);
-    }
-  };
-  auto get_odd = [&](int i) -> T {
-    if constexpr (MODE == MODE_REG) return fv[K - 1][i];
-    else return lds_c(colo + i * COLS);
-  };
 
   // a2: moments (Eq. moments), in stored units
   T X[K];
@@ -346,11 +309,80 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
     for (int i = 0; i < Q; ++i) {
       T a, b;
       get_pair(kp, i, a, b);
-      st_pair(reinterpret_cast<V*>(B + eidx<K, Q>(2 * kp, i, cell, plane)), out_of(2 * kp, i, a), out_of(2 * kp + 1, i, b));
+      const T oa = out_of(2 * kp, i, a), ob = out_of(2 * kp + 1, i, b);
+      if (active) st_pair(reinterpret_cast<V*>(B + eidx<K, Q>(2 * kp, i, cell, plane)), oa, ob);
     }
   if constexpr (ODD) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st_out(B + eidx<K, Q>(K - 1, i, cell, plane), out_of(K - 1, i, get_odd(i)));
+    for (int i = 0; i < Q; ++i) {
+      const T o = out_of(K - 1, i, get_odd(i));
+      if (active) st_out(B + eidx<K, Q>(K - 1, i, cell, plane), o);
+    }
+  }
+}
+
+// Issue the copies of one node's pulled populations into a staged column: pairs
+// [KP q][COLS] of V, then the odd component [q][COLS] of S.
+template <class Lat, template <typename> class SysT, class St, int COLS>
+__device__ __forceinline__ void stage_node(const typename St::S* __restrict__ A,
+                                           typename PairOf<typename St::S>::V* colv, typename St::S* colo,
+                                           const PullIdx& pi, const KParams<typename St::C>& p) {
+  using S = typename St::S;
+  using V = typename PairOf<S>::V;
+  constexpr int K = SysT<typename St::C>::K, Q = Lat::Q, KP = K / 2;
+  const unsigned int plane = (unsigned int)p.ncell;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const unsigned int src = pi.src<Lat>(i, p.nx, p.ny);
+#pragma unroll
+    for (int kp = 0; kp < KP; ++kp)
+      stage_pair(colv + (kp * Q + i) * COLS, reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, plane)));
+    if constexpr ((K & 1) != 0) stage(colo + i * COLS, A + eidx<K, Q>(K - 1, i, src, plane));
+  }
+}
+
+template <class Lat, template <typename> class SysT, class St, int MODE, int COLS = 128>
+__device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
+                                          const KParams<typename St::C>& p, int x, int y, int z,
+                                          long long step) {
+  using T = typename St::C;
+  using S = typename St::S;
+  using V = typename PairOf<S>::V;
+  constexpr int K = SysT<T>::K, Q = Lat::Q, KP = K / 2;
+  constexpr bool ODD = (K & 1) != 0;
+  const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
+  // element offsets fit in 32 bits (the host guarantees K q cells < 2^32)
+  const unsigned int plane = (unsigned int)p.ncell;
+  const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
+  if constexpr (MODE == MODE_REG) {
+    // a1: pull every population of the node into registers, two components per access
+    T fv[K][Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const unsigned int src = pi.src<Lat>(i, p.nx, p.ny);
+#pragma unroll
+      for (int kp = 0; kp < KP; ++kp)
+        split(ldg_pair(reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, plane))), fv[2 * kp][i],
+              fv[2 * kp + 1][i]);
+      if constexpr (ODD) fv[K - 1][i] = to_c(__ldg(A + eidx<K, Q>(K - 1, i, src, plane)));
+    }
+    finish_node<Lat, SysT, St>(
+        B, p, x, y, cell, step, true,
+        [&](int kp, int i, T& a, T& b) {
+          a = fv[2 * kp][i];
+          b = fv[2 * kp + 1][i];
+        },
+        [&](int i) -> T { return fv[ODD ? K - 1 : 0][i]; });
+  } else {
+    // a1: stage every population of the node in this thread's shared-memory column
+    extern __shared__ __align__(16) unsigned char lbx_smem[];
+    V* colv = reinterpret_cast<V*>(lbx_smem) + threadIdx.x;
+    S* colo = reinterpret_cast<S*>(reinterpret_cast<V*>(lbx_smem) + KP * Q * COLS) + threadIdx.x;
+    stage_node<Lat, SysT, St, COLS>(A, colv, colo, pi, p);
+    stage_wait();
+    finish_node<Lat, SysT, St>(
+        B, p, x, y, cell, step, true, [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); },
+        [&](int i) -> T { return lds_c(colo + i * COLS); });
   }
 }
 

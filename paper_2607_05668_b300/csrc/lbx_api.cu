@@ -4,6 +4,7 @@
 // lbx_last_error(); none aborts.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

@@ -366,3 +366,23 @@ def test_fp16_halo_matches_register_kernel_statistics():
     Qo = och.moments(och.run(och.init(syn.mhd_fields(case)), 10))
     e = H.fluct_rel_l2(st.moments(), Qo, case.reference_state())
     assert e.max() <= 3e-2, e
+
+
+@pytest.mark.parametrize("name,prec", [("mhd", lbx.FP32_SHIFT), ("mhd", lbx.FP16_SCALED), ("nsf", lbx.FP64)])
+def test_staged_launch_shapes_are_bitwise_identical(name, prec):
+    """Staged step kernels (shared-memory columns) give identical results for blocks of 32,
+    64 and 128 threads."""
+    if name == "mhd":
+        case = syn.MhdCase(n=20)
+        Q, make = syn.mhd_fields(case), lambda: W.mhd_scheme(case, prec)
+    else:
+        case = syn.NsfCase(n=72)
+        Q, make = syn.nsf_fields(case), lambda: W.nsf_scheme(case, prec)
+    outs = []
+    for blk in (32, 64, 128):
+        st = lbx.State(make(), Q)
+        st.set_block(blk)
+        st.step(5)
+        outs.append(st.moments())
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
