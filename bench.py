@@ -77,6 +77,12 @@ def profile_traffic(workload_key, cells=None):
     return b
 
 
+def profile_kernel(workload_key):
+    """Kernel and block of the committed capture (the launch shape the tuner kept there)."""
+    d = profile_entry(workload_key)
+    return {"kernel": d.get("kernel_fn"), "block": d.get("block"), "cells": d.get("cells")} if d else None
+
+
 class ClockSampler:
     """nvidia-smi samples every 200 ms while the timed region runs."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -186,12 +192,22 @@ def _timed_steps(obj, stream, steps):
     return e0.elapsed_time(e1) / steps
 
 
+def launch_desc(L, rep):
+    """The step kernel lbx_state_tune kept: staging and block (register-resident: none)."""
+    if rep["ms_per_step"] < 0:
+        return {"kernel": "k_step (register-resident)", "block": 128}
+    name = {L.STAGE_THREAD: "k_step (per-thread copies)", L.STAGE_BULK: "k_step_bulk (bulk row copies)"}
+    return {"kernel": name.get(rep["staging"], str(rep["staging"])), "block": rep["block"],
+            "tuned_ms_per_step": rep["ms_per_step"]}
+
+
 def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=False):
     """Time one grid workload; returns a dict of rate, ms per step and GB/s."""
     case = make_case(workload, n)
     K, q = kq(workload)
     ncell = cells(workload, case)
     st = L.State(scheme(W, L, workload, case, precision), fields(workload, case).cuda(), stream=stream)
+    launch = st.tune()
     if graph:
         st.use_graph(True)
     st.step(warmup)
@@ -199,7 +215,8 @@ def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=Fals
     ms = _timed_steps(st, stream, steps)
     nbytes = 2 * K * q * STORE_BYTES[precision] * ncell
     out = {"lup_s": ncell / (ms * 1e-3), "ms_per_step": ms, "gbs": nbytes / (ms * 1e-3) / 1e9,
-           "bytes_per_launch": nbytes, "finite": st.check_finite(), "graph": graph}
+           "bytes_per_launch": nbytes, "finite": st.check_finite(), "graph": graph,
+           "launch": launch_desc(L, launch)}
     return out, st
 
 
@@ -282,6 +299,7 @@ def run_variants(L, W, args, stream, peak, probe_fp64=None):
         r["frac_of_hbm_peak"] = r["gbs"] / peak
         ncell = n ** (3 if wl == "mhd" else 2)
         r["traffic_per_launch"] = profile_traffic(f"{wl}_{prec}", ncell)
+        r["traffic_kernel"] = profile_kernel(f"{wl}_{prec}")
         if prec == "fp64":
             fl = profile_entry(f"{wl}_fp64_flops")
             if fl:
@@ -316,6 +334,7 @@ def run_ours(args):
     sch = scheme(W, L, args.workload, case, args.precision)
     stream = torch.cuda.Stream()
     st = L.State(sch, Q.cuda(), stream=stream)
+    launch = launch_desc(L, st.tune())      # staged kernels: fastest launch shape, state unchanged
     st.step(args.warmup)
     st.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -349,7 +368,8 @@ def run_ours(args):
     achieved = bytes_launch / (ms_step * 1e-3) / 1e9
     traffic = profile_traffic(f"{args.workload}_{args.precision}", ncell)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch}
+            "traffic": traffic, "traffic_kernel": profile_kernel(f"{args.workload}_{args.precision}"),
+            "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch}
     if args.precision == "fp64":
         roof["note"] = "FP64 arithmetic on B300 is far below the HBM ridge; see fp64_alu"
 
@@ -360,6 +380,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st2 = L.State(sch, Qh, stream=stream)
+    if launch.get("tuned_ms_per_step") is not None:
+        st2.set_staging(L.STAGE_BULK if launch["kernel"].startswith("k_step_bulk") else L.STAGE_THREAD)
+        st2.set_block(launch["block"])
     st2.step(args.steps)
     Qd = st2.moments(device=True)
     out_h.copy_(Qd, non_blocking=True)
@@ -381,7 +404,7 @@ def run_ours(args):
                    "grid": [case.n] * (3 if args.workload == "mhd" else 2), "components": K, "velocities": q,
                    "precision": args.precision, "l2": "inputs larger than L2 (each population buffer "
                    f"{bytes_launch / 2 / 1e6:.0f} MB > 126 MB)", "parallelism": f"replicas x{ws}"},
-        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "finite": finite,
+        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "finite": finite, "launch": launch,
         "clocks": clk.summary(),
     }
     if args.precision == "fp64" or args.probe or not args.no_variants:

@@ -163,6 +163,31 @@ lbx_status lbx_step(lbx_state* st, int64_t n);
  * populations in shared memory (K q s > 360 bytes: MHD on D3Q19, FP64 NSF); the other
  * kernels always use 128.  Only speed changes, never results. */
 lbx_status lbx_state_set_block(lbx_state* st, int block);
+/* How the staged step kernels (K q s > 360 bytes) bring a node's pulled populations into
+ * shared memory; only speed changes, except LBX_STAGE_LANES2, whose moment sums add in
+ * another order (results change by rounding only).
+ *   LBX_STAGE_AUTO     bulk row copies when they apply, else per-thread copies (default)
+ *   LBX_STAGE_THREAD   each thread copies its node's K q values (cp.async)
+ *   LBX_STAGE_LANES2   two adjacent lanes share a node: one takes the rest population, and
+ *                      of every opposite velocity pair each takes one velocity; partial
+ *                      moments are combined by a warp shuffle
+ *   LBX_STAGE_BULK     warp 0 of a block issues one bulk copy (TMA engine) per population
+ *                      row segment the block pulls; needs nx % 8 == 0 and 16-byte aligned
+ *                      population buffers (LBX_ERR_UNSUPPORTED otherwise).  Its wait on the
+ *                      copies is bounded: a timeout sets a device error word that
+ *                      lbx_synchronize and lbx_check_finite report as LBX_ERR_TIMEOUT.
+ * The register-resident kernels ignore it.  LBX_ERR_ARG for unknown values. */
+typedef enum { LBX_STAGE_AUTO = 0, LBX_STAGE_THREAD = 1, LBX_STAGE_LANES2 = 2, LBX_STAGE_BULK = 3 } lbx_staging;
+lbx_status lbx_state_set_staging(lbx_state* st, int staging);
+/* Autotune the staged step kernel of this state: time per-thread copies and (where they
+ * apply) bulk row copies, each with blocks of 32, 64 and 128 threads, over `trials`
+ * launches (1..1000) after one warm-up launch, and keep the fastest.  Every timed launch
+ * reads the current populations and writes the other buffer, which the next step
+ * rewrites anyway, so neither the populations nor the time change; all candidates give
+ * bitwise identical results (two lanes per node is not a candidate).  Register-resident
+ * kernels have one launch shape: nothing is timed and *ms_per_step is -1.  Synchronous.
+ * Outputs (each may be NULL): the chosen staging and block, the best time per launch. */
+lbx_status lbx_state_tune(lbx_state* st, int trials, int* staging, int* block, double* ms_per_step);
 /* Enable (1) or disable (0) graph replay in lbx_step; needs a non-default stream. */
 lbx_status lbx_state_use_graph(lbx_state* st, int enable);
 

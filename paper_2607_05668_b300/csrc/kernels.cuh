@@ -45,6 +45,7 @@ struct KParams {
   T mms_c0, mms_cx, mms_cy;    // A(-1 + 8 pi^2 nu), 2 pi A a_x, 2 pi A a_y
   const long long* step_ptr;   // step index at the start of this launch sequence
   int step_rel;                // offset of this launch in the sequence
+  unsigned int* err;           // device error word: bit 0 = a bounded wait timed out
 };
 
 // Element index of population (k, i) at `cell` (see the storage layout above).
@@ -384,6 +385,362 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
         B, p, x, y, cell, step, true, [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); },
         [&](int i) -> T { return lds_c(colo + i * COLS); });
   }
+}
+
+// ------------------------------------------------------------ two lanes per node
+// Staged variant for large K q: the two adjacent lanes 2m, 2m + 1 of a warp share node m.
+// Lane h takes the rest population (h = 0 only) and, of every opposite pair (i, i + 1) of
+// the lattice (i odd, c_{i+1} = -c_i, first nonzero entry of c_i = +1), velocity i + h,
+// whose direction is (1 - 2h) c_i.  Pulling along -c_i mirrors the neighbour table, and
+// the population planes of velocity i + h sit h planes after those of i, so both lanes run
+// the same instruction stream.  Each lane sums its own populations and the pair adds the
+// partner's partial sums with one shuffle per component (a + b = b + a bitwise, so both
+// lanes hold identical moments); both evaluate the flux, each updates its own velocities.
+// Per lane this halves the staged column, the loads, the moment adds and the update, and
+// the same shared memory then keeps twice as many warps resident.
+template <class Lat>
+struct SplitLat {
+  static constexpr int NP = (Lat::Q - 1) / 2;    // opposite pairs
+  static constexpr int QH = NP + 1;              // velocity slots per lane (slot 0: rest)
+  static constexpr bool valid() {
+    if ((Lat::Q & 1) == 0) return false;
+    for (int d = 0; d < 3; ++d)
+      if (Lat::c(0, d) != 0) return false;
+    for (int pp = 0; pp < NP; ++pp) {
+      const int i = 2 * pp + 1;
+      int lead = 0;
+      for (int d = 0; d < 3; ++d) {
+        if (Lat::c(i + 1, d) != -Lat::c(i, d)) return false;
+        if (lead == 0) lead = Lat::c(i, d);
+      }
+      if (lead != 1) return false;
+    }
+    return true;
+  }
+};
+
+template <class Lat, template <typename> class SysT, class St, int COLS>
+struct SplitMode {
+  static constexpr size_t smem_per_thread =
+      (size_t)SysT<typename St::C>::K * SplitLat<Lat>::QH * sizeof(typename St::S);
+  static constexpr size_t smem_bytes = smem_per_thread * COLS;
+  // blocks that shared memory lets reside (228 KB per SM, 1 KB reserved per block),
+  // at most 512 threads per SM so that the flux keeps 128 registers
+  static constexpr int smem_blocks = (int)(228 * 1024 / (smem_bytes + 1024));
+  static constexpr int min_blocks =
+      smem_blocks < 1 ? 1 : (smem_blocks * COLS > 512 ? 512 / COLS : smem_blocks);
+};
+
+template <class Lat, template <typename> class SysT, class St, int COLS>
+__device__ __forceinline__ void step_node_split(const typename St::S* __restrict__ A,
+                                                typename St::S* __restrict__ B,
+                                                const KParams<typename St::C>& p, int x, int y, int z,
+                                                long long step, int h, bool active) {
+  using T = typename St::C;
+  using S = typename St::S;
+  using V = typename PairOf<S>::V;
+  using Sys = SysT<T>;
+  constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D, KP = K / 2;
+  constexpr int NP = SplitLat<Lat>::NP, QH = SplitLat<Lat>::QH;
+  constexpr bool ODD = (K & 1) != 0;
+  static_assert(SplitLat<Lat>::valid(), "lattice order must be rest, then (+c, -c) pairs");
+  const unsigned int plane = (unsigned int)p.ncell;
+  const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
+  // lane 1 pulls along -c_i: swap the +1 / -1 neighbours of every axis
+  PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
+  if (h) {
+    const int tx = pi.sx[0], ty = pi.sy[0], tz = pi.sz[0];
+    pi.sx[0] = pi.sx[2]; pi.sx[2] = tx;
+    pi.sy[0] = pi.sy[2]; pi.sy[2] = ty;
+    pi.sz[0] = pi.sz[2]; pi.sz[2] = tz;
+  }
+  // planes of velocity i + h: pairs are interleaved (2 values per node), the odd component is not
+  const S* Ap = A + (size_t)h * 2 * plane;
+  const S* Ao = A + (size_t)h * plane;
+  S* Bp = B + (size_t)h * 2 * plane;
+  S* Bo = B + (size_t)h * plane;
+
+  // a1: stage this lane's populations: pairs [KP QH][COLS] of V, odd component [QH][COLS]
+  extern __shared__ __align__(16) unsigned char lbx_smem[];
+  V* colv = reinterpret_cast<V*>(lbx_smem) + threadIdx.x;
+  S* colo = reinterpret_cast<S*>(reinterpret_cast<V*>(lbx_smem) + KP * QH * COLS) + threadIdx.x;
+  if (h == 0) {
+#pragma unroll
+    for (int kp = 0; kp < KP; ++kp)
+      stage_pair(colv + kp * QH * COLS, reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, 0, cell, plane)));
+    if constexpr (ODD) stage(colo, A + eidx<K, Q>(K - 1, 0, cell, plane));
+  }
+#pragma unroll
+  for (int pp = 0; pp < NP; ++pp) {
+    const int i = 2 * pp + 1;
+    const unsigned int src = pi.src<Lat>(i, p.nx, p.ny);
+#pragma unroll
+    for (int kp = 0; kp < KP; ++kp)
+      stage_pair(colv + (kp * QH + pp + 1) * COLS, reinterpret_cast<const V*>(Ap + eidx<K, Q>(2 * kp, i, src, plane)));
+    if constexpr (ODD) stage(colo + (pp + 1) * COLS, Ao + eidx<K, Q>(K - 1, i, src, plane));
+  }
+  stage_wait();
+
+  // a2: moments (Eq. moments), in stored units: own populations, then the partner's sum
+  T X[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) X[k] = T(0);
+  if (h == 0) {
+#pragma unroll
+    for (int kp = 0; kp < KP; ++kp) lds_pair(colv + kp * QH * COLS, X[2 * kp], X[2 * kp + 1]);
+    if constexpr (ODD) X[K - 1] = lds_c(colo);
+  }
+#pragma unroll
+  for (int kp = 0; kp < KP; ++kp)
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+      T a, b;
+      lds_pair(colv + (kp * QH + pp + 1) * COLS, a, b);
+      X[2 * kp] += a;
+      X[2 * kp + 1] += b;
+    }
+  if constexpr (ODD) {
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) X[K - 1] += lds_c(colo + (pp + 1) * COLS);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) X[k] += __shfl_xor_sync(0xffffffffu, X[k], 1);
+
+  // a3: primitives, flux and source at the node (physical units)
+  T dQ[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const T xk = St::SCALE ? X[k] * p.scale[k] : X[k];
+    dQ[k] = St::SHIFT ? xk : xk - p.Q0[k];
+  }
+  T Phi[K][D], Src[K];
+  Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
+  if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y, step);
+
+  // a4 + a5 + a6: the arithmetic of finish_node with the sign of c' . phi set by the lane
+  const T sgn = h ? T(-1) : T(1);
+  auto out_of = [&](int k, int i, T f) -> T {
+    const T inv_s = St::SCALE ? p.inv_scale[k] : T(1);
+    const T Xs = X[k] + p.tau[k] * (p.dt * Src[k] * inv_s);
+    const T wi = T(Lat::w(i));
+    T F;
+    if (i == 0) {
+      F = wi * Xs;
+    } else {
+      T P = T(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int cd = Lat::c(i, d);
+        const T phd = (p.lc * Phi[k][d] + (St::SHIFT ? T(0) : p.F0l[k][d])) * inv_s;
+        if (cd == 1) P += phd;
+        if (cd == -1) P -= phd;
+      }
+      F = fma(sgn * wi, P, wi * Xs);
+    }
+    return fma(p.omega[k], F - f, f);
+  };
+  const bool rest = active && h == 0;
+#pragma unroll
+  for (int kp = 0; kp < KP; ++kp) {
+    {
+      T a, b;
+      lds_pair(colv + kp * QH * COLS, a, b);
+      const T oa = out_of(2 * kp, 0, a), ob = out_of(2 * kp + 1, 0, b);
+      if (rest) st_pair(reinterpret_cast<V*>(B + eidx<K, Q>(2 * kp, 0, cell, plane)), oa, ob);
+    }
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+      const int i = 2 * pp + 1;
+      T a, b;
+      lds_pair(colv + (kp * QH + pp + 1) * COLS, a, b);
+      const T oa = out_of(2 * kp, i, a), ob = out_of(2 * kp + 1, i, b);
+      if (active) st_pair(reinterpret_cast<V*>(Bp + eidx<K, Q>(2 * kp, i, cell, plane)), oa, ob);
+    }
+  }
+  if constexpr (ODD) {
+    {
+      const T o = out_of(K - 1, 0, lds_c(colo));
+      if (rest) st_out(B + eidx<K, Q>(K - 1, 0, cell, plane), o);
+    }
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+      const int i = 2 * pp + 1;
+      const T o = out_of(K - 1, i, lds_c(colo + (pp + 1) * COLS));
+      if (active) st_out(Bo + eidx<K, Q>(K - 1, i, cell, plane), o);
+    }
+  }
+}
+
+// Blocks of COLS lanes cover COLS / 2 nodes along x.  Lanes past the row end compute on a
+// clamped node and store nothing, so every lane takes part in the shuffles.
+template <class Lat, template <typename> class SysT, class St, int COLS>
+__global__ void __launch_bounds__(COLS, SplitMode<Lat, SysT, St, COLS>::min_blocks)
+    k_step_split(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
+                 const KParams<typename St::C> p) {
+  const int xr = blockIdx.x * (COLS / 2) + (int)(threadIdx.x >> 1);
+  const bool active = xr < p.nx;
+  const int x = active ? xr : p.nx - 1;
+  const long long step = p.mms_tab != nullptr ? *p.step_ptr + p.step_rel : 0;
+  step_node_split<Lat, SysT, St, COLS>(A, B, p, x, blockIdx.y, blockIdx.z, step, (int)(threadIdx.x & 1), active);
+}
+
+// ------------------------------------------------------------ bulk-copied rows (TMA)
+// Staged variant for large K q whose pulled populations reach shared memory by bulk
+// copies (cp.async.bulk, executed by the TMA engine) instead of per-thread copies.  A
+// block owns COLS consecutive nodes x0 .. x0 + COLS - 1 of one row; for velocity i and
+// every component the pull reads one contiguous run of the row at (y - c_iy, z - c_iz),
+// shifted by c_ix.  Lane i of warp 0 issues the runs of velocity i (one per component
+// pair, one for an odd component), each widened by E = 16 / element-bytes elements on the
+// side the shift reaches into so that it starts and ends on 16-byte boundaries, and
+// clamped to the row: the periodic wrap of the two edge nodes (x = 0 pulling along +x,
+// x = nx - 1 along -x) is filled by those threads with plain loads.  All copies complete
+// on one mbarrier; the wait is bounded and a timeout raises p.err and skips the node.
+// Needs nx % 8 == 0 and 16-byte aligned population buffers (the host checks both).
+template <class Lat, template <typename> class SysT, class St, int COLS>
+struct BulkMode {
+  using S = typename St::S;
+  using V = typename PairOf<S>::V;
+  static constexpr int K = SysT<typename St::C>::K, Q = Lat::Q, KP = K / 2;
+  static constexpr bool ODD = (K & 1) != 0;
+  static constexpr int EP = 16 / (int)sizeof(V), EO = 16 / (int)sizeof(S);
+  static constexpr int ROWP = COLS + EP, ROWO = COLS + EO;      // row pitch in elements
+  static constexpr size_t smem_bytes =
+      16 + (size_t)KP * Q * ROWP * sizeof(V) + (ODD ? (size_t)Q * ROWO * sizeof(S) : 0);
+  static constexpr int smem_blocks = (int)(228 * 1024 / (smem_bytes + 1024));
+  static constexpr int min_blocks =
+      smem_blocks < 1 ? 1 : (smem_blocks * COLS > 512 ? 512 / COLS : smem_blocks);
+  // offset of the pulled element of thread t in the row of velocity i (E: pad elements)
+  __host__ __device__ static constexpr int shift(int i, int E) {
+    return Lat::c(i, 0) == 1 ? E - 1 : (Lat::c(i, 0) == -1 ? 1 : 0);
+  }
+};
+
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned int bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned int bar, unsigned int bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned int bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+// Suspend until phase `parity` of the barrier completes: tries of at most about a
+// microsecond each, for no longer than `limit_ns` of the global timer and no more than
+// 2^22 tries; false on timeout.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned int bar, unsigned int parity, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned int done;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity), "r"(1000u)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > limit_ns) break;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned int dst, const void* src, unsigned int bytes, unsigned int bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+constexpr unsigned long long BULK_WAIT_NS = 1000000000ull;   // 1 s
+
+template <class Lat, template <typename> class SysT, class St, int COLS>
+__global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_blocks)
+    k_step_bulk(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
+                const KParams<typename St::C> p) {
+  using M = BulkMode<Lat, SysT, St, COLS>;
+  using T = typename St::C;
+  using S = typename St::S;
+  using V = typename M::V;
+  constexpr int K = M::K, Q = Lat::Q, KP = M::KP, EP = M::EP, EO = M::EO;
+  constexpr bool ODD = M::ODD;
+  static_assert(Q <= 32, "one issuing lane per velocity");
+  extern __shared__ __align__(16) unsigned char lbx_smem[];
+  V* rowv = reinterpret_cast<V*>(lbx_smem + 16);                 // [KP q][ROWP]
+  S* rowo = reinterpret_cast<S*>(rowv + (size_t)KP * Q * M::ROWP); // [q][ROWO]
+  const unsigned int bar = smem_u32(lbx_smem);
+  const int t = (int)threadIdx.x, x0 = (int)blockIdx.x * COLS, y = (int)blockIdx.y, z = (int)blockIdx.z;
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const unsigned int plane = (unsigned int)p.ncell;
+
+  if (t == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (t < 32) {
+    if (t < Q) {
+      int cx = 0, cy = 0, cz = 0;
+#pragma unroll
+      for (int j = 0; j < Q; ++j)
+        if (j == t) {
+          cx = Lat::c(j, 0);
+          cy = Lat::c(j, 1);
+          cz = Lat::c(j, 2);
+        }
+      const int ys = y - cy < 0 ? ny - 1 : (y - cy >= ny ? 0 : y - cy);
+      const int zs = z - cz < 0 ? nz - 1 : (z - cz >= nz ? 0 : z - cz);
+      const unsigned int cell0 = ((unsigned int)zs * (unsigned int)ny + (unsigned int)ys) * (unsigned int)nx;
+      const int xsp = x0 - (cx == 1 ? EP : 0), xep = x0 + COLS + (cx == -1 ? EP : 0);
+      const int lop = xsp < 0 ? 0 : xsp, hip = xep > nx ? nx : xep;
+      const unsigned int bp = (unsigned int)(hip - lop) * (unsigned int)sizeof(V);
+      const int xso = x0 - (cx == 1 ? EO : 0), xeo = x0 + COLS + (cx == -1 ? EO : 0);
+      const int loo = xso < 0 ? 0 : xso, hio = xeo > nx ? nx : xeo;
+      const unsigned int bo = ODD ? (unsigned int)(hio - loo) * (unsigned int)sizeof(S) : 0u;
+      mbar_expect_tx(bar, KP * bp + bo);
+      const V* Av = reinterpret_cast<const V*>(A);
+#pragma unroll
+      for (int kp = 0; kp < KP; ++kp)
+        bulk_g2s(smem_u32(rowv + (size_t)(kp * Q + t) * M::ROWP + (lop - xsp)),
+                 Av + (size_t)(kp * Q + t) * plane + cell0 + lop, bp, bar);
+      if constexpr (ODD)
+        bulk_g2s(smem_u32(rowo + (size_t)t * M::ROWO + (loo - xso)),
+                 A + (size_t)2 * KP * Q * plane + (size_t)t * plane + cell0 + loo, bo, bar);
+    }
+    __syncwarp();
+    if (t == 0) mbar_arrive(bar);
+  }
+  const int x = x0 + t;
+  if (x >= nx) return;
+
+  // periodic wrap at the row ends: the slot the clamped copy left empty
+  if (x == 0 || x == nx - 1) {
+    const PullIdx pi(x, y, z, nx, ny, nz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cx = Lat::c(i, 0);
+      if ((cx == 1 && x == 0) || (cx == -1 && x == nx - 1)) {
+        const unsigned int src = pi.src<Lat>(i, nx, ny);
+#pragma unroll
+        for (int kp = 0; kp < KP; ++kp)
+          rowv[(size_t)(kp * Q + i) * M::ROWP + t + M::shift(i, EP)] =
+              __ldg(reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, plane)));
+        if constexpr (ODD) rowo[(size_t)i * M::ROWO + t + M::shift(i, EO)] = A[eidx<K, Q>(K - 1, i, src, plane)];
+      }
+    }
+  }
+  if (!mbar_wait(bar, 0, BULK_WAIT_NS)) {
+    if (p.err) atomicOr(p.err, 1u);
+    mbar_wait(bar, 0, BULK_WAIT_NS);         // let copies in flight land before leaving
+    return;
+  }
+  const unsigned int cell = ((unsigned int)z * (unsigned int)ny + (unsigned int)y) * (unsigned int)nx + x;
+  const long long step = p.mms_tab != nullptr ? *p.step_ptr + p.step_rel : 0;
+  finish_node<Lat, SysT, St>(
+      B, p, x, y, cell, step, true,
+      [&](int kp, int i, T& a, T& b) { lds_pair(rowv + (size_t)(kp * Q + i) * M::ROWP + t + M::shift(i, EP), a, b); },
+      [&](int i) -> T { return lds_c(rowo + (size_t)(ODD ? i : 0) * M::ROWO + t + M::shift(i, EO)); });
 }
 
 // Register budget per thread follows the residency the populations' staging allows.

@@ -391,6 +391,7 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
   p.lc = (T)lc;
   p.dt = (T)s.dt;
   p.step_ptr = st->d_step;
+  p.err = st->d_err;
   if (s.d.mms == LBX_MMS_ADR_SEPARABLE) {
     const double A = s.d.mms_amp, nu = s.sys.params[2], tp = 2.0 * M_PI;
     p.mms_c0 = (T)(A * (-1.0 + 2.0 * tp * tp * nu));
@@ -401,6 +402,27 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
 }
 
 // ------------------------------------------------------------------------ dispatch
+// Bulk row copies need rows of whole 16-byte runs and 16-byte aligned population buffers.
+static bool bulk_eligible(const lbx_state* st) {
+  return st->sch.nx % 8 == 0 && ((uintptr_t)st->fa % 16) == 0 && ((uintptr_t)st->fb % 16) == 0;
+}
+// The staging a staged step kernel uses: LBX_STAGE_AUTO resolves to bulk row copies when
+// they apply and to per-thread copies otherwise.
+static int resolved_staging(const lbx_state* st) {
+  if (st->staging != LBX_STAGE_AUTO) return st->staging;
+  return bulk_eligible(st) ? LBX_STAGE_BULK : LBX_STAGE_THREAD;
+}
+// Device error word (bit 0: a bounded wait in a step kernel timed out), read after a
+// synchronisation; a raised word is reported once and cleared.
+static lbx_status check_err_word(lbx_state* st) {
+  unsigned int w = 0;
+  cudaError_t e = cudaMemcpy(&w, st->d_err, sizeof(w), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && w != 0) e = cudaMemset(st->d_err, 0, sizeof(w));
+  if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "reading the step kernels' error word: %s", cudaGetErrorString(e));
+  if (w == 0) return LBX_OK;
+  return fail(LBX_ERR_TIMEOUT, "step kernel: a bounded wait for bulk copies timed out (error word %u)", w);
+}
+
 template <class Lat, template <typename> class SysT, class St>
 struct OpsImpl {
   using C = typename St::C;
@@ -430,20 +452,59 @@ struct OpsImpl {
     return cudaGetLastError();
   }
 
+  template <int COLS>
+  static cudaError_t launch_split(const lbx_state* st, const void* A, void* B, const KParams<C>& p,
+                                  cudaStream_t strm) {
+    const size_t bytes = SplitMode<Lat, SysT, St, COLS>::smem_bytes;
+    static cudaError_t prep = prepare((const void*)k_step_split<Lat, SysT, St, COLS>, bytes);
+    if (prep != cudaSuccess) return prep;
+    const dim3 b(COLS, 1, 1), g((st->sch.nx + COLS / 2 - 1) / (COLS / 2), st->sch.ny, st->sch.nz);
+    k_step_split<Lat, SysT, St, COLS><<<g, b, bytes, strm>>>((const S*)A, (S*)B, p);
+    return cudaGetLastError();
+  }
+
+  template <int COLS>
+  static cudaError_t launch_bulk(const lbx_state* st, const void* A, void* B, const KParams<C>& p,
+                                 cudaStream_t strm) {
+    const size_t bytes = BulkMode<Lat, SysT, St, COLS>::smem_bytes;
+    static cudaError_t prep = prepare((const void*)k_step_bulk<Lat, SysT, St, COLS>, bytes);
+    if (prep != cudaSuccess) return prep;
+    const dim3 b(COLS, 1, 1), g((st->sch.nx + COLS - 1) / COLS, st->sch.ny, st->sch.nz);
+    k_step_bulk<Lat, SysT, St, COLS><<<g, b, bytes, strm>>>((const S*)A, (S*)B, p);
+    return cudaGetLastError();
+  }
+
   // Register-resident kernels use 128-thread blocks (narrower grids: the smallest multiple
-  // of 32 covering nx); staged kernels use st->block in {32, 64, 128}.
+  // of 32 covering nx); staged kernels use st->block in {32, 64, 128} and the staging
+  // st->staging resolves to.
   static cudaError_t step(const lbx_state* st, const void* A, void* B, int rel, cudaStream_t strm) {
     KParams<C> p = st->pc<C>();
     p.step_rel = rel;
-    if (MODE == MODE_REG) {
+    if constexpr (MODE == MODE_REG) {
       dim3 b = block(st->sch), g = grid(st->sch, b);
       k_step<Lat, SysT, St, MODE, 128><<<g, b, 0, strm>>>((const S*)A, (S*)B, p);
       return cudaGetLastError();
-    }
-    switch (st->block) {
-      case 32: return launch<32>(st, A, B, p, strm);
-      case 64: return launch<64>(st, A, B, p, strm);
-      default: return launch<128>(st, A, B, p, strm);
+    } else {
+      const int mode = resolved_staging(st);
+      if (mode == LBX_STAGE_BULK) {
+        switch (st->block) {
+          case 32: return launch_bulk<32>(st, A, B, p, strm);
+          case 64: return launch_bulk<64>(st, A, B, p, strm);
+          default: return launch_bulk<128>(st, A, B, p, strm);
+        }
+      }
+      if (mode == LBX_STAGE_LANES2) {
+        switch (st->block) {
+          case 32: return launch_split<32>(st, A, B, p, strm);
+          case 64: return launch_split<64>(st, A, B, p, strm);
+          default: return launch_split<128>(st, A, B, p, strm);
+        }
+      }
+      switch (st->block) {
+        case 32: return launch<32>(st, A, B, p, strm);
+        case 64: return launch<64>(st, A, B, p, strm);
+        default: return launch<128>(st, A, B, p, strm);
+      }
     }
   }
   static cudaError_t init(const lbx_state* st, const double* Q, void* A, unsigned long long* maxbits, int write) {
@@ -543,6 +604,7 @@ static void free_state(lbx_state* st) {
   if (st->own_a && st->fa) cudaFree(st->fa);
   if (st->own_b && st->fb) cudaFree(st->fb);
   cudaFree(st->d_step);
+  cudaFree(st->d_err);
   cudaFree(st->d_feq0);
   cudaFree(st->d_partials);
   cudaFree(st->d_red_out);
@@ -637,6 +699,8 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
   }
   CKI(cudaMalloc(&st->d_step, sizeof(long long)));
   CKI(cudaMemsetAsync(st->d_step, 0, sizeof(long long), st->stream));
+  CKI(cudaMalloc(&st->d_err, sizeof(unsigned int)));
+  CKI(cudaMemsetAsync(st->d_err, 0, sizeof(unsigned int), st->stream));
   CKI(cudaMalloc(&st->d_feq0, sizeof(double) * K * q));
   {
     std::vector<double> t(K * q);
@@ -747,6 +811,80 @@ extern "C" lbx_status lbx_state_set_block(lbx_state* st, int block) {
   return LBX_OK;
 }
 
+extern "C" lbx_status lbx_state_set_staging(lbx_state* st, int staging) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_state_set_staging: null state");
+  if (staging < LBX_STAGE_AUTO || staging > LBX_STAGE_BULK)
+    return fail(LBX_ERR_ARG, "lbx_state_set_staging: unknown staging %d", staging);
+  if (staging == LBX_STAGE_BULK && !bulk_eligible(st))
+    return fail(LBX_ERR_UNSUPPORTED,
+                "lbx_state_set_staging: bulk row copies need nx %% 8 == 0 and 16-byte aligned buffers");
+  if (staging != st->staging) {
+    for (auto& g : st->graphs) cudaGraphExecDestroy(g.second);
+    st->graphs.clear();
+  }
+  st->staging = staging;
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_state_tune(lbx_state* st, int trials, int* staging, int* block, double* ms_per_step) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_state_tune: null state");
+  if (trials < 1 || trials > 1000) return fail(LBX_ERR_ARG, "lbx_state_tune: trials must be in 1..1000");
+  if (st->nonfinite) return fail(LBX_ERR_NONFINITE, "lbx_state_tune: state holds non-finite values");
+  const int old_staging = st->staging, old_block = st->block;
+  int best_s = old_staging, best_b = old_block;
+  double best = -1.0;
+  if (!st->ops.reg) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaError_t e = cudaEventCreate(&e1)) {
+      cudaEventDestroy(e0);
+      return fail(LBX_ERR_CUDA, "lbx_state_tune: %s", cudaGetErrorString(e));
+    }
+    const int stagings[2] = {LBX_STAGE_THREAD, LBX_STAGE_BULK};
+    const int blocks[3] = {32, 64, 128};
+    cudaError_t err = cudaSuccess;
+    for (int sg : stagings) {
+      if (sg == LBX_STAGE_BULK && !bulk_eligible(st)) continue;
+      for (int b : blocks) {
+        st->staging = sg;
+        st->block = b;
+        // cur -> nxt only: the other buffer is rewritten by the next step anyway
+        err = st->ops.step(st, st->cur(), st->nxt(), 0, st->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, st->stream);
+        for (int r = 0; r < trials && err == cudaSuccess; ++r) err = st->ops.step(st, st->cur(), st->nxt(), 0, st->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, st->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) break;
+        const double per = ms / trials;
+        if (best < 0.0 || per < best) {
+          best = per;
+          best_s = sg;
+          best_b = b;
+        }
+      }
+      if (err != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st->staging = old_staging;
+    st->block = old_block;
+    if (err != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_state_tune: %s", cudaGetErrorString(err));
+    if (lbx_status s = check_err_word(st)) return s;
+    if (best_s != old_staging || best_b != old_block) {
+      for (auto& g : st->graphs) cudaGraphExecDestroy(g.second);
+      st->graphs.clear();
+    }
+    st->staging = best_s;
+    st->block = best_b;
+  }
+  if (staging) *staging = st->ops.reg ? LBX_STAGE_AUTO : st->staging;
+  if (block) *block = st->ops.reg ? 128 : st->block;
+  if (ms_per_step) *ms_per_step = best;
+  return LBX_OK;
+}
+
 extern "C" lbx_status lbx_state_use_graph(lbx_state* st, int enable) {
   if (!st) return fail(LBX_ERR_ARG, "lbx_state_use_graph: null state");
   if (enable && st->stream == nullptr)
@@ -830,6 +968,7 @@ extern "C" lbx_status lbx_check_finite(lbx_state* st, int* finite) {
   if (!st || !finite) return fail(LBX_ERR_ARG, "lbx_check_finite: null argument");
   double out[KMAX * 4];
   if (lbx_status s = run_reduce(st, nullptr, 0, out)) return s;
+  if (lbx_status s = check_err_word(st)) return s;
   int ok = 1;
   for (int k = 0; k < st->sch.sys.K; ++k)
     if (out[4 * k + 3] != 0.0) ok = 0;
@@ -904,7 +1043,7 @@ extern "C" lbx_status lbx_synchronize(lbx_state* st) {
   if (!st) return fail(LBX_ERR_ARG, "lbx_synchronize: null state");
   CK(cudaStreamSynchronize(st->stream));
   if (lbx_status s = sync_step_counter(st)) return s;
-  return LBX_OK;
+  return check_err_word(st);
 }
 
 extern "C" void lbx_state_destroy(lbx_state* st) {

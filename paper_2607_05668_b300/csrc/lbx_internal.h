@@ -75,6 +75,8 @@ struct lbx_state {
   lbx::KParams<float> pf;
   bool use_graph = false;       // lbx_step replays captured graphs
   int block = 128;              // threads per block of staged (shared-memory) step kernels
+  int staging = 0;              // lbx_staging of staged step kernels (0 = automatic)
+  unsigned int* d_err = nullptr; // device error word of the step kernels
   std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
 
   void* cur() const { return cur_a ? fa : fb; }

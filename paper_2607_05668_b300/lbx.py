@@ -22,6 +22,7 @@ D2Q5, D2Q9, D3Q7, D3Q19 = 1, 2, 3, 4
 ACOUSTIC, DIFFUSIVE = 1, 2
 FP64, FP32_SHIFT, FP16_SCALED = 1, 2, 3
 MMS_NONE, MMS_ADR_SEPARABLE = 0, 1
+STAGE_AUTO, STAGE_THREAD, STAGE_LANES2, STAGE_BULK = 0, 1, 2, 3
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_SUBCHAR", 5: "ERR_NONFINITE",
           6: "ERR_TIMEOUT", 7: "ERR_STATE", 8: "ERR_IO", 9: "ERR_UNSUPPORTED"}
@@ -72,6 +73,8 @@ _sig("lbx_state_buffer_bytes", C.c_size_t, [_P])
 _sig("lbx_step", C.c_int, [_P, C.c_int64])
 _sig("lbx_state_use_graph", C.c_int, [_P, C.c_int])
 _sig("lbx_state_set_block", C.c_int, [_P, C.c_int])
+_sig("lbx_state_set_staging", C.c_int, [_P, C.c_int])
+_sig("lbx_state_tune", C.c_int, [_P, C.c_int, _I, _I, _D])
 _sig("lbx_moments", C.c_int, [_P, _P, C.c_int])
 _sig("lbx_conserved_sums", C.c_int, [_P, _D])
 _sig("lbx_error_norms", C.c_int, [_P, _P, C.c_int, _D, _D])
@@ -223,6 +226,18 @@ class State:
     def set_block(self, block):
         """Threads per block of staged step kernels (32, 64 or 128); results do not change."""
         check(_lib.lbx_state_set_block(self._h, int(block)))
+
+    def set_staging(self, staging):
+        """Staging of the staged step kernels: STAGE_AUTO, STAGE_THREAD, STAGE_LANES2 or
+        STAGE_BULK (see lbx_state_set_staging)."""
+        check(_lib.lbx_state_set_staging(self._h, int(staging)))
+
+    def tune(self, trials=5):
+        """lbx_state_tune: pick the fastest staging and block without changing the state;
+        returns {"staging", "block", "ms_per_step"}."""
+        sg, blk, ms = C.c_int(), C.c_int(), C.c_double()
+        check(_lib.lbx_state_tune(self._h, int(trials), C.byref(sg), C.byref(blk), C.byref(ms)))
+        return {"staging": sg.value, "block": blk.value, "ms_per_step": ms.value}
 
     def use_graph(self, enable=True):
         """Replay lbx_step's launches from captured CUDA graphs (needs a non-default stream)."""

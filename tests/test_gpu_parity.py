@@ -386,3 +386,118 @@ def test_staged_launch_shapes_are_bitwise_identical(name, prec):
         outs.append(st.moments())
     for o in outs[1:]:
         assert torch.equal(o, outs[0])
+
+
+# ------------------------------------------- staging modes of the staged step kernels
+
+STAGINGS = {"thread": lbx.STAGE_THREAD, "lanes2": lbx.STAGE_LANES2, "bulk": lbx.STAGE_BULK}
+
+
+def _staged_state(name, prec, staging, n, lattice=None):
+    kw = {} if lattice is None else {"lattice": lattice}
+    if name == "mhd":
+        case = syn.MhdCase(n=n)
+        st = lbx.State(W.mhd_scheme(case, prec, **kw), syn.mhd_fields(case))
+    else:
+        case = syn.NsfCase(n=n)
+        st = lbx.State(W.nsf_scheme(case, prec, **kw), syn.nsf_fields(case))
+    st.set_staging(STAGINGS[staging])
+    return case, st
+
+
+def _oracle_moments(name, case, steps, lattice=None):
+    lat = {None: None, lbx.D3Q7: "D3Q7", lbx.D2Q5: "D2Q5"}[lattice]
+    kw = {} if lat is None else {"lattice": lat}
+    if name == "mhd":
+        och = H.oracle_mhd(case, **kw)
+        return och.moments(och.run(och.init(syn.mhd_fields(case)), steps))
+    och = H.oracle_nsf(case, **kw)
+    return och.moments(och.run(och.init(syn.nsf_fields(case)), steps))
+
+
+@pytest.mark.parametrize("staging", ["lanes2", "bulk"])
+@pytest.mark.parametrize("name,n,lattice", [("mhd", 24, None), ("mhd", 16, lbx.D3Q7),
+                                            ("nsf", 48, None), ("nsf", 136, None), ("nsf", 72, lbx.D2Q5)])
+def test_staged_modes_fp64_match_oracle(staging, name, n, lattice):
+    """FP64 through each staging.  Rows of 16, 24 and 48 nodes leave idle threads in the
+    last block; 136 spans two 128-node blocks and an 8-node tail, so the bulk copies are
+    clamped at both row ends and the wrap nodes patch their slots."""
+    case, st = _staged_state(name, lbx.FP64, staging, n, lattice)
+    st.step(9)
+    err = H.rel_linf_per_field(st.moments(), _oracle_moments(name, case, 9, lattice))
+    assert err.max() <= 1e-12, err
+
+
+@pytest.mark.parametrize("staging", ["lanes2", "bulk"])
+@pytest.mark.parametrize("prec,bound", [(lbx.FP32_SHIFT, 1e-4), (lbx.FP16_SCALED, 3e-2)])
+def test_staged_modes_mhd_32_reduced_precision_against_fp64_oracle(staging, prec, bound):
+    case, st = _staged_state("mhd", prec, staging, 32)
+    st.step(40)
+    e = H.fluct_rel_l2(st.moments(), _oracle_moments("mhd", case, 40), case.reference_state())
+    assert e.max() <= bound, e
+
+
+@pytest.mark.parametrize("name,prec", [("mhd", lbx.FP32_SHIFT), ("mhd", lbx.FP16_SCALED), ("nsf", lbx.FP64)])
+def test_staged_modes_launch_shapes_and_agreement(name, prec):
+    """Per staging, blocks of 32, 64 and 128 threads give identical results; bulk row copies
+    equal per-thread copies bitwise (same arithmetic, same order); two lanes per node add
+    the moments in another order and agree to rounding."""
+    n = 24 if name == "mhd" else 136
+    res = {}
+    for staging in ("thread", "lanes2", "bulk"):
+        outs = []
+        for blk in (32, 64, 128):
+            case, st = _staged_state(name, prec, staging, n)
+            st.set_block(blk)
+            st.step(5)
+            outs.append(st.moments())
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0]), staging
+        res[staging] = outs[0]
+    assert torch.equal(res["bulk"], res["thread"])
+    one, two = res["thread"], res["lanes2"]
+    if prec == lbx.FP64:
+        # rounding-order differences, relative to the small tracker gradients
+        assert H.rel_linf_per_field(two, one).max() <= 1e-13
+    else:
+        q0 = torch.tensor(case.reference_state(), dtype=F64).reshape(-1, *([1] * (one.dim() - 1)))
+        d = (two - one).reshape(one.shape[0], -1).norm(dim=1)
+        r = (one - q0).reshape(one.shape[0], -1).norm(dim=1)
+        assert (d / r).max() <= (1e-5 if prec == lbx.FP32_SHIFT else 1e-2)
+
+
+def test_set_staging_rejects_unknown_and_inapplicable_modes():
+    case, st = _staged_state("mhd", lbx.FP32_SHIFT, "thread", 8)
+    for bad in (-1, 4):
+        with pytest.raises(lbx.LbxError):
+            st.set_staging(bad)
+    case = syn.MhdCase(n=12)                      # 12 % 8 != 0: no bulk row copies
+    st = lbx.State(W.mhd_scheme(case, lbx.FP32_SHIFT), syn.mhd_fields(case))
+    with pytest.raises(lbx.LbxError, match="ERR_UNSUPPORTED"):
+        st.set_staging(lbx.STAGE_BULK)
+    st.set_staging(lbx.STAGE_AUTO)                # falls back to per-thread copies
+    st.step(2)
+    assert st.check_finite()
+
+
+@pytest.mark.parametrize("name,prec", [("mhd", lbx.FP32_SHIFT), ("nsf", lbx.FP64), ("nsf", lbx.FP32_SHIFT)])
+def test_tune_leaves_the_state_unchanged_and_results_identical(name, prec):
+    """lbx_state_tune times launches cur -> next only: populations, time and every later
+    result equal those of an untuned state bitwise."""
+    n = 24 if name == "mhd" else 72
+    case, st = _staged_state(name, prec, "thread", n)
+    case, ref = _staged_state(name, prec, "thread", n)
+    st.step(3)
+    ref.step(3)
+    f0 = st.get_populations()
+    rep = st.tune(trials=2)
+    assert torch.equal(st.get_populations(), f0)
+    assert st.time[0] == 3
+    if prec == lbx.FP32_SHIFT and name == "nsf":
+        assert rep["ms_per_step"] == -1.0 and rep["block"] == 128      # register-resident
+    else:
+        assert rep["staging"] in (lbx.STAGE_THREAD, lbx.STAGE_BULK) and rep["block"] in (32, 64, 128)
+        assert rep["ms_per_step"] > 0
+    st.step(4)
+    ref.step(4)
+    assert torch.equal(st.moments(), ref.moments())
