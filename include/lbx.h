@@ -77,11 +77,37 @@ typedef enum { LBX_ACOUSTIC = 1, LBX_DIFFUSIVE = 2 } lbx_scaling;
 typedef enum { LBX_FP64 = 1, LBX_FP32_SHIFT = 2, LBX_FP16_SCALED = 3 } lbx_precision;
 
 /* Manufactured forcing S_MMS = d_t Q_ex + div Phi(Q_ex) - S(Q_ex) (Sec. 4), added to the
- * conserved components at t + dt/2:
+ * conserved components at t + dt/2 (node coordinates x = (i, j, l) dx, dx = 1/nx):
  *   NONE          no forcing;
  *   ADR_SEPARABLE u_ex = 1 + A sin(2 pi x) cos(2 pi y) exp(-t) for the ADR cascade with
- *                 R = 0; mms_amp = A. */
-typedef enum { LBX_MMS_NONE = 0, LBX_MMS_ADR_SEPARABLE = 1 } lbx_mms;
+ *                 R = 0; mms_amp = A;
+ *   FOURIER       every primitive field V_p of the family is mms_mean[p] plus a sum of
+ *                 modes (lbx_mms_mode, at most LBX_MMS_MAX_MODES).  The exact augmented
+ *                 state is assembled from the primitives and their derivatives, and S_MMS
+ *                 is evaluated at every node and step from the modes' analytic
+ *                 derivatives, carried through the family's own flux by forward-mode dual
+ *                 numbers.  Primitives p per family, and the state built from them:
+ *                   ADR_CASCADE (u)                  Q = (u, du/dx, du/dy)
+ *                   NSF (rho, u, v, p)               Q = (rho, rho u, rho v,
+ *                                                        p/(gamma-1) + rho|u|^2/2,
+ *                                                        grad u, grad v, grad T), T = p/(rho R)
+ *                   MHD (rho, u_x, u_y, u_z, B_x, B_y, B_z, p)
+ *                                                    Q = (rho, rho u, B, p/(gamma-1) +
+ *                                                        rho|u|^2/2 + |B|^2/2, curl B)
+ *                   BURGERS (u), MAXWELL_TM (E_z, H_x, H_y): Q = V
+ *                   EULER (rho, u, v, p)             Q = (rho, rho u, rho v,
+ *                                                        p/(gamma-1) + rho|u|^2/2)
+ *                 The table is copied by lbx_scheme_derive. */
+typedef enum { LBX_MMS_NONE = 0, LBX_MMS_ADR_SEPARABLE = 1, LBX_MMS_FOURIER = 2 } lbx_mms;
+
+#define LBX_MMS_MAX_MODES 64
+/* One term of a manufactured primitive field:
+ *   V_p(x, t) += amp sin(2 pi (k . x) + phase) exp(sigma t) cos(omega t + psi). */
+typedef struct {
+    int p;                 /* primitive index (see LBX_MMS_FOURIER)                      */
+    int k[3];              /* integer wave numbers (k[2] = 0 in 2D)                      */
+    double amp, phase, sigma, omega, psi;
+} lbx_mms_mode;
 
 typedef struct {
     int family;            /* lbx_family                                                */
@@ -107,6 +133,9 @@ typedef struct {
     int mms;               /* lbx_mms                                                   */
     double mms_amp;        /* amplitude A of the ADR manufactured solution              */
     int allow_subchar_violation; /* nonzero: lbx_init does not fail on a violated bound */
+    const lbx_mms_mode* mms_modes; /* FOURIER: the mode table (read during the call)    */
+    int mms_n_modes;       /* FOURIER: 1 .. LBX_MMS_MAX_MODES                           */
+    double mms_mean[8];    /* FOURIER: mean of each primitive                           */
 } lbx_scheme_desc;
 
 typedef struct lbx_system lbx_system;

@@ -13,35 +13,9 @@
 // sum_{k conserved, j} mu_{k,j} (g_{k,j} - f^eq_{k,j}), to be divided by tau^2.
 #pragma once
 
-#include <type_traits>
-
 #include "kernels.cuh"
 
 namespace lbx {
-
-// ------------------------------------------------------------------- dual numbers
-template <typename T>
-struct Dual {
-  T v, d;
-  __host__ __device__ Dual() : v(0), d(0) {}
-  __host__ __device__ Dual(T a, T b) : v(a), d(b) {}
-  template <typename U, typename = typename std::enable_if<std::is_arithmetic<U>::value>::type>
-  __host__ __device__ Dual(U a) : v(T(a)), d(0) {}
-  __host__ __device__ Dual& operator+=(const Dual& o) { v += o.v; d += o.d; return *this; }
-  __host__ __device__ Dual& operator-=(const Dual& o) { v -= o.v; d -= o.d; return *this; }
-  __host__ __device__ Dual& operator*=(const Dual& o) { d = d * o.v + v * o.d; v *= o.v; return *this; }
-};
-template <typename T> __host__ __device__ inline Dual<T> operator+(Dual<T> a, const Dual<T>& b) { return a += b; }
-template <typename T> __host__ __device__ inline Dual<T> operator-(Dual<T> a, const Dual<T>& b) { return a -= b; }
-template <typename T> __host__ __device__ inline Dual<T> operator-(const Dual<T>& a) { return Dual<T>(-a.v, -a.d); }
-template <typename T> __host__ __device__ inline Dual<T> operator*(const Dual<T>& a, const Dual<T>& b) {
-  return Dual<T>(a.v * b.v, a.d * b.v + a.v * b.d);
-}
-template <typename T> __host__ __device__ inline Dual<T> operator/(const Dual<T>& a, const Dual<T>& b) {
-  const T inv = T(1) / b.v;
-  const T q = a.v * inv;
-  return Dual<T>(q, (a.d - q * b.d) * inv);
-}
 
 // h_k of the header at one node: w_k m0_k + gradient of
 // F(Q) = sum_k' w_k' lc m1_k' . Phi_k'(Q) + dt m0_k' S_k'(Q) with respect to Q (delta form:
@@ -117,7 +91,7 @@ __global__ void __launch_bounds__(128) k_adj_step(const typename St::S* __restri
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const T mu = Lnext[((size_t)k * Q + i) * plane + cell];
-      const T wm = T(Lat::w(i)) * mu;
+      const T wm = weight<Lat, T>(i) * mu;
       m0[k] += wm;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
@@ -148,7 +122,7 @@ __global__ void __launch_bounds__(128) k_adj_step(const typename St::S* __restri
           if (Lat::c(i, d) == 1) cph += ph[d];
           if (Lat::c(i, d) == -1) cph -= ph[d];
         }
-        const T feq = T(Lat::w(i)) * (X[k] + cph);
+        const T feq = weight<Lat, T>(i) * (X[k] + cph);
         const T g = (T)ld_again(An + eidx<K, Q>(k, i, pi.src<Lat>(i, p.nx, p.ny), (unsigned int)plane));
         tacc += mu * (g - feq);
       }

@@ -1,0 +1,32 @@
+// Forward-mode dual numbers: a value and one derivative, carried through generic system
+// code (the flux, the source and the manufactured-state assembly of systems.cuh).
+#pragma once
+
+#include <type_traits>
+
+namespace lbx {
+
+template <typename T>
+struct Dual {
+  T v, d;
+  __host__ __device__ Dual() : v(0), d(0) {}
+  __host__ __device__ Dual(T a, T b) : v(a), d(b) {}
+  template <typename U, typename = typename std::enable_if<std::is_arithmetic<U>::value>::type>
+  __host__ __device__ Dual(U a) : v(T(a)), d(0) {}
+  __host__ __device__ Dual& operator+=(const Dual& o) { v += o.v; d += o.d; return *this; }
+  __host__ __device__ Dual& operator-=(const Dual& o) { v -= o.v; d -= o.d; return *this; }
+  __host__ __device__ Dual& operator*=(const Dual& o) { d = d * o.v + v * o.d; v *= o.v; return *this; }
+};
+template <typename T> __host__ __device__ inline Dual<T> operator+(Dual<T> a, const Dual<T>& b) { return a += b; }
+template <typename T> __host__ __device__ inline Dual<T> operator-(Dual<T> a, const Dual<T>& b) { return a -= b; }
+template <typename T> __host__ __device__ inline Dual<T> operator-(const Dual<T>& a) { return Dual<T>(-a.v, -a.d); }
+template <typename T> __host__ __device__ inline Dual<T> operator*(const Dual<T>& a, const Dual<T>& b) {
+  return Dual<T>(a.v * b.v, a.d * b.v + a.v * b.d);
+}
+template <typename T> __host__ __device__ inline Dual<T> operator/(const Dual<T>& a, const Dual<T>& b) {
+  const T inv = T(1) / b.v;
+  const T q = a.v * inv;
+  return Dual<T>(q, (a.d - q * b.d) * inv);
+}
+
+}  // namespace lbx

@@ -23,10 +23,18 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "dual.cuh"
 #include "lattices.cuh"
 #include "systems.cuh"
 
 namespace lbx {
+
+// One manufactured mode on the device (lbx_mms_mode with 2 pi k precomputed).
+struct MmsMode {
+  double k2pi[3];
+  double amp, phase, sigma, omega, psi;
+  int p, pad_;
+};
 
 template <typename T>
 struct KParams {
@@ -46,7 +54,16 @@ struct KParams {
   const long long* step_ptr;   // step index at the start of this launch sequence
   int step_rel;                // offset of this launch in the sequence
   unsigned int* err;           // device error word: bit 0 = a bounded wait timed out
+  T dx;                        // node spacing (coordinates of the manufactured fields)
+  const MmsMode* mms_modes;    // FOURIER forcing table; null = off
+  int mms_n;
+  T mms_mean[8];               // mean of each primitive
 };
+
+template <typename T>
+__host__ __device__ __forceinline__ bool has_forcing(const KParams<T>& p) {
+  return p.mms_tab != nullptr || p.mms_modes != nullptr;
+}
 
 // Element index of population (k, i) at `cell` (see the storage layout above).
 template <int K, int Q>
@@ -129,6 +146,98 @@ __device__ __forceinline__ T adr_mms(const KParams<T>& p, int x, int y, long lon
   const T* tb = p.mms_tab;
   const T sxv = tb[x], cxv = tb[p.nx + x], syv = tb[2 * p.nx + y], cyv = tb[2 * p.nx + p.ny + y];
   return e * (p.mms_c0 * sxv * cyv + p.mms_cx * cxv * cyv - p.mms_cy * sxv * syv);
+}
+
+// Manufactured forcing of a FOURIER table (Sec. 4): S_MMS = d_t Q_ex + div Phi(Q_ex) - S(Q_ex)
+// at (x, t + dt/2), added to the conserved components of Src.  Every primitive is
+// mean + sum amp sin(theta) g(t), theta = 2 pi k.x + phase, g = exp(sigma t) cos(omega t + psi),
+// so its value, time derivative, gradient and Hessian follow in closed form from one sin/cos
+// of theta and of the time phase per mode.  The exact augmented state (Sys::augment) is then
+// formed with dual numbers that carry d/dt once and d/dx_b once per direction b (the trackers'
+// derivative along b comes from the Hessian), and the flux of each direction-b state gives
+// d Phi_k,b / dx_b from the same delta-form system code the step uses.  Kept out of line: it
+// runs only in forced verification runs and must not cost the step kernels registers.
+template <class Lat, template <typename> class SysT, typename T>
+__device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int z, long long step,
+                                         T* __restrict__ Src) {
+  using D1 = Dual<T>;
+  using SysD = SysT<D1>;
+  constexpr int K = SysD::K, NC = SysD::NC, NP = SysD::NPRIM, D = Lat::D;
+  const T t = (T(step) + T(0.5)) * p.dt;
+  const T xc[3] = {T(x) * p.dx, T(y) * p.dx, T(z) * p.dx};
+  T V[NP], Vt[NP], G[NP][3], H[NP][3][3];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    V[q] = p.mms_mean[q];
+    Vt[q] = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      G[q][b] = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) H[q][b][c] = T(0);
+    }
+  }
+  for (int m = 0; m < p.mms_n; ++m) {
+    const MmsMode& md = p.mms_modes[m];
+    const T k[3] = {T(md.k2pi[0]), T(md.k2pi[1]), T(md.k2pi[2])};
+    T th = T(md.phase);
+#pragma unroll
+    for (int d = 0; d < D; ++d) th += k[d] * xc[d];
+    T sn, cs, st, ct;
+    sincos(th, &sn, &cs);
+    sincos(T(md.omega) * t + T(md.psi), &st, &ct);
+    const T e = exp(T(md.sigma) * t);
+    const T g = e * ct, gt = T(md.sigma) * g - T(md.omega) * e * st;
+    const T a = T(md.amp);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      if (q != md.p) continue;
+      V[q] += a * sn * g;
+      Vt[q] += a * sn * gt;
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        G[q][b] += a * cs * k[b] * g;
+#pragma unroll
+        for (int c = 0; c < D; ++c) H[q][b][c] -= a * sn * k[b] * k[c] * g;
+      }
+    }
+  }
+  D1 pd[NPRM], q0[K];
+#pragma unroll
+  for (int i = 0; i < NPRM; ++i) pd[i] = D1(p.prm[i], T(0));
+#pragma unroll
+  for (int k2 = 0; k2 < K; ++k2) q0[k2] = D1(p.Q0[k2], T(0));
+  D1 Vd[NP], Gd[NP][3], Qd[K];
+  // d/dt of the conserved components
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    Vd[q] = D1(V[q], Vt[q]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Gd[q][b] = D1(G[q][b], T(0));
+  }
+  SysD::augment(pd, Vd, Gd, Qd);
+  T acc[NC];
+#pragma unroll
+  for (int k2 = 0; k2 < NC; ++k2) acc[k2] = Qd[k2].d;
+  // divergence of the flux and the state source
+#pragma unroll 1
+  for (int b = 0; b < D; ++b) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      Vd[q] = D1(V[q], G[q][b]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Gd[q][c] = D1(G[q][c], H[q][b][c]);
+    }
+    SysD::augment(pd, Vd, Gd, Qd);
+    D1 dQd[K], Phi[K][D], S[K];
+#pragma unroll
+    for (int k2 = 0; k2 < K; ++k2) dQd[k2] = Qd[k2] - q0[k2];
+    SysD::eval(pd, q0, dQd, Phi, S);
+#pragma unroll
+    for (int k2 = 0; k2 < NC; ++k2) acc[k2] += Phi[k2][b].d - (b == 0 ? S[k2].v : T(0));
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < NC; ++k2) Src[k2] += acc[k2];
 }
 
 // --------------------------------------------------------------------------- the step
@@ -247,9 +356,9 @@ __device__ __forceinline__ double to_c(double v) { return v; }
 // divided by s_k): X, phi and dt S are divided by s_k once per component.
 // Moments, flux and source, equilibrium, BGK and store for one node whose populations
 // are available through get_pair(kp, i, a, b) / get_odd(i) (registers or a staged column).
-template <class Lat, template <typename> class SysT, class St, class GetPair, class GetOdd>
+template <class Lat, template <typename> class SysT, class St, bool FOURIER = false, class GetPair, class GetOdd>
 __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, const KParams<typename St::C>& p,
-                                            int x, int y, unsigned int cell, long long step, bool active,
+                                            int x, int y, int z, unsigned int cell, long long step, bool active,
                                             GetPair get_pair, GetOdd get_odd) {
   using T = typename St::C;
   using V = typename PairOf<typename St::S>::V;
@@ -286,6 +395,9 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
   T Phi[K][D], Src[K];
   Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
   if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y, step);
+  if constexpr (FOURIER) {
+    if (p.mms_modes != nullptr) mms_fourier<Lat, SysT, T>(p, x, y, z, step, Src);
+  }
 
   // a4 + a5 + a6: equilibrium (Eq. feq), BGK with source (Eq. lbe_update), store
   auto out_of = [&](int k, int i, T f) -> T {
@@ -300,7 +412,7 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
       if (cd == -1) P -= phd;
     }
     const T Xs = X[k] + p.tau[k] * (p.dt * Src[k] * inv_s);
-    const T wi = T(Lat::w(i));
+    const T wi = weight<Lat, T>(i);
     const T Fi = fma(T(sg) * wi, P, wi * Xs);
     return fma(p.omega[k], Fi - f, f);
   };
@@ -342,7 +454,7 @@ __device__ __forceinline__ void stage_node(const typename St::S* __restrict__ A,
   }
 }
 
-template <class Lat, template <typename> class SysT, class St, int MODE, int COLS = 128>
+template <class Lat, template <typename> class SysT, class St, int MODE, int COLS = 128, bool FOURIER = false>
 __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
                                           const KParams<typename St::C>& p, int x, int y, int z,
                                           long long step) {
@@ -367,8 +479,8 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
               fv[2 * kp + 1][i]);
       if constexpr (ODD) fv[K - 1][i] = to_c(__ldg(A + eidx<K, Q>(K - 1, i, src, plane)));
     }
-    finish_node<Lat, SysT, St>(
-        B, p, x, y, cell, step, true,
+    finish_node<Lat, SysT, St, FOURIER>(
+        B, p, x, y, z, cell, step, true,
         [&](int kp, int i, T& a, T& b) {
           a = fv[2 * kp][i];
           b = fv[2 * kp + 1][i];
@@ -381,8 +493,8 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
     S* colo = reinterpret_cast<S*>(reinterpret_cast<V*>(lbx_smem) + KP * Q * COLS) + threadIdx.x;
     stage_node<Lat, SysT, St, COLS>(A, colv, colo, pi, p);
     stage_wait();
-    finish_node<Lat, SysT, St>(
-        B, p, x, y, cell, step, true, [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); },
+    finish_node<Lat, SysT, St, FOURIER>(
+        B, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); },
         [&](int i) -> T { return lds_c(colo + i * COLS); });
   }
 }
@@ -522,7 +634,7 @@ __device__ __forceinline__ void step_node_split(const typename St::S* __restrict
   auto out_of = [&](int k, int i, T f) -> T {
     const T inv_s = St::SCALE ? p.inv_scale[k] : T(1);
     const T Xs = X[k] + p.tau[k] * (p.dt * Src[k] * inv_s);
-    const T wi = T(Lat::w(i));
+    const T wi = weight<Lat, T>(i);
     T F;
     if (i == 0) {
       F = wi * Xs;
@@ -580,7 +692,7 @@ __global__ void __launch_bounds__(COLS, SplitMode<Lat, SysT, St, COLS>::min_bloc
   const int xr = blockIdx.x * (COLS / 2) + (int)(threadIdx.x >> 1);
   const bool active = xr < p.nx;
   const int x = active ? xr : p.nx - 1;
-  const long long step = p.mms_tab != nullptr ? *p.step_ptr + p.step_rel : 0;
+  const long long step = has_forcing(p) ? *p.step_ptr + p.step_rel : 0;
   step_node_split<Lat, SysT, St, COLS>(A, B, p, x, blockIdx.y, blockIdx.z, step, (int)(threadIdx.x & 1), active);
 }
 
@@ -736,22 +848,24 @@ __global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_block
     return;
   }
   const unsigned int cell = ((unsigned int)z * (unsigned int)ny + (unsigned int)y) * (unsigned int)nx + x;
-  const long long step = p.mms_tab != nullptr ? *p.step_ptr + p.step_rel : 0;
+  const long long step = has_forcing(p) ? *p.step_ptr + p.step_rel : 0;
   finish_node<Lat, SysT, St>(
-      B, p, x, y, cell, step, true,
+      B, p, x, y, z, cell, step, true,
       [&](int kp, int i, T& a, T& b) { lds_pair(rowv + (size_t)(kp * Q + i) * M::ROWP + t + M::shift(i, EP), a, b); },
       [&](int i) -> T { return lds_c(rowo + (size_t)(ODD ? i : 0) * M::ROWO + t + M::shift(i, EO)); });
 }
 
 // Register budget per thread follows the residency the populations' staging allows.
-// Blocks of COLS threads along x (COLS = 128 for register-resident kernels).
-template <class Lat, template <typename> class SysT, class St, int MODE, int COLS>
+// Blocks of COLS threads along x (COLS = 128 for register-resident kernels).  FOURIER
+// compiles the manufactured forcing of a mode table in (a separate instantiation, so the
+// kernels of unforced runs carry none of its code).
+template <class Lat, template <typename> class SysT, class St, int MODE, int COLS, bool FOURIER = false>
 __global__ void __launch_bounds__(COLS, StepMode<Lat, SysT, St, COLS>::min_blocks)
     k_step(const typename St::S* __restrict__ A, typename St::S* __restrict__ B, const KParams<typename St::C> p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
-  const long long step = p.mms_tab != nullptr ? *p.step_ptr + p.step_rel : 0;
-  step_node<Lat, SysT, St, MODE, COLS>(A, B, p, x, blockIdx.y, blockIdx.z, step);
+  const long long step = has_forcing(p) ? *p.step_ptr + p.step_rel : 0;
+  step_node<Lat, SysT, St, MODE, COLS, FOURIER>(A, B, p, x, blockIdx.y, blockIdx.z, step);
 }
 
 // Many independent 2D grids in one persistent launch.  Instance j's populations start at

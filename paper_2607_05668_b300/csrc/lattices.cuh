@@ -57,4 +57,25 @@ struct LatD3Q19 {
   static constexpr double cs2 = 1.0 / 3.0;
 };
 
+// Weights for binary32 arithmetic: the moving weights rounded to multiples of 2^-26
+// (exact in binary32) and the rest weight 1 minus their sum, so that the weights add up
+// to exactly 1.  The nearest binary32 values of 1/3, 1/6, 1/9, ... add up to about
+// 1 + 3e-8, and an update that forms w_i (X + ...) would then gain that fraction of X at
+// every step: a systematic drift of about 6e-8 of the field per step.  The change of the
+// moving weights (at most 2^-27 absolute) is far below the binary32 rounding of the update.
+template <class Lat>
+__host__ __device__ constexpr double weight_sum1(int i) {
+  constexpr double S = 67108864.0;   // 2^26
+  if (i != 0) return (double)(long long)(Lat::w(i) * S + 0.5) / S;
+  double r = 1.0;
+  for (int j = 1; j < Lat::Q; ++j) r -= (double)(long long)(Lat::w(j) * S + 0.5) / S;
+  return r;
+}
+
+// Lattice weight w_i in the arithmetic type T (binary64: the exact value's nearest double).
+template <class Lat, typename T>
+__host__ __device__ constexpr T weight(int i) {
+  return sizeof(T) == 8 ? T(Lat::w(i)) : T(weight_sum1<Lat>(i));
+}
+
 }  // namespace lbx

@@ -55,6 +55,18 @@ static int family_NC(int f) {
   }
 }
 static int family_D(int f) { return f == LBX_MHD_J_TRACK ? 3 : 2; }
+// Primitive fields of a FOURIER manufactured solution (lbx_mms).
+static int family_nprim(int f) {
+  switch (f) {
+    case LBX_ADR_CASCADE: return 1;
+    case LBX_NSF_PRIM_TRACK: return 4;
+    case LBX_MHD_J_TRACK: return 8;
+    case LBX_BURGERS: return 1;
+    case LBX_EULER: return 4;
+    case LBX_MAXWELL_TM: return 3;
+  }
+  return 0;
+}
 
 static const char* NAMES_ADR[] = {"u", "G_x", "G_y"};
 static const char* NAMES_NSF[] = {"rho", "m_x", "m_y", "E", "G_u_x", "G_u_y", "G_v_x", "G_v_y", "G_T_x", "G_T_y"};
@@ -175,13 +187,33 @@ extern "C" lbx_status lbx_scheme_derive(const lbx_system* sys, const lbx_scheme_
     return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown precision %d", d->precision);
   if (d->mms == LBX_MMS_ADR_SEPARABLE && (sys->family != LBX_ADR_CASCADE || sys->params[3] != 0.0))
     return fail(LBX_ERR_ARG, "lbx_scheme_derive: ADR_SEPARABLE forcing needs the ADR cascade with R = 0");
-  if (d->mms != LBX_MMS_NONE && d->mms != LBX_MMS_ADR_SEPARABLE)
+  if (d->mms != LBX_MMS_NONE && d->mms != LBX_MMS_ADR_SEPARABLE && d->mms != LBX_MMS_FOURIER)
     return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown forcing %d", d->mms);
+  if (d->mms == LBX_MMS_FOURIER) {
+    if (!d->mms_modes || d->mms_n_modes < 1 || d->mms_n_modes > LBX_MMS_MAX_MODES)
+      return fail(LBX_ERR_ARG, "lbx_scheme_derive: FOURIER forcing needs 1..%d modes", LBX_MMS_MAX_MODES);
+    for (int m = 0; m < d->mms_n_modes; ++m) {
+      const lbx_mms_mode& md = d->mms_modes[m];
+      if (md.p < 0 || md.p >= family_nprim(sys->family))
+        return fail(LBX_ERR_ARG, "lbx_scheme_derive: mode %d names primitive %d of %d", m, md.p,
+                    family_nprim(sys->family));
+      if (sys->D == 2 && md.k[2] != 0)
+        return fail(LBX_ERR_ARG, "lbx_scheme_derive: mode %d has k_z != 0 in 2D", m);
+      if (!std::isfinite(md.amp) || !std::isfinite(md.phase) || !std::isfinite(md.sigma) ||
+          !std::isfinite(md.omega) || !std::isfinite(md.psi))
+        return fail(LBX_ERR_ARG, "lbx_scheme_derive: mode %d is not finite", m);
+    }
+  }
   const bool has_trackers = sys->K > sys->NC;
   if (has_trackers && !(d->g_tau > 0.0)) return fail(LBX_ERR_ARG, "lbx_scheme_derive: g_tau must be > 0");
   auto* s = new lbx_scheme();
   s->sys = *sys;
   s->d = *d;
+  if (d->mms == LBX_MMS_FOURIER)
+    for (int m = 0; m < d->mms_n_modes; ++m) s->modes[m] = d->mms_modes[m];
+  else
+    s->d.mms_n_modes = 0;
+  s->d.mms_modes = nullptr;
   s->q = q;
   s->nx = (int)nx;
   s->ny = (int)ny;
@@ -399,6 +431,12 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
     p.mms_cy = (T)(tp * A * s.sys.params[1]);
     p.mms_tab = sizeof(T) == 8 ? (const T*)st->d_mms_tab64 : (const T*)st->d_mms_tab32;
   }
+  p.dx = (T)s.dx;
+  if (s.d.mms == LBX_MMS_FOURIER && st->d_mms_modes) {
+    p.mms_modes = (const MmsMode*)st->d_mms_modes;
+    p.mms_n = s.d.mms_n_modes;
+    for (int q = 0; q < 8; ++q) p.mms_mean[q] = (T)s.d.mms_mean[q];
+  }
 }
 
 // ------------------------------------------------------------------------ dispatch
@@ -480,6 +518,15 @@ struct OpsImpl {
   static cudaError_t step(const lbx_state* st, const void* A, void* B, int rel, cudaStream_t strm) {
     KParams<C> p = st->pc<C>();
     p.step_rel = rel;
+    if (p.mms_modes != nullptr) {
+      // mode-table forcing: its own instantiation, 128 threads, per-thread staging
+      const size_t bytes = StepMode<Lat, SysT, St, 128>::smem_bytes;
+      static cudaError_t prep = prepare((const void*)k_step<Lat, SysT, St, MODE, 128, true>, bytes);
+      if (prep != cudaSuccess) return prep;
+      dim3 b = MODE == MODE_REG ? block(st->sch) : dim3(128, 1, 1), g = grid(st->sch, b);
+      k_step<Lat, SysT, St, MODE, 128, true><<<g, b, bytes, strm>>>((const S*)A, (S*)B, p);
+      return cudaGetLastError();
+    }
     if constexpr (MODE == MODE_REG) {
       dim3 b = block(st->sch), g = grid(st->sch, b);
       k_step<Lat, SysT, St, MODE, 128><<<g, b, 0, strm>>>((const S*)A, (S*)B, p);
@@ -608,6 +655,7 @@ static void free_state(lbx_state* st) {
   cudaFree(st->d_feq0);
   cudaFree(st->d_partials);
   cudaFree(st->d_red_out);
+  cudaFree(st->d_mms_modes);
   cudaFree(st->d_mms_tab64);
   cudaFree(st->d_mms_tab32);
   delete st;
@@ -731,6 +779,23 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
     CKI(cudaMalloc(&st->d_mms_tab32, sizeof(float) * t.size()));
     CKI(cudaMemcpyAsync(st->d_mms_tab64, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, st->stream));
     CKI(cudaMemcpyAsync(st->d_mms_tab32, tf.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice, st->stream));
+    CKI(cudaStreamSynchronize(st->stream));
+  }
+  if (sch->d.mms == LBX_MMS_FOURIER) {
+    std::vector<MmsMode> md(sch->d.mms_n_modes);
+    for (int m = 0; m < sch->d.mms_n_modes; ++m) {
+      const lbx_mms_mode& a = sch->modes[m];
+      for (int d = 0; d < 3; ++d) md[m].k2pi[d] = 2.0 * M_PI * a.k[d];
+      md[m].amp = a.amp;
+      md[m].phase = a.phase;
+      md[m].sigma = a.sigma;
+      md[m].omega = a.omega;
+      md[m].psi = a.psi;
+      md[m].p = a.p;
+      md[m].pad_ = 0;
+    }
+    CKI(cudaMalloc(&st->d_mms_modes, sizeof(MmsMode) * md.size()));
+    CKI(cudaMemcpyAsync(st->d_mms_modes, md.data(), sizeof(MmsMode) * md.size(), cudaMemcpyHostToDevice, st->stream));
     CKI(cudaStreamSynchronize(st->stream));
   }
   refresh_params(st);

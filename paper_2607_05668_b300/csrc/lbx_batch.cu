@@ -130,6 +130,8 @@ extern "C" lbx_status lbx_batch_create(const lbx_scheme* const* schemes, int n, 
   }
   if (s0.d.precision == LBX_FP16_SCALED)
     return fail(LBX_ERR_UNSUPPORTED, "lbx_batch_create: FP16_SCALED storage is not batched");
+  if (s0.d.mms == LBX_MMS_FOURIER)
+    return fail(LBX_ERR_UNSUPPORTED, "lbx_batch_create: FOURIER forcing is not batched");
   auto* b = new lbx_batch();
   b->n = n;
   b->K = s0.sys.K;

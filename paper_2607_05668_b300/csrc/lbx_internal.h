@@ -18,7 +18,8 @@ struct lbx_system {
 
 struct lbx_scheme {
   lbx_system sys;
-  lbx_scheme_desc d;
+  lbx_scheme_desc d;            // d.mms_modes is cleared: the table lives in `modes`
+  lbx_mms_mode modes[LBX_MMS_MAX_MODES];
   int q;
   int nx, ny, nz;
   long long ncell;
@@ -68,6 +69,7 @@ struct lbx_state {
   double* d_partials = nullptr; // reduction scratch [red_blocks][K][4]
   double* d_red_out = nullptr;  // [K][4]
   int red_blocks = 0;
+  void* d_mms_modes = nullptr;  // lbx::MmsMode[n] of a FOURIER forcing
   double* d_mms_tab64 = nullptr;
   float* d_mms_tab32 = nullptr;
   double scale[lbx::KMAX];

@@ -12,6 +12,12 @@
 //
 // Parameters arrive as a T array `p` whose layout each system documents; the host fills
 // it (physical values plus derived background quantities).
+//
+// augment() builds the exact augmented state of a manufactured solution from the family's
+// NPRIM primitive fields V and their gradients G[p][b] = dV_p/dx_b: the conserved
+// components from V, the trackers from G (the gradients of their parents, or curl B).  It
+// is written for a generic scalar U so that a dual number carries one derivative of every
+// input through it.
 #pragma once
 
 namespace lbx {
@@ -25,7 +31,14 @@ constexpr int NPRM = 24;
 // p: 0 a_x, 1 a_y, 2 nu, 3 R, 4 1/tau_grad
 template <typename T>
 struct SysADR {
-  static constexpr int K = 3, NC = 1, D = 2, FAMILY = 1;
+  static constexpr int K = 3, NC = 1, D = 2, FAMILY = 1, NPRIM = 1;
+  // primitive: u
+  template <typename U>
+  __host__ __device__ static void augment(const T* p, const U (&V)[NPRIM], const U (&G)[NPRIM][3], U (&Q)[K]) {
+    Q[0] = V[0];
+    Q[1] = G[0][0];
+    Q[2] = G[0][1];
+  }
   __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
     const T a[2] = {p[0], p[1]};
     const T nu = p[2], R = p[3], itg = p[4];
@@ -52,7 +65,23 @@ struct SysADR {
 //    9 tau_v0_xx, 10 tau_v0_xy, 11 tau_v0_yy, 12 gamma, 13 1/R
 template <typename T>
 struct SysNSF {
-  static constexpr int K = 10, NC = 4, D = 2, FAMILY = 2;
+  static constexpr int K = 10, NC = 4, D = 2, FAMILY = 2, NPRIM = 4;
+  // primitives: rho, u, v, p; E = p/(gamma-1) + rho |u|^2/2; trackers grad u, grad v and
+  // grad T with T = p/(rho R): dT/dx_b = (dp/dx_b - R T drho/dx_b) / (rho R)
+  template <typename U>
+  __host__ __device__ static void augment(const T* p, const U (&V)[NPRIM], const U (&G)[NPRIM][3], U (&Q)[K]) {
+    const U rho = V[0], u = V[1], v = V[2], pr = V[3];
+    const U rR = rho * p[1], Tm = pr / rR;
+    Q[0] = rho;
+    Q[1] = rho * u;
+    Q[2] = rho * v;
+    Q[3] = pr / p[0] + U(0.5) * rho * (u * u + v * v);
+    for (int b = 0; b < 2; ++b) {
+      Q[4 + b] = G[1][b];
+      Q[6 + b] = G[2][b];
+      Q[8 + b] = (G[3][b] - p[1] * Tm * G[0][b]) / rR;
+    }
+  }
   __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
     const T gm1 = p[0], mu = p[2], kap = p[3], itg = p[4];
     const T u0[2] = {p[5], p[6]};
@@ -115,7 +144,24 @@ struct SysNSF {
 // p: 0 gamma-1, 1 eta, 2 1/tau_grad, 3..5 u0, 6 E0 + p_t0, 7 u0.B0, 8 gamma
 template <typename T>
 struct SysMHD {
-  static constexpr int K = 11, NC = 8, D = 3, FAMILY = 3;
+  static constexpr int K = 11, NC = 8, D = 3, FAMILY = 3, NPRIM = 8;
+  // primitives: rho, u(3), B(3), p; E = p/(gamma-1) + rho |u|^2/2 + |B|^2/2, j = curl B
+  template <typename U>
+  __host__ __device__ static void augment(const T* p, const U (&V)[NPRIM], const U (&G)[NPRIM][3], U (&Q)[K]) {
+    const U rho = V[0];
+    U ke = U(0), b2 = U(0);
+    Q[0] = rho;
+    for (int a = 0; a < 3; ++a) {
+      Q[1 + a] = rho * V[1 + a];
+      Q[4 + a] = V[4 + a];
+      ke += V[1 + a] * V[1 + a];
+      b2 += V[4 + a] * V[4 + a];
+    }
+    Q[7] = V[7] / p[0] + U(0.5) * (rho * ke + b2);
+    Q[8] = G[6][1] - G[5][2];       // j_x = dB_z/dy - dB_y/dz
+    Q[9] = G[4][2] - G[6][0];       // j_y = dB_x/dz - dB_z/dx
+    Q[10] = G[5][0] - G[4][1];      // j_z = dB_y/dx - dB_x/dy
+  }
   __host__ __device__ static constexpr int eps(int a, int b, int c) {
     return (a - b) * (b - c) * (c - a) / 2;
   }
@@ -192,7 +238,11 @@ struct SysMHD {
 // Sec. 3 (inviscid Burgers): Phi = (u^2/2, u^2/2).  No parameters.
 template <typename T>
 struct SysBurgers {
-  static constexpr int K = 1, NC = 1, D = 2, FAMILY = 4;
+  static constexpr int K = 1, NC = 1, D = 2, FAMILY = 4, NPRIM = 1;
+  template <typename U>
+  __host__ __device__ static void augment(const T* p, const U (&V)[NPRIM], const U (&G)[NPRIM][3], U (&Q)[K]) {
+    Q[0] = V[0];
+  }
   __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
     const T h = T(0.5) * dQ[0] * (T(2) * Q0[0] + dQ[0]);
     dPhi[0][0] = h;
@@ -208,7 +258,16 @@ struct SysBurgers {
 // Sec. 3 (compressible Euler).  p: 0 gamma-1, 1 u0x, 2 u0y, 3 E0+p0, 4 gamma
 template <typename T>
 struct SysEuler {
-  static constexpr int K = 4, NC = 4, D = 2, FAMILY = 5;
+  static constexpr int K = 4, NC = 4, D = 2, FAMILY = 5, NPRIM = 4;
+  // primitives: rho, u, v, p; E = p/(gamma-1) + rho |u|^2/2
+  template <typename U>
+  __host__ __device__ static void augment(const T* p, const U (&V)[NPRIM], const U (&G)[NPRIM][3], U (&Q)[K]) {
+    const U rho = V[0], u = V[1], v = V[2];
+    Q[0] = rho;
+    Q[1] = rho * u;
+    Q[2] = rho * v;
+    Q[3] = V[3] / p[0] + U(0.5) * rho * (u * u + v * v);
+  }
   __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
     const T gm1 = p[0];
     const T u0[2] = {p[1], p[2]};
@@ -242,7 +301,11 @@ struct SysEuler {
 // p: 0 c
 template <typename T>
 struct SysMaxwell {
-  static constexpr int K = 3, NC = 3, D = 2, FAMILY = 6;
+  static constexpr int K = 3, NC = 3, D = 2, FAMILY = 6, NPRIM = 3;
+  template <typename U>
+  __host__ __device__ static void augment(const T* p, const U (&V)[NPRIM], const U (&G)[NPRIM][3], U (&Q)[K]) {
+    for (int k = 0; k < 3; ++k) Q[k] = V[k];
+  }
   __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
     const T c = p[0];
     dPhi[0][0] = -c * dQ[2];

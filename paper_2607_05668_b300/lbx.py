@@ -21,7 +21,8 @@ ADR_CASCADE, NSF_PRIM_TRACK, MHD_J_TRACK, BURGERS, EULER, MAXWELL_TM = 1, 2, 3, 
 D2Q5, D2Q9, D3Q7, D3Q19 = 1, 2, 3, 4
 ACOUSTIC, DIFFUSIVE = 1, 2
 FP64, FP32_SHIFT, FP16_SCALED = 1, 2, 3
-MMS_NONE, MMS_ADR_SEPARABLE = 0, 1
+MMS_NONE, MMS_ADR_SEPARABLE, MMS_FOURIER = 0, 1, 2
+MMS_MAX_MODES = 64
 STAGE_AUTO, STAGE_THREAD, STAGE_LANES2, STAGE_BULK = 0, 1, 2, 3
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_SUBCHAR", 5: "ERR_NONFINITE",
@@ -39,11 +40,17 @@ class SystemDesc(C.Structure):
     _fields_ = [("family", C.c_int), ("params", C.c_double * 8), ("Q0", C.c_double * 16)]
 
 
+class MmsMode(C.Structure):
+    _fields_ = [("p", C.c_int), ("k", C.c_int * 3), ("amp", C.c_double), ("phase", C.c_double),
+                ("sigma", C.c_double), ("omega", C.c_double), ("psi", C.c_double)]
+
+
 class SchemeDesc(C.Structure):
     _fields_ = [("lattice", C.c_int), ("extent", C.c_int64 * 3), ("scaling", C.c_int),
                 ("f", C.c_double), ("tau_lb", C.c_double), ("tau_R", C.c_double),
                 ("g_tau", C.c_double), ("precision", C.c_int), ("mms", C.c_int),
-                ("mms_amp", C.c_double), ("allow_subchar_violation", C.c_int)]
+                ("mms_amp", C.c_double), ("allow_subchar_violation", C.c_int),
+                ("mms_modes", C.POINTER(MmsMode)), ("mms_n_modes", C.c_int), ("mms_mean", C.c_double * 8)]
 
 
 _P = C.c_void_p
@@ -170,7 +177,9 @@ class Scheme:
 
     def __init__(self, system: System, lattice, extent, scaling, f, tau_lb=0.0, tau_R=0.0,
                  g_tau=0.0, precision=FP64, mms=MMS_NONE, mms_amp=0.0,
-                 allow_subchar_violation=False):
+                 allow_subchar_violation=False, mms_modes=None, mms_mean=None):
+        """mms_modes: sequence of (p, (kx, ky[, kz]), amp, phase, sigma, omega, psi) for
+        MMS_FOURIER; mms_mean: the primitives' means."""
         d = SchemeDesc()
         d.lattice = lattice
         ext = list(extent) + [1] * (3 - len(extent))
@@ -179,6 +188,20 @@ class Scheme:
         d.scaling, d.f, d.tau_lb, d.tau_R, d.g_tau = scaling, float(f), float(tau_lb), float(tau_R), float(g_tau)
         d.precision, d.mms, d.mms_amp = precision, mms, float(mms_amp)
         d.allow_subchar_violation = int(bool(allow_subchar_violation))
+        table = None
+        if mms_modes is not None:
+            table = (MmsMode * len(mms_modes))()
+            for m, (pi, k, amp, phase, sigma, omega, psi) in enumerate(mms_modes):
+                kk = list(k) + [0] * (3 - len(k))
+                table[m].p = int(pi)
+                for i in range(3):
+                    table[m].k[i] = int(kk[i])
+                table[m].amp, table[m].phase, table[m].sigma = float(amp), float(phase), float(sigma)
+                table[m].omega, table[m].psi = float(omega), float(psi)
+            d.mms_modes = C.cast(table, C.POINTER(MmsMode))
+            d.mms_n_modes = len(mms_modes)
+        for i, v in enumerate(mms_mean or []):
+            d.mms_mean[i] = float(v)
         h = _P()
         check(_lib.lbx_scheme_derive(system._h, C.byref(d), C.byref(h)))
         self._h = h

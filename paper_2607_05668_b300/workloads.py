@@ -41,3 +41,22 @@ def mhd_scheme(case, precision=L.FP32_SHIFT, lattice=L.D3Q19):
     """Acoustic refinement dt = f dx, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
     return L.Scheme(mhd_system(case), lattice, (case.n, case.n, case.n), L.ACOUSTIC, case.f,
                     tau_R=case.tau_R, g_tau=case.g_tau, precision=precision)
+
+
+# ------------------------------------------------------------- forced (manufactured) runs
+_FAMILY = {"adr": L.ADR_CASCADE, "nsf": L.NSF_PRIM_TRACK, "mhd": L.MHD_J_TRACK,
+           "burgers": L.BURGERS, "euler": L.EULER, "maxwell": L.MAXWELL_TM}
+
+
+def table_system(table, params, Q0):
+    """The family of a manufactured mode table (duck-typed: .family) with its parameters."""
+    return L.System(_FAMILY[table.family], params=params, Q0=Q0)
+
+
+def forced_scheme(table, system, lattice, extent, scaling, f, precision=L.FP64, tau_lb=0.0,
+                  tau_R=0.0, g_tau=0.0):
+    """A scheme whose conserved components carry the FOURIER forcing of `table`
+    (.lbx_modes(), .mean)."""
+    return L.Scheme(system, lattice, extent, scaling, f, tau_lb=tau_lb, tau_R=tau_R, g_tau=g_tau,
+                    precision=precision, mms=L.MMS_FOURIER, mms_modes=table.lbx_modes(),
+                    mms_mean=list(table.mean))

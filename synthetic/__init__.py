@@ -321,3 +321,262 @@ def maxwell_exact(x, y, t, A=0.5, w=4.0):
 def adr_exact_stack(case: AdrCase):
     """Callable (x, y, t) -> [1, ...] conserved exact field for the ADR case."""
     return lambda x, y, t: adr_exact(case, x, y, t).unsqueeze(0)
+
+
+# --------------------------------------------------------------------------------------
+# Manufactured solutions as mode tables of primitive fields (forced verification runs)
+# --------------------------------------------------------------------------------------
+
+# primitive fields per family, in table order
+PRIMITIVES = {"adr": ("u",), "nsf": ("rho", "u", "v", "p"),
+              "mhd": ("rho", "u_x", "u_y", "u_z", "B_x", "B_y", "B_z", "p"),
+              "burgers": ("u",), "euler": ("rho", "u", "v", "p"), "maxwell": ("E_z", "H_x", "H_y")}
+
+
+@dataclass
+class ModeTable:
+    """Primitive fields V_p(x, t) = mean[p] + sum over the modes of p of
+    amp sin(2 pi k.x + phase) exp(sigma t) cos(omega t + psi), and the conserved state the
+    family assembles from them (gamma, R: the gas constants where the family has them)."""
+    family: str
+    mean: list
+    modes: list            # (p, k, amp, phase, sigma, omega, psi), k a tuple of ints
+    gamma: float = 1.4
+    R: float = 1.0
+
+    def primitives(self, xs, t):
+        t = t if torch.is_tensor(t) else torch.full_like(xs[0], float(t))
+        V = [torch.full_like(xs[0], float(m)) for m in self.mean]
+        for (p, k, amp, phase, sigma, omega, psi) in self.modes:
+            th = TWO_PI * sum(float(k[d]) * xs[d] for d in range(len(xs))) + phase
+            V[p] = V[p] + amp * torch.sin(th) * torch.exp(sigma * t) * torch.cos(omega * t + psi)
+        return V
+
+    def conserved(self, V):
+        g, R = self.gamma, self.R
+        if self.family in ("adr", "burgers", "maxwell"):
+            return torch.stack(V)
+        if self.family in ("nsf", "euler"):
+            rho, u, v, p = V
+            return torch.stack([rho, rho * u, rho * v, p / (g - 1.0) + 0.5 * rho * (u * u + v * v)])
+        if self.family == "mhd":
+            rho, u, B, p = V[0], V[1:4], V[4:7], V[7]
+            E = p / (g - 1.0) + 0.5 * rho * sum(c * c for c in u) + 0.5 * sum(c * c for c in B)
+            return torch.stack([rho] + [rho * c for c in u] + list(B) + [E])
+        raise ValueError(self.family)
+
+    def exact(self, *xt):
+        """Conserved exact fields at coordinates xt[:-1] and time xt[-1] (oracle callable)."""
+        return self.conserved(self.primitives(xt[:-1], xt[-1]))
+
+    def gradient(self, xs, t, p, b):
+        """d V_p / d x_b, analytic."""
+        t = t if torch.is_tensor(t) else torch.full_like(xs[0], float(t))
+        g = torch.zeros_like(xs[0])
+        for (q, k, amp, phase, sigma, omega, psi) in self.modes:
+            if q != p or k[b] == 0:
+                continue
+            th = TWO_PI * sum(float(k[d]) * xs[d] for d in range(len(xs))) + phase
+            g = g + amp * TWO_PI * k[b] * torch.cos(th) * torch.exp(sigma * t) * torch.cos(omega * t + psi)
+        return g
+
+    def augmented(self, xs, t):
+        """Conserved exact fields plus the family's trackers (ADR: grad u; NSF: grad u,
+        grad v, grad T; MHD: curl B), the initial state of a forced run."""
+        Qc = self.exact(*xs, t)
+        if self.family == "adr":
+            tr = [self.gradient(xs, t, 0, b) for b in range(2)]
+        elif self.family == "nsf":
+            # T = p/(rho R): grad T = (grad p - R T grad rho)/(rho R)
+            rho, _, _, p = self.primitives(xs, t)
+            T = p / (rho * self.R)
+            tr = [self.gradient(xs, t, q, b) for q in (1, 2) for b in range(2)]
+            tr += [(self.gradient(xs, t, 3, b) - self.R * T * self.gradient(xs, t, 0, b)) / (rho * self.R)
+                   for b in range(2)]
+        elif self.family == "mhd":
+            G = lambda c, b: self.gradient(xs, t, 4 + c, b)
+            tr = [G(2, 1) - G(1, 2), G(0, 2) - G(2, 0), G(1, 0) - G(0, 1)]
+        else:
+            return Qc
+        return torch.cat([Qc, torch.stack(tr)])
+
+    def lbx_modes(self):
+        return [(p, tuple(int(c) for c in k), float(a), float(ph), float(s), float(w), float(ps))
+                for (p, k, a, ph, s, w, ps) in self.modes]
+
+
+def _product_modes(p, amp, fx, fy, kx, ky, omega, psi):
+    """amp f_x(2 pi kx x) f_y(2 pi ky y) cos(omega t + psi) as two sine modes (f in sin/cos)."""
+    # sin a cos b = [sin(a+b) + sin(a-b)]/2, cos a sin b = [sin(a+b) - sin(a-b)]/2,
+    # sin a sin b = [sin(a-b+pi/2) - sin(a+b+pi/2)]/2, cos a cos b = [sin(a+b+pi/2) + sin(a-b+pi/2)]/2
+    h = 0.5 * amp
+    plus, minus = (kx, ky, 0), (kx, -ky, 0)
+    q = 0.5 * math.pi
+    if (fx, fy) == ("sin", "cos"):
+        return [(p, plus, h, 0.0, 0.0, omega, psi), (p, minus, h, 0.0, 0.0, omega, psi)]
+    if (fx, fy) == ("cos", "sin"):
+        return [(p, plus, h, 0.0, 0.0, omega, psi), (p, minus, -h, 0.0, 0.0, omega, psi)]
+    if (fx, fy) == ("sin", "sin"):
+        return [(p, minus, h, q, 0.0, omega, psi), (p, plus, -h, q, 0.0, omega, psi)]
+    return [(p, plus, h, q, 0.0, omega, psi), (p, minus, h, q, 0.0, omega, psi)]
+
+
+def burgers_table(A=1.3):
+    """The paper's Burgers field u = A sin(2 pi x) sin(2 pi y) cos t (supplement, MMS)."""
+    return ModeTable("burgers", [0.0], _product_modes(0, A, "sin", "sin", 1, 1, 1.0, 0.0))
+
+
+def maxwell_table(A=0.5, w=4.0):
+    """The paper's TM field: E_z = A sin(kx x) sin(ky y) cos(w t), H_x = A sin(kx x) cos(ky y)
+    sin(w t), H_y = -A (kx/ky) cos(kx x) sin(ky y) sin(w t), kx = 2 pi, ky = 4 pi."""
+    s = -0.5 * math.pi                     # sin(w t) = cos(w t - pi/2)
+    return ModeTable("maxwell", [0.0, 0.0, 0.0],
+                     _product_modes(0, A, "sin", "sin", 1, 2, w, 0.0)
+                     + _product_modes(1, A, "sin", "cos", 1, 2, w, s)
+                     + _product_modes(2, -A * 0.5, "cos", "sin", 1, 2, w, s))
+
+
+def euler_table(gamma=1.4):
+    """The paper's Euler field in the units its scales divide out (rho0 = 1, c_s = 1):
+    p0 = 1/gamma, background u0 = v0 = 3 c_s, k = 2 pi,
+    rho = 1 + 0.3 sin(kx) cos(ky) cos t, u = 3 + 0.3 cos(kx) sin(ky) sin t,
+    v = 3 + 0.3 sin(kx) sin(ky) sin t, p = p0 + (rho - 1) + 0.2 p0 cos(kx) sin(ky) sin t."""
+    p0 = 1.0 / gamma
+    s = -0.5 * math.pi
+    modes = (_product_modes(0, 0.3, "sin", "cos", 1, 1, 1.0, 0.0)
+             + _product_modes(1, 0.3, "cos", "sin", 1, 1, 1.0, s)
+             + _product_modes(2, 0.3, "sin", "sin", 1, 1, 1.0, s)
+             + _product_modes(3, 0.3, "sin", "cos", 1, 1, 1.0, 0.0)
+             + _product_modes(3, 0.2 * p0, "cos", "sin", 1, 1, 1.0, s))
+    return ModeTable("euler", [1.0, 3.0, 3.0, p0], modes, gamma=gamma)
+
+
+def nsf_mms_table(case: NsfCase, seed: int = 2):
+    """Forced NSF field: each primitive (rho, u, v, p) = the case's mean (p0 = rho0 R T0 = 1)
+    + 4 seeded modes (k in [-3, 3]^2 without 0, amp U(0, 0.05), phase U(0, 2 pi)) times
+    cos(t + psi), psi U(0, 2 pi)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u0, v0 = case.U0
+    modes = []
+    for p in range(4):
+        for k in _modes(rng, case.n_modes, 3, 2):
+            modes.append((p, (int(k[0]), int(k[1]), 0), float(rng.uniform(0.0, case.amp_max)),
+                          float(rng.uniform(0.0, TWO_PI)), 0.0, 1.0, float(rng.uniform(0.0, TWO_PI))))
+    return ModeTable("nsf", [1.0, u0, v0, 1.0 * case.R * 1.0], modes, gamma=case.gamma, R=case.R)
+
+
+@dataclass
+class NsfPaperCase:
+    """The paper's NSF manufactured flow (supplement, MMS section) in the units its scales
+    divide out: rho0 = 1, sound speed c_s = 1 at T0 = 1, so R = 1/gamma and p0 = 1/gamma;
+    mu = 3.52 Pa s / (rho0 c_s L) with rho0 = 1.225 kg/m^3, c_s = 340.2 m/s, L = 1 m;
+    kappa = mu c_p / Pr, c_p = gamma R/(gamma - 1), Pr = 0.71; background (u0, v0) = (3, 2).
+    Recipe: diffusive f = 2, tau_R = 60, g_tau = 6."""
+    n: int
+    gamma: float = 1.4
+    Pr: float = 0.71
+    f: float = 2.0
+    tau_R: float = 60.0
+    g_tau: float = 6.0
+
+    @property
+    def R(self):
+        return 1.0 / self.gamma
+
+    @property
+    def mu(self):
+        return 3.52 / (1.225 * 340.2)
+
+    @property
+    def kappa(self):
+        return self.mu * (self.gamma * self.R / (self.gamma - 1.0)) / self.Pr
+
+    @property
+    def dx(self):
+        return 1.0 / self.n
+
+    @property
+    def dt(self):
+        return self.f * self.dx * self.dx
+
+    def reference_state(self):
+        p0 = 1.0 / self.gamma
+        return [1.0, 3.0, 2.0, p0 / (self.gamma - 1.0) + 0.5 * 13.0] + [0.0] * 6
+
+    def table(self):
+        """rho = 1 + 0.2 sin(kx) cos(ky) cos t, u = 3 + 0.2 cos(kx) sin(ky) sin t,
+        v = 2 + 0.15 sin(kx) sin(ky) cos t, p = p0 + (rho - 1) + 0.2 p0 cos(kx) sin(ky) sin t."""
+        p0, s = 1.0 / self.gamma, -0.5 * math.pi
+        modes = (_product_modes(0, 0.2, "sin", "cos", 1, 1, 1.0, 0.0)
+                 + _product_modes(1, 0.2, "cos", "sin", 1, 1, 1.0, s)
+                 + _product_modes(2, 0.15, "sin", "sin", 1, 1, 1.0, 0.0)
+                 + _product_modes(3, 0.2, "sin", "cos", 1, 1, 1.0, 0.0)
+                 + _product_modes(3, 0.2 * p0, "cos", "sin", 1, 1, 1.0, s))
+        return ModeTable("nsf", [1.0, 3.0, 2.0, p0], modes, gamma=self.gamma, R=self.R)
+
+
+@dataclass
+class MhdPaperCase:
+    """The paper's MHD manufactured flow (supplement, MMS section), uniform along z, in the
+    units its scales divide out (rho0 = 1, c_s = 1, p0 = 1/gamma, B in Alfven units):
+    background u0 = v0 = 3, B0 = (0.5, 0.5, 0); eta = 3.4 m^2/s / (c_s L) = 0.01.
+    Recipe of configuration 3: acoustic f = 0.05, tau_R = 160, g_tau = 4."""
+    n: int
+    gamma: float = 1.4
+    eta: float = 0.01
+    f: float = 0.05
+    tau_R: float = 160.0
+    g_tau: float = 4.0
+
+    @property
+    def dx(self):
+        return 1.0 / self.n
+
+    @property
+    def dt(self):
+        return self.f * self.dx
+
+    def reference_state(self):
+        p0 = 1.0 / self.gamma
+        E0 = p0 / (self.gamma - 1.0) + 0.5 * 18.0 + 0.5 * 0.5
+        return [1.0, 3.0, 3.0, 0.0, 0.5, 0.5, 0.0, E0, 0.0, 0.0, 0.0]
+
+    def table(self):
+        """rho = 1 + 0.3 sin(kx) cos(ky) cos t, p = p0 + (rho - 1) + 0.2 p0 cos(kx) sin(ky) sin t,
+        u = 3 + 0.3 cos(kx) sin(ky) sin t, v = 3 + 0.3 sin(kx) sin(ky) sin t, w = 0,
+        B_x = 0.5 - 0.3 cos(kx) sin(ky) sin t, B_y = 0.5 + 0.3 sin(kx) cos(ky) sin t, B_z = 0."""
+        p0, s = 1.0 / self.gamma, -0.5 * math.pi
+        modes = (_product_modes(0, 0.3, "sin", "cos", 1, 1, 1.0, 0.0)
+                 + _product_modes(7, 0.3, "sin", "cos", 1, 1, 1.0, 0.0)
+                 + _product_modes(7, 0.2 * p0, "cos", "sin", 1, 1, 1.0, s)
+                 + _product_modes(1, 0.3, "cos", "sin", 1, 1, 1.0, s)
+                 + _product_modes(2, 0.3, "sin", "sin", 1, 1, 1.0, s)
+                 + _product_modes(4, -0.3, "cos", "sin", 1, 1, 1.0, s)
+                 + _product_modes(5, 0.3, "sin", "cos", 1, 1, 1.0, s))
+        return ModeTable("mhd", [1.0, 3.0, 3.0, 0.0, 0.5, 0.5, 0.0, p0], modes, gamma=self.gamma)
+
+
+def mhd_mms_table(case: MhdCase, seed: int = 2):
+    """Forced 3D MHD field: rho = 1 + 2 modes (amp 0.05), p = 1/gamma + 2 modes (amp 0.02),
+    u from case.n_modes velocity modes and B = curl A from as many potential modes
+    (amplitude case.amp / n_modes each, so div B = 0 exactly), every mode times
+    cos(t + psi) with a seeded psi."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    scale = case.amp / case.n_modes
+    modes = []
+
+    def tphase():
+        return float(rng.uniform(0.0, TWO_PI))
+    for p, amp in ((0, 0.05), (7, 0.02)):
+        for k in _modes(rng, 2, 2, 3):
+            modes.append((p, tuple(int(c) for c in k), amp, float(rng.uniform(0.0, TWO_PI)), 0.0, 1.0, tphase()))
+    for _ in range(case.n_modes):
+        k, d, ph, ps = _modes(rng, 1, 2, 3)[0], rng.uniform(-1, 1, 3), float(rng.uniform(0, TWO_PI)), tphase()
+        for c in range(3):
+            modes.append((1 + c, tuple(int(v) for v in k), scale * float(d[c]), ph, 0.0, 1.0, ps))
+    for _ in range(case.n_modes):
+        k, d, ph, ps = _modes(rng, 1, 2, 3)[0], rng.uniform(-1, 1, 3), float(rng.uniform(0, TWO_PI)), tphase()
+        kxd = np.cross(k, d) / float(np.linalg.norm(k))
+        for c in range(3):          # B = curl of A = scale d sin(th)/(2 pi |k|): cos(th) (k x d)/|k|
+            modes.append((4 + c, tuple(int(v) for v in k), scale * float(kxd[c]), ph + 0.5 * math.pi, 0.0, 1.0, ps))
+    return ModeTable("mhd", [1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0 / case.gamma], modes, gamma=case.gamma)

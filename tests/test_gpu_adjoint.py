@@ -128,3 +128,45 @@ def test_autograd_function_returns_the_adjoint_gradients():
     J2, g2, gt2 = lbx.adjoint(mk(lbx.FP64), Q.detach(), 12, 5, tgt)
     assert float(J) == J2
     assert torch.equal(gQ, 3.0 * g2) and float(gt) == 3.0 * gt2
+
+
+def test_linear_adr_adjoint_is_the_transposed_oracle_matrix_8x8():
+    """Linear ADR cascade (no forcing) on 8 x 8: with the oracle's equilibrium map E
+    (192 -> 960), one-step matrix M (960 x 960) and density projection P, both built column
+    by column, J = 1/2 |P M^n E Q0 - rho*|^2 has the gradient E^T (M^T)^n P^T r.  The GPU
+    adjoint must equal it; and, J being quadratic, a central difference of J along any
+    direction equals <dJ/dQ0, v> for any step h (the tangent-adjoint dot-product identity)."""
+    N, steps = 8, 6
+    case = syn.AdrCase(n=N, tau_u=0.83)
+    och = H.oracle_adr(case, forcing=False)
+    K, q, nn = 3, 5, N * N
+    nQ, nf = K * nn, K * q * nn
+    E = torch.zeros(nf, nQ, dtype=F64)
+    for j in range(nQ):
+        e = torch.zeros(nQ, dtype=F64)
+        e[j] = 1.0
+        E[:, j] = och.init(e.reshape(K, N, N)).reshape(-1)
+    M = torch.zeros(nf, nf, dtype=F64)
+    P = torch.zeros(nn, nf, dtype=F64)
+    for j in range(nf):
+        e = torch.zeros(nf, dtype=F64)
+        e[j] = 1.0
+        f = e.reshape(K, q, N, N)
+        M[:, j] = och.step(f, 0.0).reshape(-1)
+        P[:, j] = och.moments(f)[0].reshape(-1)
+    g = torch.Generator().manual_seed(3)
+    Q = syn.adr_fields(case) + 0.01 * torch.randn((K, N, N), dtype=F64, generator=g)
+    tgt = 1.0 + 0.05 * torch.randn((N, N), dtype=F64, generator=g)
+    Mn = torch.linalg.matrix_power(M, steps)
+    r = P @ Mn @ E @ Q.reshape(-1) - tgt.reshape(-1)
+    grad_m = (E.T @ Mn.T @ P.T @ r).reshape(K, N, N)
+    sch = W.adr_scheme(case, lbx.FP64, forcing=False)
+    J, gq, _ = lbx.adjoint(sch, Q, steps, 4, tgt)
+    assert abs(J - 0.5 * float(r @ r)) <= 1e-12 * abs(J)
+    assert _rel(gq, grad_m) <= 1e-12
+    v = torch.randn((K, N, N), dtype=F64, generator=g)
+    for h in (1e-1, 1e-3):
+        Jp = lbx.adjoint(sch, Q + h * v, steps, steps, tgt)[0]
+        Jm = lbx.adjoint(sch, Q - h * v, steps, steps, tgt)[0]
+        dd = float((gq * v).sum())
+        assert abs((Jp - Jm) / (2 * h) - dd) <= 1e-9 * abs(dd) + 1e-12 * J / h
