@@ -199,6 +199,145 @@ class MhdCurrent(System):
                 for a in range(3)]
 
 
+class NsfConservedGradients(System):
+    """Compressible Navier-Stokes-Fourier with trackers of the conserved fields, the
+    paper's own 12-component cascade (Sec. 2.1.1: the chain rule expands grad u and grad T
+    over the gradients of rho, rho u and E; supplement, NSF system).
+
+    Q = (rho, m_x, m_y, E, G_rho(2), G_mx(2), G_my(2), G_E(2)), G_{V,b} ~ d V / d x_b.
+    grad u = (G_m - u (x) G_rho) / rho, i.e. d u_a / d x_b = (G_{m_a,b} - u_a G_{rho,b}) / rho;
+    grad p = (gamma-1)(G_E - u . G_m + |u|^2/2 G_rho), u . G_m = sum_a u_a G_{m_a};
+    grad T = (grad p / R - T G_rho) / rho, T = p / (rho R).
+    Phi_rho = m, Phi_m = m (x) u + p I - tau_v, Phi_E = (E + p) u - tau_v u - kappa grad T,
+    tau_v = mu (L + L^T - 2/3 tr(L) I), L = grad u; trackers of V in (rho, m_x, m_y, E).
+    """
+    name = "nsf12"
+    K = 12
+    D = 2
+    n_cons = 4
+
+    def __init__(self, gamma, R, mu, kappa, tau_grad):
+        self.gamma, self.R, self.mu, self.kappa = float(gamma), float(R), float(mu), float(kappa)
+        self.tau_grad = float(tau_grad)
+
+    def flux(self, Q):
+        g1 = self.gamma - 1.0
+        rho, m, E = Q[0], Q[1:3], Q[3]
+        u = m / rho
+        u2 = u[0] * u[0] + u[1] * u[1]
+        p = g1 * (E - 0.5 * rho * u2)
+        T = p / (rho * self.R)
+        Gr, Gm, GE = Q[4:6], [Q[6:8], Q[8:10]], Q[10:12]
+        L = [[(Gm[a][b] - u[a] * Gr[b]) / rho for b in range(2)] for a in range(2)]
+        Gp = [g1 * (GE[b] - (u[0] * Gm[0][b] + u[1] * Gm[1][b]) + 0.5 * u2 * Gr[b]) for b in range(2)]
+        GT = [(Gp[b] / self.R - T * Gr[b]) / rho for b in range(2)]
+        div = L[0][0] + L[1][1]
+        tv = [[self.mu * (L[a][b] + L[b][a] - (2.0 / 3.0) * div * (1.0 if a == b else 0.0))
+               for b in range(2)] for a in range(2)]
+        rows = [torch.stack([m[0], m[1]])]
+        for a in range(2):
+            rows.append(torch.stack([m[a] * u[b] + (p if a == b else 0 * p) - tv[a][b] for b in range(2)]))
+        rows.append(torch.stack([(E + p) * u[b] - (tv[b][0] * u[0] + tv[b][1] * u[1])
+                                 - self.kappa * GT[b] for b in range(2)]))
+        for pi, V in enumerate([rho, m[0], m[1], E]):
+            for b in range(2):
+                G = Q[4 + 2 * pi + b]
+                rows.append(torch.stack([G * u[c] - (V / self.tau_grad if b == c else 0 * V)
+                                         for c in range(2)]))
+        return torch.stack(rows)
+
+    def source(self, Q):
+        S = torch.zeros_like(Q)
+        S[4:] = -Q[4:] / self.tau_grad
+        return S
+
+    def parents(self, Qc):
+        return [Qc[0], Qc[1], Qc[2], Qc[3]]
+
+    def trackers_from_grads(self, dP):
+        return [dP[p][b] for p in range(4) for b in range(2)]
+
+
+class MhdPowell2D(System):
+    """2D viscous, heat-conducting resistive MHD with Powell divergence cleaning, the
+    paper's own 18-component cascade (Sec. 3, MHD system; supplement, MHD system):
+    trackers of rho, rho u, E and B, the chain rule for grad u and grad T (T = p / rho),
+    and div B = tr G_B in the Powell source.
+
+    Q = (rho, m_x, m_y, E, B_x, B_y, G_rho(2), G_mx(2), G_my(2), G_E(2), G_Bx(2), G_By(2)).
+    p = (gamma-1)(E - |m|^2/(2 rho) - |B|^2/2), p_t = p + |B|^2/2,
+    grad p = (gamma-1)(G_E - u . G_m + |u|^2/2 G_rho - B . G_B), grad T = (grad p - T G_rho)/rho,
+    j_z = G_{By,x} - G_{Bx,y}, j x B = (-j_z B_y, j_z B_x),
+    Phi_m = m (x) u + p_t I - B (x) B - tau_v,
+    Phi_E = (E + p_t) u - B (u . B) - tau_v u - K grad T + eta (j x B),
+    Phi_B = B (x) u - u (x) B - eta G_B,  S = -(div B) (0, B, u . B, u) on (rho, m, E, B).
+    """
+    name = "mhd18"
+    K = 18
+    D = 2
+    n_cons = 6
+
+    def __init__(self, gamma, mu, kappa, eta, tau_grad):
+        self.gamma, self.mu, self.kappa, self.eta = float(gamma), float(mu), float(kappa), float(eta)
+        self.tau_grad = float(tau_grad)
+
+    def _parts(self, Q):
+        g1 = self.gamma - 1.0
+        rho, m, E, B = Q[0], Q[1:3], Q[3], Q[4:6]
+        u = m / rho
+        u2 = u[0] * u[0] + u[1] * u[1]
+        b2 = B[0] * B[0] + B[1] * B[1]
+        p = g1 * (E - 0.5 * rho * u2 - 0.5 * b2)
+        return rho, m, E, B, u, u2, b2, p
+
+    def flux(self, Q):
+        g1 = self.gamma - 1.0
+        rho, m, E, B, u, u2, b2, p = self._parts(Q)
+        pt = p + 0.5 * b2
+        T = p / rho
+        Gr, Gm, GE, GB = Q[6:8], [Q[8:10], Q[10:12]], Q[12:14], [Q[14:16], Q[16:18]]
+        L = [[(Gm[a][b] - u[a] * Gr[b]) / rho for b in range(2)] for a in range(2)]
+        Gp = [g1 * (GE[b] - (u[0] * Gm[0][b] + u[1] * Gm[1][b]) + 0.5 * u2 * Gr[b]
+                    - (B[0] * GB[0][b] + B[1] * GB[1][b])) for b in range(2)]
+        GT = [(Gp[b] - T * Gr[b]) / rho for b in range(2)]
+        div = L[0][0] + L[1][1]
+        tv = [[self.mu * (L[a][b] + L[b][a] - (2.0 / 3.0) * div * (1.0 if a == b else 0.0))
+               for b in range(2)] for a in range(2)]
+        jz = GB[1][0] - GB[0][1]
+        jxB = [-jz * B[1], jz * B[0]]
+        uB = u[0] * B[0] + u[1] * B[1]
+        rows = [torch.stack([m[0], m[1]])]
+        for a in range(2):
+            rows.append(torch.stack([m[a] * u[b] + (pt if a == b else 0 * pt) - B[a] * B[b] - tv[a][b]
+                                     for b in range(2)]))
+        rows.append(torch.stack([(E + pt) * u[b] - B[b] * uB - (tv[b][0] * u[0] + tv[b][1] * u[1])
+                                 - self.kappa * GT[b] + self.eta * jxB[b] for b in range(2)]))
+        for a in range(2):
+            rows.append(torch.stack([B[a] * u[b] - u[a] * B[b] - self.eta * GB[a][b] for b in range(2)]))
+        for pi, V in enumerate([rho, m[0], m[1], E, B[0], B[1]]):
+            for b in range(2):
+                G = Q[6 + 2 * pi + b]
+                rows.append(torch.stack([G * u[c] - (V / self.tau_grad if b == c else 0 * V)
+                                         for c in range(2)]))
+        return torch.stack(rows)
+
+    def source(self, Q):
+        rho, m, E, B, u, u2, b2, p = self._parts(Q)
+        divB = Q[14] + Q[17]
+        S = torch.zeros_like(Q)
+        S[1], S[2] = -divB * B[0], -divB * B[1]
+        S[3] = -divB * (u[0] * B[0] + u[1] * B[1])
+        S[4], S[5] = -divB * u[0], -divB * u[1]
+        S[6:] = -Q[6:] / self.tau_grad
+        return S
+
+    def parents(self, Qc):
+        return [Qc[k] for k in range(6)]
+
+    def trackers_from_grads(self, dP):
+        return [dP[p][b] for p in range(6) for b in range(2)]
+
+
 class Burgers(System):
     """Inviscid Burgers, Sec. 3: Phi = (u^2/2, u^2/2) (and u^2/2 in 1D)."""
     name = "burgers"

@@ -206,6 +206,7 @@ def test_tracker_steady_states_recover_gradient_and_curl():
 CASES = [
     ("adr", "D2Q5"), ("adr", "D2Q9"), ("nsf", "D2Q9"), ("nsf", "D2Q5"), ("mhd", "D3Q19"),
     ("mhd", "D3Q7"), ("burgers", "D2Q5"), ("euler", "D2Q5"), ("maxwell", "D2Q5"),
+    ("nsf12", "D2Q5"), ("nsf12", "D2Q9"), ("mhd18", "D2Q5"), ("mhd18", "D2Q9"),
 ]
 
 
@@ -214,14 +215,16 @@ def _system(name):
             "nsf": lambda: S.NsfPrimitive(1.4, 1.0, 0.02, 0.07, 0.3),
             "mhd": lambda: S.MhdCurrent(1.4, 0.01, 0.3),
             "burgers": lambda: S.Burgers(), "euler": lambda: S.Euler(1.4),
-            "maxwell": lambda: S.MaxwellTM(1.0)}[name]()
+            "maxwell": lambda: S.MaxwellTM(1.0),
+            "nsf12": lambda: S.NsfConservedGradients(1.4, 1.0, 0.02, 0.07, 0.3),
+            "mhd18": lambda: S.MhdPowell2D(1.4, 0.01, 0.01, 0.01, 0.3)}[name]()
 
 
 def _positive_state(sysm, n, seed):
     Q = 0.1 * _rand_state(sysm, n, seed)
-    if sysm.name in ("nsf", "euler", "mhd"):
+    if sysm.name in ("nsf", "euler", "mhd", "nsf12", "mhd18"):
         Q[0] += 1.0
-        Q[3 if sysm.name != "mhd" else 7] += 3.0
+        Q[7 if sysm.name == "mhd" else 3] += 3.0
     return Q
 
 
@@ -520,3 +523,134 @@ def test_oracle_adjoint_matches_central_differences():
     fdt = (oracle.adjoint.misfit(make, Q, target, steps, tau0 + h)
            - oracle.adjoint.misfit(make, Q, target, steps, tau0 - h)) / (2 * h)
     assert abs(fdt - gt) <= 1e-6 * abs(fdt)
+
+
+# ------------------------------------------------- the paper's own cascades (12 and 18)
+
+def _uniform_draws(seed, n=9):
+    gen = torch.Generator().manual_seed(seed)
+    return lambda lo, hi: lo + (hi - lo) * torch.rand(n, generator=gen, dtype=F64)
+
+
+def test_nsf12_flux_and_source_match_the_paper_expanded_system():
+    """Supplement, NSF system (N = 12): every flux component Phi_{i,j} and source S_i of the
+    fully expanded listing, evaluated at random states, against NsfConservedGradients."""
+    g, R, mu, K, tg = 1.4, 0.8, 0.03, 0.05, 0.37
+    sysm = S.NsfConservedGradients(g, R, mu, K, tau_grad=tg)
+    rnd = _uniform_draws(11)
+    r, m0, m1, E = rnd(0.8, 1.2), rnd(-0.5, 0.5), rnd(-0.5, 0.5), rnd(2.0, 3.0)
+    G0r, G1r, G00, G01, G10, G11, GE0, GE1 = (rnd(-1, 1) for _ in range(8))
+    # our order: rho, m0, m1, E, G_rho(0,1), G_m0(0,1), G_m1(0,1), G_E(0,1)
+    Q = torch.stack([r, m0, m1, E, G0r, G1r, G00, G01, G10, G11, GE0, GE1])
+    Phi, Src = sysm.flux(Q), sysm.source(Q)
+    exp10 = (E * g - E + 4 * G0r * mu * m0 / (3 * r ** 2) - 2 * G1r * mu * m1 / (3 * r ** 2)
+             - 4 * G00 * mu / (3 * r) + 2 * G11 * mu / (3 * r) - g * m0 ** 2 / (2 * r)
+             - g * m1 ** 2 / (2 * r) + 3 * m0 ** 2 / (2 * r) + m1 ** 2 / (2 * r))
+    exp11 = G0r * mu * m1 / r ** 2 + G1r * mu * m0 / r ** 2 - G01 * mu / r - G10 * mu / r + m0 * m1 / r
+    exp21 = (E * g - E - 2 * G0r * mu * m0 / (3 * r ** 2) + 4 * G1r * mu * m1 / (3 * r ** 2)
+             + 2 * G00 * mu / (3 * r) - 4 * G11 * mu / (3 * r) - g * m0 ** 2 / (2 * r)
+             - g * m1 ** 2 / (2 * r) + m0 ** 2 / (2 * r) + 3 * m1 ** 2 / (2 * r))
+    exp30 = (E * G0r * K * g / (R * r ** 2) - E * G0r * K / (R * r ** 2) + E * g * m0 / r
+             - GE0 * K * g / (R * r) + GE0 * K / (R * r) - G0r * K * g * m0 ** 2 / (R * r ** 3)
+             - G0r * K * g * m1 ** 2 / (R * r ** 3) + G0r * K * m0 ** 2 / (R * r ** 3)
+             + G0r * K * m1 ** 2 / (R * r ** 3) + 4 * G0r * mu * m0 ** 2 / (3 * r ** 3)
+             + G0r * mu * m1 ** 2 / r ** 3 + G1r * mu * m0 * m1 / (3 * r ** 3)
+             + G00 * K * g * m0 / (R * r ** 2) - G00 * K * m0 / (R * r ** 2)
+             - 4 * G00 * mu * m0 / (3 * r ** 2) - G01 * mu * m1 / r ** 2
+             + G10 * K * g * m1 / (R * r ** 2) - G10 * K * m1 / (R * r ** 2)
+             - G10 * mu * m1 / r ** 2 + 2 * G11 * mu * m0 / (3 * r ** 2)
+             - g * m0 ** 3 / (2 * r ** 2) - g * m0 * m1 ** 2 / (2 * r ** 2) + m0 ** 3 / (2 * r ** 2)
+             + m0 * m1 ** 2 / (2 * r ** 2))
+    exp31 = (E * G1r * K * g / (R * r ** 2) - E * G1r * K / (R * r ** 2) + E * g * m1 / r
+             - GE1 * K * g / (R * r) + GE1 * K / (R * r) + G0r * mu * m0 * m1 / (3 * r ** 3)
+             - G1r * K * g * m0 ** 2 / (R * r ** 3) - G1r * K * g * m1 ** 2 / (R * r ** 3)
+             + G1r * K * m0 ** 2 / (R * r ** 3) + G1r * K * m1 ** 2 / (R * r ** 3)
+             + G1r * mu * m0 ** 2 / r ** 3 + 4 * G1r * mu * m1 ** 2 / (3 * r ** 3)
+             + 2 * G00 * mu * m1 / (3 * r ** 2) + G01 * K * g * m0 / (R * r ** 2)
+             - G01 * K * m0 / (R * r ** 2) - G01 * mu * m0 / r ** 2
+             - G10 * mu * m0 / r ** 2 + G11 * K * g * m1 / (R * r ** 2)
+             - G11 * K * m1 / (R * r ** 2) - 4 * G11 * mu * m1 / (3 * r ** 2)
+             - g * m0 ** 2 * m1 / (2 * r ** 2) - g * m1 ** 3 / (2 * r ** 2)
+             + m0 ** 2 * m1 / (2 * r ** 2) + m1 ** 3 / (2 * r ** 2))
+    want = {(0, 0): m0, (0, 1): m1, (1, 0): exp10, (1, 1): exp11, (2, 0): exp11, (2, 1): exp21,
+            (3, 0): exp30, (3, 1): exp31}
+    # trackers: G of V in direction c: G u_c - delta V / tau  (paper Phi_{4..11})
+    for k, (Gk, V, b) in enumerate([(G0r, r, 0), (G1r, r, 1), (G00, m0, 0), (G01, m0, 1),
+                                    (G10, m1, 0), (G11, m1, 1), (GE0, E, 0), (GE1, E, 1)]):
+        for c, mc in enumerate((m0, m1)):
+            want[(4 + k, c)] = Gk * mc / r - (V / tg if b == c else 0.0)
+        torch.testing.assert_close(Src[4 + k], -Gk / tg, rtol=1e-13, atol=1e-14)
+    for (i, j), v in want.items():
+        torch.testing.assert_close(Phi[i, j], v, rtol=1e-12, atol=1e-12)
+    assert float(Src[:4].abs().max()) == 0.0
+
+
+def test_mhd18_flux_and_source_match_the_paper_expanded_system():
+    """Supplement, resistive MHD system (N = 18, T = p/rho): the expanded momentum, energy and
+    induction fluxes and the Powell sources, at random states, against MhdPowell2D."""
+    g, mu, K, eta, tg = 1.4, 0.03, 0.05, 0.07, 0.29
+    sysm = S.MhdPowell2D(g, mu, K, eta, tau_grad=tg)
+    rnd = _uniform_draws(12)
+    r, m0, m1, E, B0, B1 = rnd(0.8, 1.2), rnd(-0.5, 0.5), rnd(-0.5, 0.5), rnd(3.0, 4.0), rnd(-.6, .6), rnd(-.6, .6)
+    G0r, G1r, G00, G01, G10, G11, GE0, GE1, GB00, GB01, GB10, GB11 = (rnd(-1, 1) for _ in range(12))
+    Q = torch.stack([r, m0, m1, E, B0, B1, G0r, G1r, G00, G01, G10, G11, GE0, GE1, GB00, GB01, GB10, GB11])
+    Phi, Src = sysm.flux(Q), sysm.source(Q)
+    exp10 = (-B0 ** 2 * g / 2 - B1 ** 2 * g / 2 + B1 ** 2 + E * g - E + 4 * G0r * mu * m0 / (3 * r ** 2)
+             - 2 * G1r * mu * m1 / (3 * r ** 2) - 4 * G00 * mu / (3 * r) + 2 * G11 * mu / (3 * r)
+             - g * m0 ** 2 / (2 * r) - g * m1 ** 2 / (2 * r) + 3 * m0 ** 2 / (2 * r) + m1 ** 2 / (2 * r))
+    exp11 = (-B0 * B1 + G0r * mu * m1 / r ** 2 + G1r * mu * m0 / r ** 2 - G01 * mu / r - G10 * mu / r
+             + m0 * m1 / r)
+    exp21 = (-B0 ** 2 * g / 2 + B0 ** 2 - B1 ** 2 * g / 2 + E * g - E - 2 * G0r * mu * m0 / (3 * r ** 2)
+             + 4 * G1r * mu * m1 / (3 * r ** 2) + 2 * G00 * mu / (3 * r) - 4 * G11 * mu / (3 * r)
+             - g * m0 ** 2 / (2 * r) - g * m1 ** 2 / (2 * r) + m0 ** 2 / (2 * r) + 3 * m1 ** 2 / (2 * r))
+    exp30 = (-B0 ** 2 * G0r * K * g / (2 * r ** 2) + B0 ** 2 * G0r * K / (2 * r ** 2)
+             - B0 ** 2 * g * m0 / (2 * r) - B0 * B1 * m1 / r + B0 * GB00 * K * g / r
+             - B0 * GB00 * K / r - B1 ** 2 * G0r * K * g / (2 * r ** 2) + B1 ** 2 * G0r * K / (2 * r ** 2)
+             - B1 ** 2 * g * m0 / (2 * r) + B1 ** 2 * m0 / r + B1 * GB01 * eta
+             + B1 * GB10 * K * g / r - B1 * GB10 * K / r - B1 * GB10 * eta
+             + E * G0r * K * g / r ** 2 - E * G0r * K / r ** 2 + E * g * m0 / r
+             - GE0 * K * g / r + GE0 * K / r - G0r * K * g * m0 ** 2 / r ** 3
+             - G0r * K * g * m1 ** 2 / r ** 3 + G0r * K * m0 ** 2 / r ** 3
+             + G0r * K * m1 ** 2 / r ** 3 + 4 * G0r * mu * m0 ** 2 / (3 * r ** 3)
+             + G0r * mu * m1 ** 2 / r ** 3 + G1r * mu * m0 * m1 / (3 * r ** 3)
+             + G00 * K * g * m0 / r ** 2 - G00 * K * m0 / r ** 2
+             - 4 * G00 * mu * m0 / (3 * r ** 2) - G01 * mu * m1 / r ** 2
+             + G10 * K * g * m1 / r ** 2 - G10 * K * m1 / r ** 2
+             - G10 * mu * m1 / r ** 2 + 2 * G11 * mu * m0 / (3 * r ** 2)
+             - g * m0 ** 3 / (2 * r ** 2) - g * m0 * m1 ** 2 / (2 * r ** 2) + m0 ** 3 / (2 * r ** 2)
+             + m0 * m1 ** 2 / (2 * r ** 2))
+    exp31 = (-B0 ** 2 * G1r * K * g / (2 * r ** 2) + B0 ** 2 * G1r * K / (2 * r ** 2)
+             - B0 ** 2 * g * m1 / (2 * r) + B0 ** 2 * m1 / r - B0 * B1 * m0 / r
+             + B0 * GB01 * K * g / r - B0 * GB01 * K / r - B0 * GB01 * eta + B0 * GB10 * eta
+             - B1 ** 2 * G1r * K * g / (2 * r ** 2) + B1 ** 2 * G1r * K / (2 * r ** 2)
+             - B1 ** 2 * g * m1 / (2 * r) + B1 * GB11 * K * g / r - B1 * GB11 * K / r
+             + E * G1r * K * g / r ** 2 - E * G1r * K / r ** 2 + E * g * m1 / r
+             - GE1 * K * g / r + GE1 * K / r + G0r * mu * m0 * m1 / (3 * r ** 3)
+             - G1r * K * g * m0 ** 2 / r ** 3 - G1r * K * g * m1 ** 2 / r ** 3
+             + G1r * K * m0 ** 2 / r ** 3 + G1r * K * m1 ** 2 / r ** 3
+             + G1r * mu * m0 ** 2 / r ** 3 + 4 * G1r * mu * m1 ** 2 / (3 * r ** 3)
+             + 2 * G00 * mu * m1 / (3 * r ** 2) + G01 * K * g * m0 / r ** 2
+             - G01 * K * m0 / r ** 2 - G01 * mu * m0 / r ** 2
+             - G10 * mu * m0 / r ** 2 + G11 * K * g * m1 / r ** 2
+             - G11 * K * m1 / r ** 2 - 4 * G11 * mu * m1 / (3 * r ** 2)
+             - g * m0 ** 2 * m1 / (2 * r ** 2) - g * m1 ** 3 / (2 * r ** 2)
+             + m0 ** 2 * m1 / (2 * r ** 2) + m1 ** 3 / (2 * r ** 2))
+    want = {(0, 0): m0, (0, 1): m1, (1, 0): exp10, (1, 1): exp11, (2, 0): exp11, (2, 1): exp21,
+            (3, 0): exp30, (3, 1): exp31,
+            (4, 0): -GB00 * eta, (4, 1): B0 * m1 / r - B1 * m0 / r - GB01 * eta,
+            (5, 0): -B0 * m1 / r + B1 * m0 / r - GB10 * eta, (5, 1): -GB11 * eta}
+    for (i, j), v in want.items():
+        torch.testing.assert_close(Phi[i, j], v, rtol=1e-12, atol=1e-12)
+    div = GB00 + GB11
+    torch.testing.assert_close(Src[1], -B0 * GB00 - B0 * GB11, rtol=1e-13, atol=1e-14)
+    torch.testing.assert_close(Src[2], -B1 * GB00 - B1 * GB11, rtol=1e-13, atol=1e-14)
+    torch.testing.assert_close(Src[3], -div * (B0 * m0 + B1 * m1) / r, rtol=1e-13, atol=1e-14)
+    torch.testing.assert_close(Src[4], -div * m0 / r, rtol=1e-13, atol=1e-14)
+    torch.testing.assert_close(Src[5], -div * m1 / r, rtol=1e-13, atol=1e-14)
+    assert float(Src[0].abs().max()) == 0.0
+    for k, (Gk, V, b) in enumerate([(G0r, r, 0), (G1r, r, 1), (G00, m0, 0), (G01, m0, 1), (G10, m1, 0),
+                                    (G11, m1, 1), (GE0, E, 0), (GE1, E, 1), (GB00, B0, 0), (GB01, B0, 1),
+                                    (GB10, B1, 0), (GB11, B1, 1)]):
+        for c, mc in enumerate((m0, m1)):
+            torch.testing.assert_close(Phi[6 + k, c], Gk * mc / r - (V / tg if b == c else 0.0), rtol=1e-12, atol=1e-12)
+        torch.testing.assert_close(Src[6 + k], -Gk / tg, rtol=1e-13, atol=1e-14)
