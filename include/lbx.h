@@ -54,6 +54,13 @@ typedef enum {
  *   NSF_PRIM_TRACK   (rho, m_x, m_y, E, G_u(2), G_v(2), G_T(2))           K = 10, 2D
  *   MHD_J_TRACK      (rho, m(3), B(3), E, j(3))                           K = 11, 3D
  *   BURGERS (u), EULER (rho, m_x, m_y, E), MAXWELL_TM (E_z, H_x, H_y)     2D
+ *   NSF_CONS_TRACK   (rho, m_x, m_y, E, G_rho(2), G_mx(2), G_my(2), G_E(2))       K = 12, 2D
+ *                    the paper's own cascade: trackers of the conserved fields, the chain
+ *                    rule for grad u and grad T (Sec. 2.1.1)
+ *   MHD_POWELL_2D    (rho, m_x, m_y, E, B_x, B_y, G_rho(2), G_mx(2), G_my(2), G_E(2),
+ *                     G_Bx(2), G_By(2))                                         K = 18, 2D
+ *                    the paper's own MHD: viscous, heat-conducting (T = p/rho), resistive,
+ *                    Powell source -(tr G_B)(0, B, u.B, u)
  * Trackers G_{V,b} ~ dV/dx_b follow Eq. gradient_advection with tau_grad = g_tau dt. */
 typedef enum {
     LBX_ADR_CASCADE = 1,
@@ -61,7 +68,9 @@ typedef enum {
     LBX_MHD_J_TRACK = 3,
     LBX_BURGERS = 4,
     LBX_EULER = 5,
-    LBX_MAXWELL_TM = 6
+    LBX_MAXWELL_TM = 6,
+    LBX_NSF_CONS_TRACK = 7,
+    LBX_MHD_POWELL_2D = 8
 } lbx_family;
 
 typedef enum { LBX_D2Q5 = 1, LBX_D2Q9 = 2, LBX_D3Q7 = 3, LBX_D3Q19 = 4 } lbx_lattice;
@@ -80,7 +89,7 @@ typedef enum { LBX_FP64 = 1, LBX_FP32_SHIFT = 2, LBX_FP16_SCALED = 3 } lbx_preci
  * conserved components at t + dt/2 (node coordinates x = (i, j, l) dx, dx = 1/nx):
  *   NONE          no forcing;
  *   ADR_SEPARABLE u_ex = 1 + A sin(2 pi x) cos(2 pi y) exp(-t) for the ADR cascade with
- *                 R = 0; mms_amp = A;
+ *                 R = 0; mms_amp = A; closed form, conserved component only;
  *   FOURIER       every primitive field V_p of the family is mms_mean[p] plus a sum of
  *                 modes (lbx_mms_mode, at most LBX_MMS_MAX_MODES).  The exact augmented
  *                 state is assembled from the primitives and their derivatives, and S_MMS
@@ -94,10 +103,20 @@ typedef enum { LBX_FP64 = 1, LBX_FP32_SHIFT = 2, LBX_FP16_SCALED = 3 } lbx_preci
  *                   MHD (rho, u_x, u_y, u_z, B_x, B_y, B_z, p)
  *                                                    Q = (rho, rho u, B, p/(gamma-1) +
  *                                                        rho|u|^2/2 + |B|^2/2, curl B)
+ *                   NSF_CONS_TRACK (rho, u, v, p)    as NSF, trackers grad rho, grad(rho u),
+ *                                                        grad(rho v), grad E
+ *                   MHD_POWELL_2D (rho, u, v, p, B_x, B_y)
+ *                                                    Q = (rho, rho u, rho v, p/(gamma-1) +
+ *                                                        rho|u|^2/2 + |B|^2/2, B, gradients
+ *                                                        of the six conserved fields)
  *                   BURGERS (u), MAXWELL_TM (E_z, H_x, H_y): Q = V
  *                   EULER (rho, u, v, p)             Q = (rho, rho u, rho v,
  *                                                        p/(gamma-1) + rho|u|^2/2)
- *                 The table is copied by lbx_scheme_derive. */
+ *                 S_MMS is the residual of the whole augmented state (the paper's Sec. 4
+ *                 definition on Q+): each tracker is forced with d_t G_ex + div Phi_G(Q_ex)
+ *                 - S_G(Q_ex), G_ex its exact gradient (or curl B), so it carries no
+ *                 relaxation lag; mms_conserved_only = 1 forces the conserved components
+ *                 alone.  The table is copied by lbx_scheme_derive. */
 typedef enum { LBX_MMS_NONE = 0, LBX_MMS_ADR_SEPARABLE = 1, LBX_MMS_FOURIER = 2 } lbx_mms;
 
 #define LBX_MMS_MAX_MODES 64
@@ -115,10 +134,11 @@ typedef struct {
      *   ADR_CASCADE  {a_x, a_y, nu, R}
      *   NSF          {gamma, R_gas, mu, kappa}
      *   MHD          {gamma, eta}
-     *   BURGERS      {}            EULER {gamma}            MAXWELL_TM {c}            */
+     *   BURGERS      {}            EULER {gamma}            MAXWELL_TM {c}
+     *   NSF_CONS_TRACK {gamma, R_gas, mu, kappa}   MHD_POWELL_2D {gamma, mu, kappa, eta} */
     double params[8];
     /* Reference (background) state Q0 [K] for the shifted storage modes; F0 = Phi(Q0). */
-    double Q0[16];
+    double Q0[24];
 } lbx_system_desc;
 
 typedef struct {
@@ -136,6 +156,7 @@ typedef struct {
     const lbx_mms_mode* mms_modes; /* FOURIER: the mode table (read during the call)    */
     int mms_n_modes;       /* FOURIER: 1 .. LBX_MMS_MAX_MODES                           */
     double mms_mean[8];    /* FOURIER: mean of each primitive                           */
+    int mms_conserved_only; /* FOURIER: nonzero leaves the tracker components unforced */
 } lbx_scheme_desc;
 
 typedef struct lbx_system lbx_system;
@@ -337,7 +358,7 @@ lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, int64_t n_st
  * value a call reads is written earlier in the same call, so nothing is cleared); calls
  * whose work overlaps on the GPU race on it and must be ordered, e.g. on one stream. */
 #define LBX_STATIC_REDUCE_MAX_BLOCKS 512
-#define LBX_STATIC_REDUCE_SCRATCH_DOUBLES (LBX_STATIC_REDUCE_MAX_BLOCKS * 11 * 4 + 11 * 4)
+#define LBX_STATIC_REDUCE_SCRATCH_DOUBLES (LBX_STATIC_REDUCE_MAX_BLOCKS * 18 * 4 + 18 * 4)
 lbx_status lbx_conserved_sums_static(const lbx_scheme* sch, const void* populations, double* sums,
                                      int nblocks, void* stream);
 

@@ -4,7 +4,12 @@ The derivatives are taken by forward-mode automatic differentiation of the exact
 fields (torch.func.jvp), so no derivative is written by hand.  Tracker components of
 the exact augmented state are the exact gradients of their parent fields (supplement,
 MMS section: trackers are initialised from the spatial derivatives of the fields).
-The forcing is applied to the conserved components only.
+
+By default the forcing is the residual of the whole augmented state Q+ (conserved and
+tracker components), as the paper's compiler forms it on Q+ (Sec. 4: the residual of the
+analytical profiles, injected into the update); for a tracker the 1/tau_grad terms of
+flux and source cancel and its forcing is d_t grad V + div(grad V (x) u).  With
+`conserved_only` the trackers are left unforced (they then lag grad V by O(tau_grad)).
 """
 from __future__ import annotations
 
@@ -37,20 +42,20 @@ def exact_augmented(system, exact, xx, t):
     return torch.cat([Qc, torch.stack(system.trackers_from_grads(dP))])
 
 
-def mms_source(system, exact, xx, t):
-    """S_MMS(x, t) for the conserved components, [n_cons, *grid]."""
+def mms_source(system, exact, xx, t, conserved_only=False):
+    """S_MMS(x, t), [K, *grid] ([n_cons, *grid] with conserved_only)."""
     tt = torch.full_like(xx[0], float(t))
-    return mms_source_t(system, exact, xx, tt)
+    return mms_source_t(system, exact, xx, tt, conserved_only)
 
 
-def make_mms(system, exact, xx, dt=None, chunk=64):
+def make_mms(system, exact, xx, dt=None, chunk=64, conserved_only=False):
     """Callable t -> S_MMS(x, t) on the fixed node coordinates xx.
 
     With a time step `dt`, the forcing is evaluated for `chunk` consecutive instants
     t, t + dt, ... at once (the same definition, batched along a leading time axis to
     amortise the differentiation overhead) and served from that cache."""
     if dt is None:
-        return lambda t: mms_source(system, exact, xx, t)
+        return lambda t: mms_source(system, exact, xx, t, conserved_only)
     cache = {"t0": None, "vals": None}
 
     def fn(t):
@@ -63,21 +68,21 @@ def make_mms(system, exact, xx, dt=None, chunk=64):
         shp = (chunk,) + tuple(xx[0].shape)
         tb = ts.reshape((chunk,) + (1,) * xx[0].dim()).expand(shp).contiguous()
         xb = tuple(x.unsqueeze(0).expand(shp).contiguous() for x in xx)
-        vals = mms_source_t(system, exact, xb, tb)            # [n_cons, chunk, *grid]
+        vals = mms_source_t(system, exact, xb, tb, conserved_only)   # [K or n_cons, chunk, *grid]
         cache["t0"], cache["vals"] = t, vals.transpose(0, 1).contiguous()
         return cache["vals"][0]
     return fn
 
 
-def mms_source_t(system, exact, xx, tt):
+def mms_source_t(system, exact, xx, tt, conserved_only=False):
     """S_MMS with a time tensor tt of the same shape as the coordinates."""
-    nc = system.n_cons
-    _, dQdt = jvp(lambda T: exact(*xx, T), (tt,), (torch.ones_like(tt),))
+    nk = system.n_cons if conserved_only else system.K
+    _, dQdt = jvp(lambda T: exact_augmented(system, exact, xx, T)[:nk], (tt,), (torch.ones_like(tt),))
     div = torch.zeros_like(dQdt)
     for b in range(len(xx)):
         def flux_b(xb, b=b):
-            return system.flux(exact_augmented(system, exact, _replace(xx, b, xb), tt))[:nc, b]
+            return system.flux(exact_augmented(system, exact, _replace(xx, b, xb), tt))[:nk, b]
         _, d = jvp(flux_b, (xx[b],), (torch.ones_like(xx[b]),))
         div = div + d
     Qp = exact_augmented(system, exact, xx, tt)
-    return dQdt + div - system.source(Qp)[:nc]
+    return dQdt + div - system.source(Qp)[:nk]

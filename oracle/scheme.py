@@ -100,8 +100,8 @@ class Scheme:
     def source_total(self, Q, t):
         S = self.sys.source(Q)
         if self.mms is not None:
-            Sm = self.mms(t + 0.5 * self.dt)
-            S = torch.cat([S[: self.sys.n_cons] + Sm, S[self.sys.n_cons:]])
+            Sm = self.mms(t + 0.5 * self.dt)          # all K components, or the conserved ones
+            S = S + Sm if Sm.shape[0] == self.sys.K else torch.cat([S[: self.sys.n_cons] + Sm, S[self.sys.n_cons:]])
         return S
 
     def collide(self, f, t):

@@ -57,6 +57,7 @@ struct KParams {
   T dx;                        // node spacing (coordinates of the manufactured fields)
   const MmsMode* mms_modes;    // FOURIER forcing table; null = off
   int mms_n;
+  int mms_trackers;            // nonzero: the tracker components are forced as well
   T mms_mean[8];               // mean of each primitive
 };
 
@@ -165,7 +166,7 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
   constexpr int K = SysD::K, NC = SysD::NC, NP = SysD::NPRIM, D = Lat::D;
   const T t = (T(step) + T(0.5)) * p.dt;
   const T xc[3] = {T(x) * p.dx, T(y) * p.dx, T(z) * p.dx};
-  T V[NP], Vt[NP], G[NP][3], H[NP][3][3];
+  T V[NP], Vt[NP], G[NP][3], Gt[NP][3], H[NP][3][3];
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     V[q] = p.mms_mean[q];
@@ -173,6 +174,7 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       G[q][b] = T(0);
+      Gt[q][b] = T(0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) H[q][b][c] = T(0);
     }
@@ -197,6 +199,7 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
 #pragma unroll
       for (int b = 0; b < D; ++b) {
         G[q][b] += a * cs * k[b] * g;
+        Gt[q][b] += a * cs * k[b] * gt;
 #pragma unroll
         for (int c = 0; c < D; ++c) H[q][b][c] -= a * sn * k[b] * k[c] * g;
       }
@@ -208,17 +211,17 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
 #pragma unroll
   for (int k2 = 0; k2 < K; ++k2) q0[k2] = D1(p.Q0[k2], T(0));
   D1 Vd[NP], Gd[NP][3], Qd[K];
-  // d/dt of the conserved components
+  // d/dt of the exact augmented state
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     Vd[q] = D1(V[q], Vt[q]);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) Gd[q][b] = D1(G[q][b], T(0));
+    for (int b = 0; b < 3; ++b) Gd[q][b] = D1(G[q][b], Gt[q][b]);
   }
   SysD::augment(pd, Vd, Gd, Qd);
-  T acc[NC];
+  T acc[K];
 #pragma unroll
-  for (int k2 = 0; k2 < NC; ++k2) acc[k2] = Qd[k2].d;
+  for (int k2 = 0; k2 < K; ++k2) acc[k2] = Qd[k2].d;
   // divergence of the flux and the state source
 #pragma unroll 1
   for (int b = 0; b < D; ++b) {
@@ -234,10 +237,14 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
     for (int k2 = 0; k2 < K; ++k2) dQd[k2] = Qd[k2] - q0[k2];
     SysD::eval(pd, q0, dQd, Phi, S);
 #pragma unroll
-    for (int k2 = 0; k2 < NC; ++k2) acc[k2] += Phi[k2][b].d - (b == 0 ? S[k2].v : T(0));
+    for (int k2 = 0; k2 < K; ++k2) acc[k2] += Phi[k2][b].d - (b == 0 ? S[k2].v : T(0));
   }
 #pragma unroll
   for (int k2 = 0; k2 < NC; ++k2) Src[k2] += acc[k2];
+  if (p.mms_trackers) {
+#pragma unroll
+    for (int k2 = NC; k2 < K; ++k2) Src[k2] += acc[k2];
+  }
 }
 
 // --------------------------------------------------------------------------- the step
@@ -252,9 +259,13 @@ constexpr int MODE_REG = 0, MODE_SMEM = 1;
 // COLS: threads per block of a staged launch (the column stride of its layout).
 template <class Lat, template <typename> class SysT, class St, int COLS = 128>
 struct StepMode {
-  // register-resident or per-thread staged (also the batched kernel's choice)
+  // register-resident or per-thread staged (also the batched kernel's choice): registers
+  // hold up to 360 bytes of populations for systems of at most 12 components; larger
+  // systems need the registers for their flux (18 components on D2Q5 spill at 128)
   static constexpr int value =
-      (size_t)SysT<typename St::C>::K * Lat::Q * sizeof(typename St::C) <= 360 ? MODE_REG : MODE_SMEM;
+      ((size_t)SysT<typename St::C>::K * Lat::Q * sizeof(typename St::C) <= 360 && SysT<typename St::C>::K <= 12)
+          ? MODE_REG
+          : MODE_SMEM;
   static constexpr size_t smem_per_thread = (size_t)SysT<typename St::C>::K * Lat::Q * sizeof(typename St::S);
   static constexpr size_t smem_bytes = value == MODE_SMEM ? smem_per_thread * COLS : 0;
   // blocks per SM the launch bounds ask the register allocator to allow: 4 for
@@ -1070,7 +1081,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename St::S* __
   }
 }
 
-// Sum (or max) the partials of `nblk` blocks in block order: out[k][4].
+// Sum (or max) the partials of `nblk` blocks in block order: out[k][4], one thread per
+// (component, statistic).
+constexpr int RED_FINAL_THREADS = ((KMAX * 4 + 31) / 32) * 32;
 static __global__ void k_reduce_final(const double* __restrict__ partials, int nblk, int K, int mode,
                                double* __restrict__ out) {
   const int t = threadIdx.x;

@@ -81,6 +81,9 @@ bool find_adj(int family, int lattice, int precision, AdjOps* o) {
     case LBX_MAXWELL_TM:
       if (lattice == LBX_D2Q5) return pick<LatD2Q5, SysMaxwell>(precision, o);
       return false;
+    case LBX_NSF_CONS_TRACK:
+      if (lattice == LBX_D2Q5) return pick<LatD2Q5, SysNSF12>(precision, o);
+      return false;
   }
   return false;
 }

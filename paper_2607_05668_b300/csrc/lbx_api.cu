@@ -43,6 +43,8 @@ static int family_K(int f) {
     case LBX_BURGERS: return 1;
     case LBX_EULER: return 4;
     case LBX_MAXWELL_TM: return 3;
+    case LBX_NSF_CONS_TRACK: return 12;
+    case LBX_MHD_POWELL_2D: return 18;
   }
   return 0;
 }
@@ -51,6 +53,8 @@ static int family_NC(int f) {
     case LBX_ADR_CASCADE: return 1;
     case LBX_NSF_PRIM_TRACK: return 4;
     case LBX_MHD_J_TRACK: return 8;
+    case LBX_NSF_CONS_TRACK: return 4;
+    case LBX_MHD_POWELL_2D: return 6;
     default: return family_K(f);
   }
 }
@@ -64,6 +68,8 @@ static int family_nprim(int f) {
     case LBX_BURGERS: return 1;
     case LBX_EULER: return 4;
     case LBX_MAXWELL_TM: return 3;
+    case LBX_NSF_CONS_TRACK: return 4;
+    case LBX_MHD_POWELL_2D: return 6;
   }
   return 0;
 }
@@ -74,6 +80,11 @@ static const char* NAMES_MHD[] = {"rho", "m_x", "m_y", "m_z", "B_x", "B_y", "B_z
 static const char* NAMES_BUR[] = {"u"};
 static const char* NAMES_EUL[] = {"rho", "m_x", "m_y", "E"};
 static const char* NAMES_MAX[] = {"E_z", "H_x", "H_y"};
+static const char* NAMES_NSF12[] = {"rho", "m_x", "m_y", "E", "G_rho_x", "G_rho_y", "G_mx_x", "G_mx_y",
+                                    "G_my_x", "G_my_y", "G_E_x", "G_E_y"};
+static const char* NAMES_MHD18[] = {"rho", "m_x", "m_y", "E", "B_x", "B_y", "G_rho_x", "G_rho_y", "G_mx_x",
+                                    "G_mx_y", "G_my_x", "G_my_y", "G_E_x", "G_E_y", "G_Bx_x", "G_Bx_y",
+                                    "G_By_x", "G_By_y"};
 
 extern "C" lbx_status lbx_system_declare(const lbx_system_desc* desc, lbx_system** out) {
   if (!desc || !out) return fail(LBX_ERR_ARG, "lbx_system_declare: null argument");
@@ -87,7 +98,8 @@ extern "C" lbx_status lbx_system_declare(const lbx_system_desc* desc, lbx_system
   s->D = family_D(desc->family);
   memcpy(s->params, desc->params, sizeof(s->params));
   memcpy(s->Q0, desc->Q0, sizeof(s->Q0));
-  if ((s->family == LBX_NSF_PRIM_TRACK || s->family == LBX_EULER || s->family == LBX_MHD_J_TRACK) &&
+  if ((s->family == LBX_NSF_PRIM_TRACK || s->family == LBX_EULER || s->family == LBX_MHD_J_TRACK ||
+       s->family == LBX_NSF_CONS_TRACK || s->family == LBX_MHD_POWELL_2D) &&
       !(s->Q0[0] > 0.0)) {
     delete s;
     return fail(LBX_ERR_ARG, "lbx_system_declare: reference density Q0[0] must be > 0");
@@ -113,6 +125,8 @@ extern "C" const char* lbx_component_name(const lbx_system* s, int k) {
     case LBX_BURGERS: return NAMES_BUR[k];
     case LBX_EULER: return NAMES_EUL[k];
     case LBX_MAXWELL_TM: return NAMES_MAX[k];
+    case LBX_NSF_CONS_TRACK: return NAMES_NSF12[k];
+    case LBX_MHD_POWELL_2D: return NAMES_MHD18[k];
   }
   return nullptr;
 }
@@ -256,6 +270,46 @@ extern "C" size_t lbx_state_buffer_bytes(const lbx_scheme* s) {
 }
 
 // Phi(Q0) in plain form (host, float64), for the unshifted storage mode and f^eq(Q0).
+// Background state of the conserved-gradient cascades (NSF_CONS_TRACK, MHD_POWELL_2D) at
+// Q0: velocity, pressure, temperature (T = p/(rho R); R = 1 for MHD), the chain-rule
+// velocity and temperature gradients and the viscous stress.  Zero gradients for a
+// uniform background.
+struct CascadeBg {
+  double rho, u[2], p, T, L[2][2], GT[2], tv[2][2], B[2], b2, uB, jz;
+};
+static CascadeBg cascade_bg(int family, const double* Q, const double* P) {
+  CascadeBg c{};
+  const bool mhd = family == LBX_MHD_POWELL_2D;
+  const double g = P[0], R = mhd ? 1.0 : P[1], mu = P[mhd ? 1 : 2];
+  const int gr = mhd ? 6 : 4;                       // first tracker: G_rho
+  const double* Gr = Q + gr;
+  const double* Gm0 = Q + gr + 2;
+  const double* Gm1 = Q + gr + 4;
+  const double* GE = Q + gr + 6;
+  c.rho = Q[0];
+  c.u[0] = Q[1] / c.rho;
+  c.u[1] = Q[2] / c.rho;
+  const double u2 = c.u[0] * c.u[0] + c.u[1] * c.u[1];
+  c.B[0] = mhd ? Q[4] : 0.0;
+  c.B[1] = mhd ? Q[5] : 0.0;
+  c.b2 = c.B[0] * c.B[0] + c.B[1] * c.B[1];
+  c.uB = c.u[0] * c.B[0] + c.u[1] * c.B[1];
+  c.p = (g - 1.0) * (Q[3] - 0.5 * c.rho * u2 - 0.5 * c.b2);
+  c.T = c.p / (c.rho * R);
+  const double* Gm[2] = {Gm0, Gm1};
+  for (int b = 0; b < 2; ++b) {
+    for (int a = 0; a < 2; ++a) c.L[a][b] = (Gm[a][b] - c.u[a] * Gr[b]) / c.rho;
+    double Gp = (g - 1.0) * (GE[b] - (c.u[0] * Gm0[b] + c.u[1] * Gm1[b]) + 0.5 * u2 * Gr[b]);
+    if (mhd) Gp -= (g - 1.0) * (c.B[0] * Q[14 + b] + c.B[1] * Q[16 + b]);
+    c.GT[b] = (Gp / R - c.T * Gr[b]) / c.rho;
+  }
+  const double dv = 2.0 / 3.0 * (c.L[0][0] + c.L[1][1]);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) c.tv[a][b] = mu * (c.L[a][b] + c.L[b][a] - (a == b ? dv : 0.0));
+  c.jz = mhd ? Q[16] - Q[15] : 0.0;
+  return c;
+}
+
 static void background_flux(const lbx_scheme* s, double F0[KMAX][3]) {
   const lbx_system& y = s->sys;
   const double* Q = y.Q0;
@@ -344,6 +398,28 @@ static void background_flux(const lbx_scheme* s, double F0[KMAX][3]) {
       F0[2][0] = -c * Q[0];
       break;
     }
+    case LBX_NSF_CONS_TRACK:
+    case LBX_MHD_POWELL_2D: {
+      const bool mhd = y.family == LBX_MHD_POWELL_2D;
+      const CascadeBg c = cascade_bg(y.family, Q, P);
+      const double kap = P[mhd ? 2 : 3], eta = mhd ? P[3] : 0.0;
+      const double pt = c.p + 0.5 * c.b2;
+      const double jxB[2] = {-c.jz * c.B[1], c.jz * c.B[0]};
+      for (int b = 0; b < 2; ++b) {
+        F0[0][b] = Q[1 + b];
+        for (int a = 0; a < 2; ++a) F0[1 + a][b] = Q[1 + a] * c.u[b] + (a == b ? pt : 0.0) - c.B[a] * c.B[b] - c.tv[a][b];
+        F0[3][b] = (Q[3] + pt) * c.u[b] - c.B[b] * c.uB - (c.tv[b][0] * c.u[0] + c.tv[b][1] * c.u[1]) -
+                   kap * c.GT[b] + eta * jxB[b];
+        if (mhd)
+          for (int a = 0; a < 2; ++a) F0[4 + a][b] = c.B[a] * c.u[b] - c.u[a] * c.B[b] - eta * Q[14 + 2 * a + b];
+      }
+      const int nv = mhd ? 6 : 4, gr = mhd ? 6 : 4;
+      for (int v = 0; v < nv; ++v)
+        for (int b = 0; b < 2; ++b)
+          for (int cc = 0; cc < 2; ++cc)
+            F0[gr + 2 * v + b][cc] = Q[gr + 2 * v + b] * c.u[cc] - (b == cc ? Q[v] * itg : 0.0);
+      break;
+    }
   }
 }
 
@@ -396,6 +472,28 @@ static void pack_prm(const lbx_scheme* s, double prm[NPRM]) {
     case LBX_MAXWELL_TM:
       prm[0] = P[0];
       break;
+    case LBX_NSF_CONS_TRACK: {
+      const CascadeBg c = cascade_bg(y.family, Q, P);
+      prm[0] = P[0] - 1.0; prm[1] = P[1]; prm[2] = P[2]; prm[3] = P[3]; prm[4] = itg;
+      prm[5] = c.u[0]; prm[6] = c.u[1]; prm[7] = Q[3] + c.p; prm[8] = c.T;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) prm[9 + 2 * a + b] = c.L[a][b];
+      prm[13] = c.GT[0]; prm[14] = c.GT[1];
+      prm[15] = c.tv[0][0]; prm[16] = c.tv[0][1]; prm[17] = c.tv[1][1];
+      prm[18] = P[0];
+      break;
+    }
+    case LBX_MHD_POWELL_2D: {
+      const CascadeBg c = cascade_bg(y.family, Q, P);
+      prm[0] = P[0] - 1.0; prm[1] = P[1]; prm[2] = P[2]; prm[3] = P[3]; prm[4] = itg;
+      prm[5] = c.u[0]; prm[6] = c.u[1]; prm[7] = Q[3] + c.p + 0.5 * c.b2; prm[8] = c.uB; prm[9] = c.T;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) prm[10 + 2 * a + b] = c.L[a][b];
+      prm[14] = c.GT[0]; prm[15] = c.GT[1];
+      prm[16] = c.tv[0][0]; prm[17] = c.tv[0][1]; prm[18] = c.tv[1][1];
+      prm[19] = P[0];
+      break;
+    }
   }
 }
 
@@ -435,6 +533,7 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
   if (s.d.mms == LBX_MMS_FOURIER && st->d_mms_modes) {
     p.mms_modes = (const MmsMode*)st->d_mms_modes;
     p.mms_n = s.d.mms_n_modes;
+    p.mms_trackers = s.d.mms_conserved_only == 0;
     for (int q = 0; q < 8; ++q) p.mms_mean[q] = (T)s.d.mms_mean[q];
   }
 }
@@ -632,6 +731,14 @@ bool lbx::find_ops(int family, int lattice, int precision, Ops* o) {
     case LBX_MAXWELL_TM:
       if (lattice == LBX_D2Q5) return pick_store<LatD2Q5, SysMaxwell>(precision, o);
       return false;
+    case LBX_NSF_CONS_TRACK:
+      if (lattice == LBX_D2Q5) return pick_store<LatD2Q5, SysNSF12>(precision, o);
+      if (lattice == LBX_D2Q9) return pick_store<LatD2Q9, SysNSF12>(precision, o);
+      return false;
+    case LBX_MHD_POWELL_2D:
+      if (lattice == LBX_D2Q5) return pick_store<LatD2Q5, SysMHD18>(precision, o);
+      if (lattice == LBX_D2Q9) return pick_store<LatD2Q9, SysMHD18>(precision, o);
+      return false;
   }
   return false;
 }
@@ -684,7 +791,7 @@ lbx_status lbx::run_reduce(lbx_state* st, const double* Qref, int mode, double* 
   const int K = st->sch.sys.K;
   if (cudaError_t e = st->ops.reduce(st, st->cur(), Qref, st->d_partials, st->red_blocks, mode))
     return fail(LBX_ERR_CUDA, "reduce launch: %s", cudaGetErrorString(e));
-  k_reduce_final<<<1, 64, 0, st->stream>>>(st->d_partials, st->red_blocks, K, mode, st->d_red_out);
+  k_reduce_final<<<1, RED_FINAL_THREADS, 0, st->stream>>>(st->d_partials, st->red_blocks, K, mode, st->d_red_out);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(host_out, st->d_red_out, sizeof(double) * K * 4, cudaMemcpyDeviceToHost, st->stream));
   CK(cudaStreamSynchronize(st->stream));
@@ -817,11 +924,20 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
     if (!e) e = cudaStreamSynchronize(st->stream);
     cudaFree(dmax);
     CKI(e);
+    // s_k = 2^ceil(log2(4 m_k)), m_k = max |f*_k| at init, floored at 2^-10 of the largest
+    // background equilibrium population of the component: a component that starts at rest
+    // (fluctuation zero up to rounding, e.g. B = B0 at t = 0) keeps room to grow instead of
+    // receiving a scale of its rounding residue that the first fluctuation overflows.
+    std::vector<double> feq0(K * q);
+    feq0_table(*sch, feq0.data());
     for (int k = 0; k < K; ++k) {
       double m;
       memcpy(&m, &hm[k], sizeof(double));
       if (!std::isfinite(m)) return bail(fail(LBX_ERR_NONFINITE, "lbx_init: non-finite initial field"));
-      st->scale[k] = m > 0.0 ? std::ldexp(1.0, (int)std::ceil(std::log2(4.0 * m))) : 1.0;
+      double b = 0.0;
+      for (int i = 0; i < q; ++i) b = std::max(b, std::fabs(feq0[k * q + i]));
+      m = std::max(m, std::ldexp(b, -10));
+      st->scale[k] = m > 1e-30 ? std::ldexp(1.0, (int)std::ceil(std::log2(4.0 * m))) : 1.0;
     }
     refresh_params(st);
   }

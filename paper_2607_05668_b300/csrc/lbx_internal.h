@@ -13,7 +13,7 @@ struct lbx_system {
   int family;
   int K, NC, D;
   double params[8];
-  double Q0[16];
+  double Q0[24];
 };
 
 struct lbx_scheme {

@@ -27,6 +27,8 @@ namespace {
 constexpr int kMaxDevices = 64;
 constexpr size_t kPartialDoubles = (size_t)LBX_STATIC_REDUCE_MAX_BLOCKS * KMAX * 4;
 constexpr size_t kScratchDoubles = kPartialDoubles + KMAX * 4;
+static_assert(kScratchDoubles == (size_t)LBX_STATIC_REDUCE_SCRATCH_DOUBLES,
+              "LBX_STATIC_REDUCE_SCRATCH_DOUBLES must follow the largest component count");
 
 // Per-block partials [block][k][4] followed by the reduced result [k][4].
 static __device__ __align__(256) double g_reduce_scratch[kScratchDoubles];
@@ -93,7 +95,7 @@ extern "C" lbx_status lbx_conserved_sums_static(const lbx_scheme* sch, const voi
   double* out = scratch + kPartialDoubles;
   cudaError_t e = ops.reduce(&view, populations, nullptr, partials, nblocks, 0);
   if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_conserved_sums_static: reduce: %s", cudaGetErrorString(e));
-  k_reduce_final<<<1, 64, 0, view.stream>>>(partials, nblocks, K, 0, out);
+  k_reduce_final<<<1, RED_FINAL_THREADS, 0, view.stream>>>(partials, nblocks, K, 0, out);
   k_pick_sums<<<1, 32, 0, view.stream>>>(out, K, sums);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_conserved_sums_static: %s", cudaGetErrorString(e));

@@ -22,7 +22,7 @@
 
 namespace lbx {
 
-constexpr int KMAX = 11;
+constexpr int KMAX = 18;
 constexpr int NPRM = 24;
 
 // ------------------------------------------------------------------------------ ADR
@@ -231,6 +231,224 @@ struct SysMHD {
     }
     const T pr = p[0] * ((Q0[7] + dQ[7]) - T(0.5) * rho * u2 - T(0.5) * b2);
     return sqrt(u2) + sqrt(p[8] * pr / rho + b2 / rho + p[1] * p[2]);
+  }
+};
+
+// ------------------------------------------------------------- NSF, the paper's cascade
+// Compressible NSF with trackers of the conserved fields (the paper's 12-component
+// cascade, Sec. 2.1.1): Q = (rho, m_x, m_y, E, G_rho(2), G_mx(2), G_my(2), G_E(2)).
+// The chain rule gives L = grad u = (G_m - u (x) G_rho)/rho,
+// grad p = (gamma-1)(G_E - u.G_m + |u|^2/2 G_rho), grad T = (grad p/R - T G_rho)/rho.
+// In delta form (background L0, grad T0, tau_v0 from the host; zero for a uniform
+// background):  rho dL = dG_m - u0 (x) dG_rho - du (x) G_rho - drho L0,
+// rho d(grad T) = d(grad p)/R - T0 dG_rho - dT G_rho - drho grad T0.
+// p: 0 gamma-1, 1 R, 2 mu, 3 kappa, 4 1/tau_grad, 5-6 u0, 7 E0+p0, 8 T0, 9-12 L0 (row-major),
+//    13-14 grad T0, 15-17 tau_v0 (xx, xy, yy), 18 gamma
+template <typename T>
+struct SysNSF12 {
+  static constexpr int K = 12, NC = 4, D = 2, FAMILY = 7, NPRIM = 4;
+  // primitives: rho, u, v, p; trackers: gradients of rho, rho u, rho v, E
+  template <typename U>
+  __host__ __device__ static void augment(const T* p, const U (&V)[NPRIM], const U (&G)[NPRIM][3], U (&Q)[K]) {
+    const U rho = V[0], u = V[1], v = V[2];
+    Q[0] = rho;
+    Q[1] = rho * u;
+    Q[2] = rho * v;
+    Q[3] = V[3] / p[0] + U(0.5) * rho * (u * u + v * v);
+    for (int b = 0; b < 2; ++b) {
+      Q[4 + b] = G[0][b];
+      Q[6 + b] = G[0][b] * u + rho * G[1][b];
+      Q[8 + b] = G[0][b] * v + rho * G[2][b];
+      Q[10 + b] = G[3][b] / p[0] + U(0.5) * G[0][b] * (u * u + v * v) + rho * (u * G[1][b] + v * G[2][b]);
+    }
+  }
+  __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
+    const T gm1 = p[0], R = p[1], mu = p[2], kap = p[3], itg = p[4];
+    const T u0[2] = {p[5], p[6]};
+    const T EP0 = p[7], T0 = p[8];
+    const T drho = dQ[0], rho = Q0[0] + drho, irho = T(1) / rho;
+    const T dm[2] = {dQ[1], dQ[2]}, m0[2] = {Q0[1], Q0[2]};
+    T du[2], u[2];
+    for (int a = 0; a < 2; ++a) {
+      du[a] = (dm[a] - u0[a] * drho) * irho;
+      u[a] = u0[a] + du[a];
+    }
+    const T dke = T(0.5) * (dm[0] * u[0] + dm[1] * u[1] + m0[0] * du[0] + m0[1] * du[1]);
+    const T dE = dQ[3], dp = gm1 * (dE - dke);
+    const T dT = (dp - R * T0 * drho) * irho / R;
+    // trackers (full values G, fluctuations dG)
+    T Gr[2], dGr[2], Gm[2][2], dGm[2][2], dGE[2];
+    for (int b = 0; b < 2; ++b) {
+      dGr[b] = dQ[4 + b];
+      Gr[b] = Q0[4 + b] + dGr[b];
+      for (int a = 0; a < 2; ++a) {
+        dGm[a][b] = dQ[6 + 2 * a + b];
+        Gm[a][b] = Q0[6 + 2 * a + b] + dGm[a][b];
+      }
+      dGE[b] = dQ[10 + b];
+    }
+    T dL[2][2], dGT[2];
+    const T u02 = u0[0] * u0[0] + u0[1] * u0[1];
+    const T duu = du[0] * (u[0] + u0[0]) + du[1] * (u[1] + u0[1]);    // |u|^2 - |u0|^2
+    for (int b = 0; b < 2; ++b) {
+      for (int a = 0; a < 2; ++a)
+        dL[a][b] = (dGm[a][b] - u0[a] * dGr[b] - du[a] * Gr[b] - drho * p[9 + 2 * a + b]) * irho;
+      const T dGp = gm1 * (dGE[b] - (du[0] * Gm[0][b] + du[1] * Gm[1][b] + u0[0] * dGm[0][b] + u0[1] * dGm[1][b]) +
+                           T(0.5) * (duu * Gr[b] + u02 * dGr[b]));
+      dGT[b] = (dGp / R - T0 * dGr[b] - dT * Gr[b] - drho * p[13 + b]) * irho;
+    }
+    const T dv = T(2.0 / 3.0) * (dL[0][0] + dL[1][1]);
+    const T dt00 = mu * (T(2) * dL[0][0] - dv), dt11 = mu * (T(2) * dL[1][1] - dv), dt01 = mu * (dL[0][1] + dL[1][0]);
+    const T t0[2][2] = {{p[15], p[16]}, {p[16], p[17]}};
+    const T dtv[2][2] = {{dt00, dt01}, {dt01, dt11}};
+    for (int b = 0; b < 2; ++b) dPhi[0][b] = dm[b];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        dPhi[1 + a][b] = dm[a] * u[b] + m0[a] * du[b] + (a == b ? dp : T(0)) - dtv[a][b];
+    for (int b = 0; b < 2; ++b) {
+      const T tu = dtv[b][0] * u[0] + dtv[b][1] * u[1] + t0[b][0] * du[0] + t0[b][1] * du[1];
+      dPhi[3][b] = (dE + dp) * u[b] + EP0 * du[b] - tu - kap * dGT[b];
+    }
+    const T dV[4] = {drho, dm[0], dm[1], dE};
+    for (int v = 0; v < 4; ++v)
+      for (int b = 0; b < 2; ++b) {
+        const int k = 4 + 2 * v + b;
+        for (int c = 0; c < 2; ++c) dPhi[k][c] = dQ[k] * u[c] + Q0[k] * du[c] - (b == c ? dV[v] * itg : T(0));
+      }
+    for (int k = 0; k < 4; ++k) S[k] = T(0);
+    for (int k = 4; k < 12; ++k) S[k] = -(Q0[k] + dQ[k]) * itg;
+  }
+  // |u| + sqrt(c^2 + (4/3 mu + (gamma-1) kappa/R) / (rho tau_g)), as for SysNSF.
+  __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) {
+    const T rho = Q0[0] + dQ[0];
+    const T ux = (Q0[1] + dQ[1]) / rho, uy = (Q0[2] + dQ[2]) / rho;
+    const T pr = p[0] * ((Q0[3] + dQ[3]) - T(0.5) * rho * (ux * ux + uy * uy));
+    const T s2 = p[18] * pr / rho + (T(4.0 / 3.0) * p[2] + p[0] * p[3] / p[1]) * p[4] / rho;
+    return sqrt(ux * ux + uy * uy) + sqrt(s2);
+  }
+};
+
+// ------------------------------------------------------------- MHD, the paper's cascade
+// 2D viscous, heat-conducting resistive MHD with Powell cleaning (the paper's 18-component
+// cascade): Q = (rho, m_x, m_y, E, B_x, B_y, G_rho(2), G_mx(2), G_my(2), G_E(2), G_Bx(2),
+// G_By(2)); p = (gamma-1)(E - rho|u|^2/2 - |B|^2/2), p_t = p + |B|^2/2, T = p/rho,
+// grad p = (gamma-1)(G_E - u.G_m + |u|^2/2 G_rho - B.G_B), j_z = G_{By,x} - G_{Bx,y},
+// Phi_m = m u + p_t I - B B - tau_v, Phi_E = (E + p_t) u - B (u.B) - tau_v u - kappa grad T
+// + eta (j x B), Phi_B = B u - u B - eta G_B, S = -(tr G_B) (0, B, u.B, u).
+// p: 0 gamma-1, 1 mu, 2 kappa, 3 eta, 4 1/tau_grad, 5-6 u0, 7 E0 + p_t0, 8 u0.B0, 9 T0,
+//    10-13 L0, 14-15 grad T0, 16-18 tau_v0 (xx, xy, yy), 19 gamma
+template <typename T>
+struct SysMHD18 {
+  static constexpr int K = 18, NC = 6, D = 2, FAMILY = 8, NPRIM = 6;
+  // primitives: rho, u, v, p, B_x, B_y; trackers: gradients of rho, rho u, rho v, E, B
+  template <typename U>
+  __host__ __device__ static void augment(const T* p, const U (&V)[NPRIM], const U (&G)[NPRIM][3], U (&Q)[K]) {
+    const U rho = V[0], u = V[1], v = V[2], bx = V[4], by = V[5];
+    Q[0] = rho;
+    Q[1] = rho * u;
+    Q[2] = rho * v;
+    Q[3] = V[3] / p[0] + U(0.5) * (rho * (u * u + v * v) + bx * bx + by * by);
+    Q[4] = bx;
+    Q[5] = by;
+    for (int b = 0; b < 2; ++b) {
+      Q[6 + b] = G[0][b];
+      Q[8 + b] = G[0][b] * u + rho * G[1][b];
+      Q[10 + b] = G[0][b] * v + rho * G[2][b];
+      Q[12 + b] = G[3][b] / p[0] + U(0.5) * G[0][b] * (u * u + v * v) + rho * (u * G[1][b] + v * G[2][b]) +
+                  bx * G[4][b] + by * G[5][b];
+      Q[14 + b] = G[4][b];
+      Q[16 + b] = G[5][b];
+    }
+  }
+  __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K]) {
+    const T gm1 = p[0], mu = p[1], kap = p[2], eta = p[3], itg = p[4];
+    const T u0[2] = {p[5], p[6]};
+    const T EPt0 = p[7], uB0 = p[8], T0 = p[9];
+    const T drho = dQ[0], rho = Q0[0] + drho, irho = T(1) / rho;
+    const T dm[2] = {dQ[1], dQ[2]}, m0[2] = {Q0[1], Q0[2]};
+    const T dB[2] = {dQ[4], dQ[5]}, B0[2] = {Q0[4], Q0[5]};
+    T du[2], u[2], B[2];
+    for (int a = 0; a < 2; ++a) {
+      du[a] = (dm[a] - u0[a] * drho) * irho;
+      u[a] = u0[a] + du[a];
+      B[a] = B0[a] + dB[a];
+    }
+    const T dke = T(0.5) * (dm[0] * u[0] + dm[1] * u[1] + m0[0] * du[0] + m0[1] * du[1]);
+    const T dme = T(0.5) * (dB[0] * (B[0] + B0[0]) + dB[1] * (B[1] + B0[1]));
+    const T dE = dQ[3];
+    const T dp = gm1 * (dE - dke - dme), dpt = dp + dme;
+    const T duB = du[0] * B[0] + du[1] * B[1] + u0[0] * dB[0] + u0[1] * dB[1];
+    const T uB = uB0 + duB;
+    const T dT = (dp - T0 * drho) * irho;
+    T Gr[2], dGr[2], Gm[2][2], dGm[2][2], dGE[2], GB[2][2], dGB[2][2];
+    for (int b = 0; b < 2; ++b) {
+      dGr[b] = dQ[6 + b];
+      Gr[b] = Q0[6 + b] + dGr[b];
+      for (int a = 0; a < 2; ++a) {
+        dGm[a][b] = dQ[8 + 2 * a + b];
+        Gm[a][b] = Q0[8 + 2 * a + b] + dGm[a][b];
+        dGB[a][b] = dQ[14 + 2 * a + b];
+        GB[a][b] = Q0[14 + 2 * a + b] + dGB[a][b];
+      }
+      dGE[b] = dQ[12 + b];
+    }
+    T dL[2][2], dGT[2];
+    const T u02 = u0[0] * u0[0] + u0[1] * u0[1];
+    const T duu = du[0] * (u[0] + u0[0]) + du[1] * (u[1] + u0[1]);
+    for (int b = 0; b < 2; ++b) {
+      for (int a = 0; a < 2; ++a)
+        dL[a][b] = (dGm[a][b] - u0[a] * dGr[b] - du[a] * Gr[b] - drho * p[10 + 2 * a + b]) * irho;
+      const T dGp = gm1 * (dGE[b] - (du[0] * Gm[0][b] + du[1] * Gm[1][b] + u0[0] * dGm[0][b] + u0[1] * dGm[1][b]) +
+                           T(0.5) * (duu * Gr[b] + u02 * dGr[b]) -
+                           (dB[0] * GB[0][b] + dB[1] * GB[1][b] + B0[0] * dGB[0][b] + B0[1] * dGB[1][b]));
+      dGT[b] = (dGp - T0 * dGr[b] - dT * Gr[b] - drho * p[14 + b]) * irho;
+    }
+    const T dv = T(2.0 / 3.0) * (dL[0][0] + dL[1][1]);
+    const T dt00 = mu * (T(2) * dL[0][0] - dv), dt11 = mu * (T(2) * dL[1][1] - dv), dt01 = mu * (dL[0][1] + dL[1][0]);
+    const T t0[2][2] = {{p[16], p[17]}, {p[17], p[18]}};
+    const T dtv[2][2] = {{dt00, dt01}, {dt01, dt11}};
+    // j x B - j0 x B0 with j_z = G_{By,x} - G_{Bx,y}
+    const T jz0 = Q0[16] - Q0[15], djz = dGB[1][0] - dGB[0][1], jz = jz0 + djz;
+    const T djxB[2] = {-(djz * B[1] + jz0 * dB[1]), djz * B[0] + jz0 * dB[0]};
+    (void)jz;
+    for (int b = 0; b < 2; ++b) dPhi[0][b] = dm[b];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        dPhi[1 + a][b] = dm[a] * u[b] + m0[a] * du[b] + (a == b ? dpt : T(0)) - (dB[a] * B[b] + B0[a] * dB[b]) -
+                         dtv[a][b];
+    for (int b = 0; b < 2; ++b) {
+      const T tu = dtv[b][0] * u[0] + dtv[b][1] * u[1] + t0[b][0] * du[0] + t0[b][1] * du[1];
+      dPhi[3][b] = (dE + dpt) * u[b] + EPt0 * du[b] - (dB[b] * uB + B0[b] * duB) - tu - kap * dGT[b] + eta * djxB[b];
+    }
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        dPhi[4 + a][b] = (dB[a] * u[b] + B0[a] * du[b]) - (du[a] * B[b] + u0[a] * dB[b]) - eta * dGB[a][b];
+    const T dV[6] = {drho, dm[0], dm[1], dE, dB[0], dB[1]};
+    for (int v = 0; v < 6; ++v)
+      for (int b = 0; b < 2; ++b) {
+        const int k = 6 + 2 * v + b;
+        for (int c = 0; c < 2; ++c) dPhi[k][c] = dQ[k] * u[c] + Q0[k] * du[c] - (b == c ? dV[v] * itg : T(0));
+      }
+    const T divB = GB[0][0] + GB[1][1];
+    S[0] = T(0);
+    S[1] = -divB * B[0];
+    S[2] = -divB * B[1];
+    S[3] = -divB * uB;
+    S[4] = -divB * u[0];
+    S[5] = -divB * u[1];
+    for (int k = 6; k < 18; ++k) S[k] = -(Q0[k] + dQ[k]) * itg;
+  }
+  // |u| + sqrt(c^2 + |B|^2/rho + (4/3 mu + (gamma-1) kappa)/(rho tau_g) + eta/tau_g): fast
+  // magnetosonic speed plus the relaxation speeds of the viscous, thermal and resistive
+  // tracker couplings.
+  __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) {
+    const T rho = Q0[0] + dQ[0];
+    const T ux = (Q0[1] + dQ[1]) / rho, uy = (Q0[2] + dQ[2]) / rho;
+    const T bx = Q0[4] + dQ[4], by = Q0[5] + dQ[5];
+    const T b2 = bx * bx + by * by;
+    const T pr = p[0] * ((Q0[3] + dQ[3]) - T(0.5) * rho * (ux * ux + uy * uy) - T(0.5) * b2);
+    const T s2 = p[19] * pr / rho + b2 / rho + (T(4.0 / 3.0) * p[1] + p[0] * p[2]) * p[4] / rho + p[3] * p[4];
+    return sqrt(ux * ux + uy * uy) + sqrt(s2);
   }
 };
 

@@ -18,6 +18,7 @@ _lib = C.CDLL(LIB_PATH)
 
 # ------------------------------------------------------------------------- constants
 ADR_CASCADE, NSF_PRIM_TRACK, MHD_J_TRACK, BURGERS, EULER, MAXWELL_TM = 1, 2, 3, 4, 5, 6
+NSF_CONS_TRACK, MHD_POWELL_2D = 7, 8
 D2Q5, D2Q9, D3Q7, D3Q19 = 1, 2, 3, 4
 ACOUSTIC, DIFFUSIVE = 1, 2
 FP64, FP32_SHIFT, FP16_SCALED = 1, 2, 3
@@ -37,7 +38,7 @@ class LbxError(RuntimeError):
 
 
 class SystemDesc(C.Structure):
-    _fields_ = [("family", C.c_int), ("params", C.c_double * 8), ("Q0", C.c_double * 16)]
+    _fields_ = [("family", C.c_int), ("params", C.c_double * 8), ("Q0", C.c_double * 24)]
 
 
 class MmsMode(C.Structure):
@@ -50,7 +51,8 @@ class SchemeDesc(C.Structure):
                 ("f", C.c_double), ("tau_lb", C.c_double), ("tau_R", C.c_double),
                 ("g_tau", C.c_double), ("precision", C.c_int), ("mms", C.c_int),
                 ("mms_amp", C.c_double), ("allow_subchar_violation", C.c_int),
-                ("mms_modes", C.POINTER(MmsMode)), ("mms_n_modes", C.c_int), ("mms_mean", C.c_double * 8)]
+                ("mms_modes", C.POINTER(MmsMode)), ("mms_n_modes", C.c_int), ("mms_mean", C.c_double * 8),
+                ("mms_conserved_only", C.c_int)]
 
 
 _P = C.c_void_p
@@ -177,7 +179,7 @@ class Scheme:
 
     def __init__(self, system: System, lattice, extent, scaling, f, tau_lb=0.0, tau_R=0.0,
                  g_tau=0.0, precision=FP64, mms=MMS_NONE, mms_amp=0.0,
-                 allow_subchar_violation=False, mms_modes=None, mms_mean=None):
+                 allow_subchar_violation=False, mms_modes=None, mms_mean=None, mms_conserved_only=False):
         """mms_modes: sequence of (p, (kx, ky[, kz]), amp, phase, sigma, omega, psi) for
         MMS_FOURIER; mms_mean: the primitives' means."""
         d = SchemeDesc()
@@ -202,6 +204,7 @@ class Scheme:
             d.mms_n_modes = len(mms_modes)
         for i, v in enumerate(mms_mean or []):
             d.mms_mean[i] = float(v)
+        d.mms_conserved_only = int(bool(mms_conserved_only))
         h = _P()
         check(_lib.lbx_scheme_derive(system._h, C.byref(d), C.byref(h)))
         self._h = h

@@ -45,7 +45,8 @@ def mhd_scheme(case, precision=L.FP32_SHIFT, lattice=L.D3Q19):
 
 # ------------------------------------------------------------- forced (manufactured) runs
 _FAMILY = {"adr": L.ADR_CASCADE, "nsf": L.NSF_PRIM_TRACK, "mhd": L.MHD_J_TRACK,
-           "burgers": L.BURGERS, "euler": L.EULER, "maxwell": L.MAXWELL_TM}
+           "burgers": L.BURGERS, "euler": L.EULER, "maxwell": L.MAXWELL_TM,
+           "nsf12": L.NSF_CONS_TRACK, "mhd18": L.MHD_POWELL_2D}
 
 
 def table_system(table, params, Q0):
@@ -54,9 +55,9 @@ def table_system(table, params, Q0):
 
 
 def forced_scheme(table, system, lattice, extent, scaling, f, precision=L.FP64, tau_lb=0.0,
-                  tau_R=0.0, g_tau=0.0):
-    """A scheme whose conserved components carry the FOURIER forcing of `table`
-    (.lbx_modes(), .mean)."""
+                  tau_R=0.0, g_tau=0.0, conserved_only=False):
+    """A scheme carrying the FOURIER forcing of `table` (.lbx_modes(), .mean): every
+    component, or the conserved ones with conserved_only."""
     return L.Scheme(system, lattice, extent, scaling, f, tau_lb=tau_lb, tau_R=tau_R, g_tau=g_tau,
                     precision=precision, mms=L.MMS_FOURIER, mms_modes=table.lbx_modes(),
-                    mms_mean=list(table.mean))
+                    mms_mean=list(table.mean), mms_conserved_only=conserved_only)

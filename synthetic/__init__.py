@@ -330,7 +330,8 @@ def adr_exact_stack(case: AdrCase):
 # primitive fields per family, in table order
 PRIMITIVES = {"adr": ("u",), "nsf": ("rho", "u", "v", "p"),
               "mhd": ("rho", "u_x", "u_y", "u_z", "B_x", "B_y", "B_z", "p"),
-              "burgers": ("u",), "euler": ("rho", "u", "v", "p"), "maxwell": ("E_z", "H_x", "H_y")}
+              "burgers": ("u",), "euler": ("rho", "u", "v", "p"), "maxwell": ("E_z", "H_x", "H_y"),
+              "nsf12": ("rho", "u", "v", "p"), "mhd18": ("rho", "u", "v", "p", "B_x", "B_y")}
 
 
 @dataclass
@@ -356,7 +357,11 @@ class ModeTable:
         g, R = self.gamma, self.R
         if self.family in ("adr", "burgers", "maxwell"):
             return torch.stack(V)
-        if self.family in ("nsf", "euler"):
+        if self.family == "mhd18":
+            rho, u, v, p, bx, by = V
+            E = p / (g - 1.0) + 0.5 * rho * (u * u + v * v) + 0.5 * (bx * bx + by * by)
+            return torch.stack([rho, rho * u, rho * v, E, bx, by])
+        if self.family in ("nsf", "euler", "nsf12"):
             rho, u, v, p = V
             return torch.stack([rho, rho * u, rho * v, p / (g - 1.0) + 0.5 * rho * (u * u + v * v)])
         if self.family == "mhd":
@@ -396,6 +401,27 @@ class ModeTable:
         elif self.family == "mhd":
             G = lambda c, b: self.gradient(xs, t, 4 + c, b)
             tr = [G(2, 1) - G(1, 2), G(0, 2) - G(2, 0), G(1, 0) - G(0, 1)]
+        elif self.family in ("nsf12", "mhd18"):
+            # gradients of the conserved fields by the product rule
+            V = self.primitives(xs, t)
+            rho, u, v, p = V[:4]
+            g1 = self.gamma - 1.0
+            tr = []
+            Gs = [[self.gradient(xs, t, q, b) for b in range(2)] for q in range(len(V))]
+            for b in range(2):
+                tr.append(Gs[0][b])
+            for q, w in ((1, u), (2, v)):
+                for b in range(2):
+                    tr.append(Gs[0][b] * w + rho * Gs[q][b])
+            for b in range(2):
+                gE = Gs[3][b] / g1 + 0.5 * Gs[0][b] * (u * u + v * v) + rho * (u * Gs[1][b] + v * Gs[2][b])
+                if self.family == "mhd18":
+                    gE = gE + V[4] * Gs[4][b] + V[5] * Gs[5][b]
+                tr.append(gE)
+            if self.family == "mhd18":
+                for q in (4, 5):
+                    for b in range(2):
+                        tr.append(Gs[q][b])
         else:
             return Qc
         return torch.cat([Qc, torch.stack(tr)])
@@ -503,7 +529,7 @@ class NsfPaperCase:
         p0 = 1.0 / self.gamma
         return [1.0, 3.0, 2.0, p0 / (self.gamma - 1.0) + 0.5 * 13.0] + [0.0] * 6
 
-    def table(self):
+    def table(self, family="nsf"):
         """rho = 1 + 0.2 sin(kx) cos(ky) cos t, u = 3 + 0.2 cos(kx) sin(ky) sin t,
         v = 2 + 0.15 sin(kx) sin(ky) cos t, p = p0 + (rho - 1) + 0.2 p0 cos(kx) sin(ky) sin t."""
         p0, s = 1.0 / self.gamma, -0.5 * math.pi
@@ -512,7 +538,11 @@ class NsfPaperCase:
                  + _product_modes(2, 0.15, "sin", "sin", 1, 1, 1.0, 0.0)
                  + _product_modes(3, 0.2, "sin", "cos", 1, 1, 1.0, 0.0)
                  + _product_modes(3, 0.2 * p0, "cos", "sin", 1, 1, 1.0, s))
-        return ModeTable("nsf", [1.0, 3.0, 2.0, p0], modes, gamma=self.gamma, R=self.R)
+        return ModeTable(family, [1.0, 3.0, 2.0, p0], modes, gamma=self.gamma, R=self.R)
+
+    def reference_state_cascade(self):
+        """Q0 of the paper's 12-component cascade (uniform background, zero trackers)."""
+        return self.reference_state()[:4] + [0.0] * 8
 
 
 @dataclass
@@ -580,3 +610,78 @@ def mhd_mms_table(case: MhdCase, seed: int = 2):
         for c in range(3):          # B = curl of A = scale d sin(th)/(2 pi |k|): cos(th) (k x d)/|k|
             modes.append((4 + c, tuple(int(v) for v in k), scale * float(kxd[c]), ph + 0.5 * math.pi, 0.0, 1.0, ps))
     return ModeTable("mhd", [1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0 / case.gamma], modes, gamma=case.gamma)
+
+
+@dataclass
+class MhdPaper2DCase:
+    """The paper's MHD manufactured flow on its own 2D system (18 components, Powell
+    source), in the units its scales divide out: rho0 = 1, c_s = 1, p0 = 1/gamma, background
+    u0 = v0 = 3, B0 = (0.5, 0.5), equal diffusivities mu = kappa = eta = 0.01
+    (4.165 Pa s / (1.225 kg/m^3 x 340 m/s x 1 m) and 3.4 m^2/s / (340 m/s x 1 m)).
+    Double-precision recipe: acoustic f = 0.025, tau_R = 140, g_tau = 4."""
+    n: int
+    gamma: float = 1.4
+    mu: float = 0.01
+    kappa: float = 0.01
+    eta: float = 0.01
+    f: float = 0.025
+    tau_R: float = 140.0
+    g_tau: float = 4.0
+
+    @property
+    def dx(self):
+        return 1.0 / self.n
+
+    @property
+    def dt(self):
+        return self.f * self.dx
+
+    def reference_state(self):
+        p0 = 1.0 / self.gamma
+        E0 = p0 / (self.gamma - 1.0) + 0.5 * 18.0 + 0.5 * 0.5
+        return [1.0, 3.0, 3.0, E0, 0.5, 0.5] + [0.0] * 12
+
+    def table(self):
+        """rho = 1 + 0.3 sin(kx) cos(ky) cos t, p = p0 + (rho - 1) + 0.2 p0 cos(kx) sin(ky) sin t,
+        u = 3 + 0.3 cos(kx) sin(ky) sin t, v = 3 + 0.3 sin(kx) sin(ky) sin t,
+        B_x = 0.5 - 0.3 cos(kx) sin(ky) sin t, B_y = 0.5 + 0.3 sin(kx) cos(ky) sin t."""
+        p0, s = 1.0 / self.gamma, -0.5 * math.pi
+        modes = (_product_modes(0, 0.3, "sin", "cos", 1, 1, 1.0, 0.0)
+                 + _product_modes(3, 0.3, "sin", "cos", 1, 1, 1.0, 0.0)
+                 + _product_modes(3, 0.2 * p0, "cos", "sin", 1, 1, 1.0, s)
+                 + _product_modes(1, 0.3, "cos", "sin", 1, 1, 1.0, s)
+                 + _product_modes(2, 0.3, "sin", "sin", 1, 1, 1.0, s)
+                 + _product_modes(4, -0.3, "cos", "sin", 1, 1, 1.0, s)
+                 + _product_modes(5, 0.3, "sin", "cos", 1, 1, 1.0, s))
+        return ModeTable("mhd18", [1.0, 3.0, 3.0, p0, 0.5, 0.5], modes, gamma=self.gamma)
+
+
+@dataclass
+class AdrPaperCase:
+    """The paper's ADR manufactured flow (supplement, MMS section):
+    c = 0.5 + 0.5 sin(2 pi (x - u0 t)) cos(2 pi (y - u1 t)) e^{-t}, u = (0.1, -0.1), D = 0.01,
+    reaction R c (1 - c) with R = 1.  Recipe: diffusive f = 1.9, tau_R = 50, g_tau = 6."""
+    n: int
+    a: tuple = (0.1, -0.1)
+    D: float = 0.01
+    R: float = 1.0
+    f: float = 1.9
+    tau_R: float = 50.0
+    g_tau: float = 6.0
+
+    @property
+    def dx(self):
+        return 1.0 / self.n
+
+    @property
+    def dt(self):
+        return self.f * self.dx * self.dx
+
+    def table(self):
+        """sin(theta - w t) = sin(theta) cos(w t) + sin(theta + pi/2) cos(w t + pi/2), so each
+        product term of the travelling wave is two standing modes decaying as e^{-t}."""
+        q = 0.5 * math.pi
+        modes = []
+        for k, w in (((1, 1, 0), TWO_PI * (self.a[0] + self.a[1])), ((1, -1, 0), TWO_PI * (self.a[0] - self.a[1]))):
+            modes += [(0, k, 0.25, 0.0, -1.0, w, 0.0), (0, k, 0.25, q, -1.0, w, q)]
+        return ModeTable("adr", [0.5], modes)

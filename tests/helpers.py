@@ -14,7 +14,9 @@ F64 = torch.float64
 def oracle_adr(case: syn.AdrCase, lattice="D2Q5", forcing=True, shifted=False):
     sysm = S.AdrCascade(case.a_phys, case.nu, case.g_tau * case.dt)
     xs = syn.coords((case.n, case.n))
-    mms = make_mms(sysm, lambda x, y, t: syn.adr_exact(case, x, y, t).unsqueeze(0), xs, dt=case.dt) if forcing else None
+    # the closed-form ADR_SEPARABLE forcing acts on the conserved component alone
+    mms = make_mms(sysm, lambda x, y, t: syn.adr_exact(case, x, y, t).unsqueeze(0), xs, dt=case.dt,
+                   conserved_only=True) if forcing else None
     tau = oracle.tau_vector(sysm, case.dt, tau_cons=case.tau_u, g_tau=case.g_tau)
     return oracle.Scheme(sysm, oracle.LATTICES[lattice], (case.n, case.n), case.dx, case.dt, tau,
                          mms=mms, shifted=shifted, Q0=[1.0, 0.0, 0.0])

@@ -111,7 +111,8 @@ def test_forced_adr_adjoint_matches_oracle():
     def make(tc):
         t = oracle.tau_vector(och_sys, case.dt, tau_cons=tc, g_tau=case.g_tau)
         xs = syn.coords((32, 32))
-        mms = make_mms(och_sys, lambda x, y, T: syn.adr_exact(case, x, y, T).unsqueeze(0), xs, dt=case.dt)
+        mms = make_mms(och_sys, lambda x, y, T: syn.adr_exact(case, x, y, T).unsqueeze(0), xs, dt=case.dt,
+                       conserved_only=True)
         return oracle.Scheme(och_sys, oracle.LATTICES["D2Q5"], (32, 32), case.dx, case.dt, t, mms=mms)
     Jo, go, gto = oracle.adjoint.misfit_and_grad(make, Q, tgt, 23, case.tau_u)
     assert abs(J - Jo) <= 1e-12 * abs(Jo)
