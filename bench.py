@@ -7,7 +7,7 @@ around rho = 1, T = 1, Mach 0.3.  A step is one collide-and-stream pass over the
 grid (one kernel launch).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload nsf|mhd|adr] [--precision fp32|fp64|fp16]
+                  [--workload nsf|mhd|adr|nsf12|mhd18] [--precision fp32|fp64|fp16]
 
 --impl reference times the CPU FP64 oracle on bounded samples of the same workload.
 Under torchrun (N > 1) every rank advances its own replica (weak scaling, no exchange)
@@ -156,10 +156,18 @@ def make_case(workload, n=None):
         return syn.MhdCase(n=n or 256)
     if workload == "adr":
         return syn.AdrCase(n=n or 64)
+    if workload == "nsf12":
+        return syn.NsfPaperCase(n=n or 1024)
+    if workload == "mhd18":
+        return syn.MhdPaper2DCase(n=n or 512)
     raise ValueError(workload)
 
 
 def fields(workload, case):
+    if workload == "nsf12":
+        return case.table("nsf12").augmented(syn.coords((case.n, case.n)), 0.0)
+    if workload == "mhd18":
+        return case.table().augmented(syn.coords((case.n, case.n)), 0.0)
     return {"nsf": syn.nsf_fields, "mhd": syn.mhd_fields, "adr": syn.adr_fields}[workload](case)
 
 
@@ -169,11 +177,30 @@ def scheme(W, L, workload, case, prec):
         return W.nsf_scheme(case, p)
     if workload == "mhd":
         return W.mhd_scheme(case, p)
+    if workload == "nsf12":
+        return W.nsf12_scheme(case, p)
+    if workload == "mhd18":
+        return W.mhd18_scheme(case, p)
     return W.adr_scheme(case, p)
 
 
 def kq(workload):
-    return {"nsf": (10, 9), "mhd": (11, 19), "adr": (3, 5)}[workload]
+    return {"nsf": (10, 9), "mhd": (11, 19), "adr": (3, 5), "nsf12": (12, 5), "mhd18": (18, 5)}[workload]
+
+
+LATTICE_NAME = {"nsf": "d2q9", "mhd": "d3q19", "adr": "d2q5", "nsf12": "d2q5", "mhd18": "d2q5"}
+
+
+def config_of(workload, case, precision, K, q, ws=1):
+    """The workload description both arms report."""
+    dim = 3 if workload == "mhd" else 2
+    grid = "x".join([str(case.n)] * dim)
+    bytes_launch = 2 * K * q * STORE_BYTES[precision] * case.n ** dim
+    return {"workload": f"{workload}_{LATTICE_NAME[workload]}_{grid}_{precision}", "grid": [case.n] * dim,
+            "components": K, "velocities": q, "precision": precision,
+            "l2": f"inputs larger than L2 (each population buffer {bytes_launch / 2 / 1e6:.0f} MB > 126 MB)"
+            if bytes_launch / 2 > 126e6 else f"L2-resident ({bytes_launch / 1e6:.1f} MB of populations)",
+            "parallelism": f"replicas x{ws}"}
 
 
 def cells(workload, case):
@@ -292,7 +319,9 @@ def run_variants(L, W, args, stream, peak, probe_fp64=None):
     t0 = time.perf_counter()
     for wl, prec, n, steps in (("nsf", "fp64", 1024, 100), ("nsf", "fp16", 1024, 1000),
                                ("mhd", "fp32", 256, 50), ("mhd", "fp16", 256, 50),
-                               ("adr", "fp64", 64, 500)):
+                               ("nsf12", "fp32", 1024, 500), ("nsf12", "fp16", 1024, 500),
+                               ("nsf12", "fp64", 1024, 100), ("mhd18", "fp32", 512, 500),
+                               ("mhd18", "fp64", 512, 100), ("adr", "fp64", 64, 500)):
         # the 64^2 case is launch-latency bound: its 500 steps replay as one CUDA graph
         r, st = measure_grid(L, W, wl, prec, n, steps, 5 if wl != "adr" else 500, stream, graph=(wl == "adr"))
         st.close()
@@ -399,11 +428,7 @@ def run_ours(args):
         "metric": "Lattice updates/s", "value": value, "unit": "LUP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAME[args.precision], "data": "synthetic",
-        "config": {"workload": f"{args.workload}_d2q9_{case.n}x{case.n}_{args.precision}" if args.workload == "nsf"
-                   else f"{args.workload}_{case.n}_{args.precision}",
-                   "grid": [case.n] * (3 if args.workload == "mhd" else 2), "components": K, "velocities": q,
-                   "precision": args.precision, "l2": "inputs larger than L2 (each population buffer "
-                   f"{bytes_launch / 2 / 1e6:.0f} MB > 126 MB)", "parallelism": f"replicas x{ws}"},
+        "config": config_of(args.workload, case, args.precision, K, q, ws),
         "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "finite": finite, "launch": launch,
         "clocks": clk.summary(),
     }
@@ -430,6 +455,12 @@ def _oracle_scheme(workload, case, shape):
     elif workload == "mhd":
         sysm = S.MhdCurrent(case.gamma, case.eta, case.g_tau * case.dt)
         lat = "D3Q19"
+    elif workload == "nsf12":
+        sysm = S.NsfConservedGradients(case.gamma, case.R, case.mu, case.kappa, case.g_tau * case.dt)
+        lat = "D2Q5"
+    elif workload == "mhd18":
+        sysm = S.MhdPowell2D(case.gamma, case.mu, case.kappa, case.eta, case.g_tau * case.dt)
+        lat = "D2Q5"
     else:
         sysm = S.AdrCascade(case.a_phys, case.nu, case.g_tau * case.dt)
         lat = "D2Q5"
@@ -494,8 +525,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}_{case.n}_{args.precision}", "grid": case.n, "components": K,
-                   "velocities": q},
+        "config": config_of(args.workload, case, args.precision, K, q, ws),
         "cpu_baseline": {"value": value, "unit": "LUP/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "LUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -507,7 +537,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nsf", choices=["nsf", "mhd", "adr"])
+    ap.add_argument("--workload", default="nsf", choices=["nsf", "mhd", "adr", "nsf12", "mhd18"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
     ap.add_argument("--n", type=int, default=None, help="grid size override")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

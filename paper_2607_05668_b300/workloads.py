@@ -61,3 +61,29 @@ def forced_scheme(table, system, lattice, extent, scaling, f, precision=L.FP64, 
     return L.Scheme(system, lattice, extent, scaling, f, tau_lb=tau_lb, tau_R=tau_R, g_tau=g_tau,
                     precision=precision, mms=L.MMS_FOURIER, mms_modes=table.lbx_modes(),
                     mms_mean=list(table.mean), mms_conserved_only=conserved_only)
+
+
+# ------------------------------------------------------------- the paper's own cascades
+def nsf12_system(case):
+    """12-component NSF with conserved-gradient trackers (case: gamma, R, mu, kappa and a
+    cascade background state)."""
+    return L.System(L.NSF_CONS_TRACK, params=(case.gamma, case.R, case.mu, case.kappa),
+                    Q0=case.reference_state_cascade())
+
+
+def nsf12_scheme(case, precision=L.FP32_SHIFT, lattice=L.D2Q5):
+    """The paper's NSF recipe: diffusive dt = f dx^2, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
+    return L.Scheme(nsf12_system(case), lattice, (case.n, case.n), L.DIFFUSIVE, case.f,
+                    tau_R=case.tau_R, g_tau=case.g_tau, precision=precision)
+
+
+def mhd18_system(case):
+    """18-component 2D MHD with Powell cleaning (case: gamma, mu, kappa, eta)."""
+    return L.System(L.MHD_POWELL_2D, params=(case.gamma, case.mu, case.kappa, case.eta),
+                    Q0=case.reference_state())
+
+
+def mhd18_scheme(case, precision=L.FP32_SHIFT, lattice=L.D2Q5):
+    """The paper's MHD recipe: acoustic dt = f dx, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
+    return L.Scheme(mhd18_system(case), lattice, (case.n, case.n), L.ACOUSTIC, case.f,
+                    tau_R=case.tau_R, g_tau=case.g_tau, precision=precision)
