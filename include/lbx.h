@@ -306,6 +306,10 @@ lbx_status lbx_batch_create(const lbx_scheme* const* schemes, int n, const doubl
 lbx_status lbx_batch_info(const lbx_batch* b, int* n, int64_t* total_cells, size_t* buffer_bytes);
 /* Advance every instance by n steps (asynchronous on the batch's stream). */
 lbx_status lbx_batch_step(lbx_batch* b, int64_t n);
+/* finite[j] = 1 when every stored population of instance j is finite, else 0 (one launch,
+ * one block per instance; synchronous).  Instances step independently, so a diverged
+ * instance does not disturb the others: the batched form of a stability sweep. */
+lbx_status lbx_batch_check_finite(lbx_batch* b, int* finite);
 lbx_status lbx_batch_synchronize(lbx_batch* b);
 /* Moments of instance j, float64 [K][cells_j] host array (synchronous). */
 lbx_status lbx_batch_moments(lbx_batch* b, int j, double* Q_out);

@@ -889,7 +889,7 @@ struct BatchInst {
   long long off;
 };
 
-template <class Lat, template <typename> class SysT, class St, int MODE>
+template <class Lat, template <typename> class SysT, class St, int MODE, bool FOURIER = false>
 __global__ void k_step_batch(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
                              const BatchInst<typename St::C>* __restrict__ insts, const int2* __restrict__ tiles,
                              int ntiles, const long long* __restrict__ step_ptr, int step_rel) {
@@ -901,7 +901,7 @@ __global__ void k_step_batch(const typename St::S* __restrict__ A, typename St::
     const int c = tl.y + (int)threadIdx.x;
     if (c < p.ncell) {
       const int y = c / p.nx;
-      step_node<Lat, SysT, St, MODE>(A + off, B + off, p, c - y * p.nx, y, 0, step);
+      step_node<Lat, SysT, St, MODE, 128, FOURIER>(A + off, B + off, p, c - y * p.nx, y, 0, step);
     }
   }
 }

@@ -674,8 +674,17 @@ struct OpsImpl {
     return cudaGetLastError();
   }
   static const void* step_fn() { return (const void*)k_step<Lat, SysT, St, MODE, 128>; }
-  static cudaError_t batch_step(const void* A, void* B, const void* insts, const int2* tiles, int ntiles,
+  static cudaError_t batch_step(const void* A, void* B, const void* insts, const int2* tiles, int ntiles, int fourier,
                                 const long long* step_ptr, int step_rel, int grid, int block, cudaStream_t strm) {
+    if (fourier) {
+      if (MODE == MODE_SMEM) {
+        cudaError_t prep = prepare((const void*)k_step_batch<Lat, SysT, St, MODE, true>, smem(block));
+        if (prep != cudaSuccess) return prep;
+      }
+      k_step_batch<Lat, SysT, St, MODE, true><<<grid, block, smem(block), strm>>>(
+          (const S*)A, (S*)B, (const BatchInst<C>*)insts, tiles, ntiles, step_ptr, step_rel);
+      return cudaGetLastError();
+    }
     if (MODE == MODE_SMEM) {
       cudaError_t prep = prepare((const void*)k_step_batch<Lat, SysT, St, MODE>, smem(block));
       if (prep != cudaSuccess) return prep;

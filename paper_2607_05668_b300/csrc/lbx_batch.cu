@@ -38,6 +38,11 @@ struct lbx_batch {
   double* d_tab64 = nullptr;
   float* d_tab32 = nullptr;
   long long* d_step = nullptr;
+  MmsMode* d_modes = nullptr;        // FOURIER forcing: every instance's mode table
+  std::vector<long long> mode_off;   // first mode of instance j
+  long long* d_eoff = nullptr;       // element offset and count of every instance (finite check)
+  long long* d_ecnt = nullptr;
+  int* d_flags = nullptr;
   long long step = 0;
   int2* d_tiles = nullptr;
   int ntiles = 0;
@@ -69,6 +74,7 @@ static void make_view(const lbx_batch* b, int j, lbx_state* v) {
   v->d_feq0 = b->d_feq0 + (size_t)j * b->K * b->q;
   v->d_mms_tab64 = b->d_tab64 ? b->d_tab64 + b->tab_off[j] : nullptr;
   v->d_mms_tab32 = b->d_tab32 ? b->d_tab32 + b->tab_off[j] : nullptr;
+  v->d_mms_modes = b->d_modes ? b->d_modes + b->mode_off[j] : nullptr;
   for (int k = 0; k < KMAX; ++k) v->scale[k] = 1.0;
   refresh_params(v);
 }
@@ -83,6 +89,10 @@ static void free_batch(lbx_batch* b) {
   cudaFree(b->d_tab64);
   cudaFree(b->d_tab32);
   cudaFree(b->d_step);
+  cudaFree(b->d_modes);
+  cudaFree(b->d_eoff);
+  cudaFree(b->d_ecnt);
+  cudaFree(b->d_flags);
   cudaFree(b->d_tiles);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -110,8 +120,34 @@ static lbx_status build_tiles(lbx_batch* b, int block) {
 }
 
 static cudaError_t launch_step(lbx_batch* b, const void* A, void* B, int rel) {
-  return b->ops.batch_step(A, B, b->d_insts, b->d_tiles, b->ntiles, b->d_step, rel, b->nsm * b->cfg.ctas_per_sm,
-                           b->cfg.block, b->stream);
+  return b->ops.batch_step(A, B, b->d_insts, b->d_tiles, b->ntiles, b->d_modes != nullptr, b->d_step, rel,
+                           b->nsm * b->cfg.ctas_per_sm, b->cfg.block, b->stream);
+}
+
+// flags[j] = 1 if any stored population of instance j is NaN or infinite; block j walks
+// the instance's elements with a block-size stride.
+template <typename S>
+__global__ void k_batch_nonfinite(const S* __restrict__ A, const long long* __restrict__ off,
+                                  const long long* __restrict__ cnt, int* __restrict__ flags) {
+  const int j = blockIdx.x;
+  const S* a = A + off[j];
+  int bad = 0;
+  for (long long e = threadIdx.x; e < cnt[j]; e += blockDim.x) {
+    float vf;
+    double vd;
+    if constexpr (sizeof(S) == 2) {
+      vf = __half2float(a[e]);
+      bad |= !isfinite(vf);
+    } else if constexpr (sizeof(S) == 4) {
+      vf = a[e];
+      bad |= !isfinite(vf);
+    } else {
+      vd = a[e];
+      bad |= !isfinite(vd);
+    }
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) flags[j] = bad;
 }
 
 extern "C" lbx_status lbx_batch_create(const lbx_scheme* const* schemes, int n, const double* const* Q,
@@ -130,8 +166,6 @@ extern "C" lbx_status lbx_batch_create(const lbx_scheme* const* schemes, int n, 
   }
   if (s0.d.precision == LBX_FP16_SCALED)
     return fail(LBX_ERR_UNSUPPORTED, "lbx_batch_create: FP16_SCALED storage is not batched");
-  if (s0.d.mms == LBX_MMS_FOURIER)
-    return fail(LBX_ERR_UNSUPPORTED, "lbx_batch_create: FOURIER forcing is not batched");
   auto* b = new lbx_batch();
   b->n = n;
   b->K = s0.sys.K;
@@ -232,6 +266,47 @@ extern "C" lbx_status lbx_batch_create(const lbx_scheme* const* schemes, int n, 
     }
     cudaFree(dQ);
     CKB(e);
+  }
+  if (s0.d.mms == LBX_MMS_FOURIER) {
+    std::vector<MmsMode> md;
+    for (int j = 0; j < n; ++j) {
+      b->mode_off.push_back((long long)md.size());
+      for (int m = 0; m < b->sch[j].d.mms_n_modes; ++m) {
+        const lbx_mms_mode& a = b->sch[j].modes[m];
+        MmsMode o{};
+        for (int d = 0; d < 3; ++d) o.k2pi[d] = 2.0 * M_PI * a.k[d];
+        o.amp = a.amp;
+        o.phase = a.phase;
+        o.sigma = a.sigma;
+        o.omega = a.omega;
+        o.psi = a.psi;
+        o.p = a.p;
+        md.push_back(o);
+      }
+    }
+    CKB(cudaMalloc((void**)&b->d_modes, sizeof(MmsMode) * md.size()));
+    CKB(cudaMemcpy(b->d_modes, md.data(), sizeof(MmsMode) * md.size(), cudaMemcpyHostToDevice));
+    // the instance parameters were filled before the tables existed: fill them again
+    for (int j = 0; j < n; ++j) {
+      lbx_state v;
+      make_view(b, j, &v);
+      if (b->precision == LBX_FP64)
+        reinterpret_cast<BatchInst<double>*>(insts.data())[j].p = v.pd;
+      else
+        reinterpret_cast<BatchInst<float>*>(insts.data())[j].p = v.pf;
+    }
+  }
+  {
+    std::vector<long long> eo(n), ec(n);
+    for (int j = 0; j < n; ++j) {
+      eo[j] = b->off[j];
+      ec[j] = (long long)b->K * b->q * b->sch[j].ncell;
+    }
+    CKB(cudaMalloc((void**)&b->d_eoff, sizeof(long long) * n));
+    CKB(cudaMalloc((void**)&b->d_ecnt, sizeof(long long) * n));
+    CKB(cudaMalloc((void**)&b->d_flags, sizeof(int) * n));
+    CKB(cudaMemcpy(b->d_eoff, eo.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+    CKB(cudaMemcpy(b->d_ecnt, ec.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
   }
   CKB(cudaMalloc(&b->d_insts, insts.size()));
   CKB(cudaMemcpy(b->d_insts, insts.data(), insts.size(), cudaMemcpyHostToDevice));
@@ -418,4 +493,22 @@ extern "C" lbx_status lbx_batch_tune(lbx_batch* b, int trials, char* report, siz
 extern "C" void lbx_batch_destroy(lbx_batch* b) {
   if (b) cudaStreamSynchronize(b->stream);
   free_batch(b);
+}
+
+extern "C" lbx_status lbx_batch_check_finite(lbx_batch* b, int* finite) {
+  if (!b || !finite) return fail(LBX_ERR_ARG, "lbx_batch_check_finite: null argument");
+  const void* A = b->cur();
+  cudaError_t e = cudaSuccess;
+  switch (b->ops.elem_bytes) {
+    case 2: k_batch_nonfinite<__half><<<b->n, 256, 0, b->stream>>>((const __half*)A, b->d_eoff, b->d_ecnt, b->d_flags); break;
+    case 4: k_batch_nonfinite<float><<<b->n, 256, 0, b->stream>>>((const float*)A, b->d_eoff, b->d_ecnt, b->d_flags); break;
+    default: k_batch_nonfinite<double><<<b->n, 256, 0, b->stream>>>((const double*)A, b->d_eoff, b->d_ecnt, b->d_flags);
+  }
+  e = cudaGetLastError();
+  std::vector<int> h(b->n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), b->d_flags, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_batch_check_finite: %s", cudaGetErrorString(e));
+  for (int j = 0; j < b->n; ++j) finite[j] = h[j] ? 0 : 1;
+  return LBX_OK;
 }

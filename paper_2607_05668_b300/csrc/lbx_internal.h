@@ -38,7 +38,8 @@ struct Ops {
   const void* (*step_fn)();
   bool reg;
   // batched persistent step: insts = BatchInst<C>[n] on the device
-  cudaError_t (*batch_step)(const void* A, void* B, const void* insts, const int2* tiles, int ntiles,
+  // fourier: the instances carry mode-table forcing (the forced instantiation)
+  cudaError_t (*batch_step)(const void* A, void* B, const void* insts, const int2* tiles, int ntiles, int fourier,
                             const long long* step_ptr, int step_rel, int grid, int block, cudaStream_t);
   const void* (*batch_fn)();
   size_t (*smem_bytes)(int threads);   // dynamic shared memory of a step launch

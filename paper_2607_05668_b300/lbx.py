@@ -356,6 +356,7 @@ class BatchConfig(C.Structure):
 _sig("lbx_batch_create", C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P), _P, C.POINTER(_P)])
 _sig("lbx_batch_info", C.c_int, [_P, _I, C.POINTER(C.c_int64), C.POINTER(C.c_size_t)])
 _sig("lbx_batch_step", C.c_int, [_P, C.c_int64])
+_sig("lbx_batch_check_finite", C.c_int, [_P, _I])
 _sig("lbx_batch_synchronize", C.c_int, [_P])
 _sig("lbx_batch_moments", C.c_int, [_P, C.c_int, _P])
 _sig("lbx_batch_get_config", C.c_int, [_P, C.POINTER(BatchConfig)])
@@ -385,6 +386,12 @@ class Batch:
 
     def synchronize(self):
         check(_lib.lbx_batch_synchronize(self._h))
+
+    def check_finite(self):
+        """Per instance: True when all its populations are finite (lbx_batch_check_finite)."""
+        out = (C.c_int * self.n)()
+        check(_lib.lbx_batch_check_finite(self._h, out))
+        return [bool(v) for v in out]
 
     def moments(self, j):
         s = self.schemes[j]

@@ -685,3 +685,11 @@ class AdrPaperCase:
         for k, w in (((1, 1, 0), TWO_PI * (self.a[0] + self.a[1])), ((1, -1, 0), TWO_PI * (self.a[0] - self.a[1]))):
             modes += [(0, k, 0.25, 0.0, -1.0, w, 0.0), (0, k, 0.25, q, -1.0, w, q)]
         return ModeTable("adr", [0.5], modes)
+
+
+def burgers_stability_grid(mach, omega, f=0.2):
+    """(Ma, omega, A, tau_LB) for every pair of a Burgers stability sweep (Sec. 3, Burgers):
+    Ma = lambda A / c_s with lambda = dt/dx = f (acoustic) and c_s^2 = 1/3, so the
+    equilibria stay monotone in u exactly while Ma <= c_s; tau_LB = 1/omega."""
+    cs = 1.0 / math.sqrt(3.0)
+    return [(float(m), float(w), float(m) * cs / f, 1.0 / float(w)) for w in omega for m in mach]

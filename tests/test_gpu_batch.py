@@ -1,5 +1,7 @@
 """Batched persistent launch (many uneven ADR grids) against single-grid runs and the
 oracle; graph replay, parity of odd step counts and the autotuner's no-advance rule."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -89,3 +91,59 @@ def test_batch_rejects_mixed_families_and_fp16():
     with pytest.raises(lbx.LbxError) as e:
         lbx.Batch([W.adr_scheme(c, lbx.FP16_SCALED)], [syn.adr_fields(c)])
     assert e.value.name == "ERR_UNSUPPORTED"
+
+
+# ------------------------------------------------ forced batches: the Burgers stability map
+
+def _burgers_batch(N, grid, steps=None):
+    gsys = lbx.System(lbx.BURGERS, (), (0.0,))
+    xs = syn.coords((N, N))
+    schemes, fields = [], []
+    for (m, w, A, tau) in grid:
+        tab = syn.burgers_table(A)
+        schemes.append(W.forced_scheme(tab, gsys, lbx.D2Q5, (N, N), lbx.ACOUSTIC, 0.2, tau_lb=tau))
+        fields.append(tab.augmented(xs, 0.0))
+    b = lbx.Batch(schemes, fields)
+    b.step(int(round(N / 0.2)) if steps is None else steps)      # to t = 1
+    return b, schemes, fields
+
+
+def _diverged(b, grid):
+    """Divergent: a non-finite population, or |u| beyond ten times the manufactured amplitude."""
+    fin = b.check_finite()
+    return [(not f) or float(b.moments(j).abs().max()) > 10.0 * grid[j][2] for j, f in enumerate(fin)]
+
+
+def test_forced_batch_equals_single_forced_runs_bitwise():
+    N, steps = 48, 37
+    grid = syn.burgers_stability_grid([0.3, 0.45, 0.55], [1.2, 1.9])
+    b, schemes, fields = _burgers_batch(N, grid, steps)
+    assert all(b.check_finite())
+    for j in (0, 3, 5):
+        st = lbx.State(schemes[j], fields[j])
+        st.step(steps)
+        assert torch.equal(b.moments(j), st.moments())
+    b.close()
+
+
+def test_burgers_stability_boundary_tightens_toward_the_monotone_bound():
+    """Sec. 3 (Burgers stability map): run every (Ma, omega) pair to t = 1 and classify it.
+    Near omega = 2 the empirical boundary approaches Ma = c_s = 1/sqrt(3) (the equilibria
+    stop being monotone in u) from above and tightens under refinement; the verification
+    working point Ma = 0.45 is stable; and with heavier relaxation (omega = 1) the boundary
+    rises well above c_s."""
+    mach = [0.45, 0.5, 0.55, 0.6, 0.65, 0.7, 0.8, 1.0, 1.2]
+    bound = {}
+    for N in (64, 256):
+        for w in (1.0, 1.99):
+            grid = syn.burgers_stability_grid(mach, [w])
+            b, _, _ = _burgers_batch(N, grid)
+            div = _diverged(b, grid)
+            b.close()
+            stable = [g[0] for g, d in zip(grid, div) if not d]
+            assert 0.45 in stable, (N, w, div)
+            bound[(N, w)] = max(stable)
+    cs = 1.0 / math.sqrt(3.0)
+    print("stability boundary (max stable Ma):", bound)
+    assert cs - 0.05 <= bound[(256, 1.99)] <= bound[(64, 1.99)] <= cs + 0.15
+    assert bound[(256, 1.0)] >= 0.8 and bound[(64, 1.0)] >= 0.8

@@ -104,7 +104,7 @@ def test_forced_mhd_fp64_matches_oracle():
     assert err.max() <= 1e-12, err
 
 
-def test_forced_runs_reject_batches_and_bad_tables():
+def test_forced_runs_reject_bad_tables():
     tab = syn.burgers_table()
     gsys = W.table_system(tab, (), (0.0,))
     with pytest.raises(lbx.LbxError, match="primitive"):
@@ -113,9 +113,6 @@ def test_forced_runs_reject_batches_and_bad_tables():
     with pytest.raises(lbx.LbxError, match="modes"):
         lbx.Scheme(gsys, lbx.D2Q5, (16, 16), lbx.ACOUSTIC, 0.2, tau_R=0.2, mms=lbx.MMS_FOURIER,
                    mms_modes=[], mms_mean=[0.0])
-    sch = W.forced_scheme(tab, gsys, lbx.D2Q5, (16, 16), lbx.ACOUSTIC, 0.2, precision=lbx.FP32_SHIFT, tau_R=0.2)
-    with pytest.raises(lbx.LbxError, match="not batched"):
-        lbx.Batch([sch], [tab.augmented(syn.coords((16, 16)), 0.0)])
 
 
 # ----------------------------------------------------------- the paper's Table 3 at N = 512
