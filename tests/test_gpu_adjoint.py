@@ -78,7 +78,8 @@ def test_checkpoint_interval_does_not_change_the_result():
 
 def test_fp64_adjoint_against_central_differences():
     """h = 1e-4 central differences of the GPU FP64 forward: a random direction of the
-    initial density, single nodes of rho, and tau; 1e-5 relative."""
+    initial density, eight single nodes of rho (corners, edges, interior), and tau; 1e-5
+    relative."""
     N, steps, tau, h = 32, 60, 0.52, 1e-4
     case, mk = _nsf(N, tau)
     Q, tgt = syn.nsf_fields(case), syn.density_target(N)
@@ -91,7 +92,7 @@ def test_fp64_adjoint_against_central_differences():
     v[0] = torch.randn(Q[0].shape, dtype=F64, generator=torch.Generator().manual_seed(0))
     fd = (Jof(Q + h * v) - Jof(Q - h * v)) / (2 * h)
     assert abs(fd - float((g * v).sum())) <= 1e-5 * abs(fd)
-    for (yy, xx) in ((3, 5), (17, 29), (31, 0)):
+    for (yy, xx) in ((3, 5), (17, 29), (31, 0), (0, 31), (8, 8), (22, 13), (30, 30), (12, 2)):
         e = torch.zeros_like(Q)
         e[0, yy, xx] = 1.0
         fdn = (Jof(Q + h * e) - Jof(Q - h * e)) / (2 * h)
@@ -171,3 +172,28 @@ def test_linear_adr_adjoint_is_the_transposed_oracle_matrix_8x8():
         Jm = lbx.adjoint(sch, Q - h * v, steps, steps, tgt)[0]
         dd = float((gq * v).sum())
         assert abs((Jp - Jm) / (2 * h) - dd) <= 1e-9 * abs(dd) + 1e-12 * J / h
+
+
+def test_paper_nsf12_adjoint_matches_oracle_gradient():
+    """The adjoint of the paper's 12-component NSF (conserved-gradient trackers) on D2Q5,
+    FP64, against the oracle's reverse-mode gradient of its own forward."""
+    N, steps, tau = 24, 20, 0.55
+    c = syn.NsfPaperCase(n=N)
+    tab = c.table("nsf12")
+    Q = tab.augmented(syn.coords((N, N)), 0.0)
+    tgt = syn.density_target(N)
+
+    def gsch(t):
+        return lbx.Scheme(lbx.System(lbx.NSF_CONS_TRACK, params=(c.gamma, c.R, c.mu, c.kappa),
+                                     Q0=c.reference_state_cascade()),
+                          lbx.D2Q5, (N, N), lbx.DIFFUSIVE, c.f, tau_lb=t, g_tau=c.g_tau, precision=lbx.FP64)
+    J, g, gt = lbx.adjoint(gsch(tau), Q, steps, 6, tgt)
+    osys = oracle.systems.NsfConservedGradients(c.gamma, c.R, c.mu, c.kappa, c.g_tau * c.dt)
+
+    def make(tc):
+        t = oracle.tau_vector(osys, c.dt, tau_cons=tc, g_tau=c.g_tau)
+        return oracle.Scheme(osys, oracle.LATTICES["D2Q5"], (N, N), c.dx, c.dt, t)
+    Jo, go, gto = oracle.adjoint.misfit_and_grad(make, Q, tgt, steps, tau)
+    assert abs(J - Jo) <= 1e-12 * abs(Jo)
+    assert _rel(g, go) <= 1e-10
+    assert abs(gt - gto) <= 1e-10 * abs(gto)
