@@ -8,13 +8,17 @@ MMS section: trackers are initialised from the spatial derivatives of the fields
 By default the forcing is the residual of the whole augmented state Q+ (conserved and
 tracker components), as the paper's compiler forms it on Q+ (Sec. 4: the residual of the
 analytical profiles, injected into the update); for a tracker the 1/tau_grad terms of
-flux and source cancel and its forcing is d_t grad V + div(grad V (x) u).  With
+flux and source cancel and its forcing is d_t grad V + div(grad V (x) u).
+For a system with prescribed coefficient fields c(x, t) the divergence differentiates
+Phi(Q_ex(x, t); c(x, t)) along x, the coefficients included.  With
 `conserved_only` the trackers are left unforced (they then lag grad V by O(tau_grad)).
 """
 from __future__ import annotations
 
 import torch
 from torch.func import jvp
+
+from .systems import flux_at, source_at
 
 
 def _replace(xx, b, xb):
@@ -81,8 +85,9 @@ def mms_source_t(system, exact, xx, tt, conserved_only=False):
     div = torch.zeros_like(dQdt)
     for b in range(len(xx)):
         def flux_b(xb, b=b):
-            return system.flux(exact_augmented(system, exact, _replace(xx, b, xb), tt))[:nk, b]
+            xb_all = _replace(xx, b, xb)
+            return flux_at(system, exact_augmented(system, exact, xb_all, tt), xb_all, tt)[:nk, b]
         _, d = jvp(flux_b, (xx[b],), (torch.ones_like(xx[b]),))
         div = div + d
     Qp = exact_augmented(system, exact, xx, tt)
-    return dQdt + div - system.source(Qp)[:nk]
+    return dQdt + div - source_at(system, Qp, xx, tt)[:nk]

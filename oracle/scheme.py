@@ -13,6 +13,10 @@ Steps, in the paper's order and notation:
     midpoint t + dt/2;
   * reference/equilibrium shift (Sec. 2.4.3): f* = f - f^eq(Q0, F0), F0 = Phi(Q0).
 
+Prescribed coefficient fields c(x, t) (HCNSF porosity and solid velocity) are evaluated
+at the node coordinates x = (i, j, l) dx and at the time level of the state they multiply:
+t^n in the equilibrium flux and the state source of step n, t = 0 at initialisation.
+
 Arrays: populations f are [K, q, *grid], fields Q are [K, *grid], grid = (nz,) ny, nx.
 The streaming here pushes post-collision values to x + c_i with torch.roll, exactly as
 Eq. lbe_update is written.
@@ -24,6 +28,7 @@ import math
 import torch
 
 from .lattice import Lattice
+from .systems import flux_at, source_at
 
 F64 = torch.float64
 
@@ -70,14 +75,17 @@ class Scheme:
         self.mms = mms
         self.shifted = shifted
         self.Q0 = None if Q0 is None else torch.as_tensor(Q0, dtype=F64)
+        # node coordinates (x, y[, z]), x fastest, for prescribed coefficient fields
+        axes = [torch.arange(n, dtype=F64) * self.dx for n in self.shape]
+        self.xx = tuple(m.contiguous() for m in reversed(torch.meshgrid(*axes, indexing="ij")))
         if shifted:
             q0 = self.Q0.reshape((system.K,) + (1,) * len(self.shape))
             self.feq0 = self.feq(q0)      # [K, q, 1, ...] background equilibrium
         assert lattice.D == system.D
 
     # -- Eq. feq --------------------------------------------------------------------
-    def feq(self, Q):
-        Phi = self.sys.flux(Q)                       # [K, D, *grid]
+    def feq(self, Q, t=0.0):
+        Phi = flux_at(self.sys, Q, self.xx, t)       # [K, D, *grid]
         out = []
         for i, ci in enumerate(self.c):
             cphi = sum(ci[d] * Phi[:, d] for d in range(self.lat.D) if ci[d] != 0)
@@ -91,14 +99,14 @@ class Scheme:
             Q = Q + self.Q0.reshape((self.sys.K,) + (1,) * len(self.shape))
         return Q
 
-    def init(self, Q):
+    def init(self, Q, t=0.0):
         """Populations at the (shifted) equilibrium of the given fields (supplement,
         recipes paragraph)."""
-        f = self.feq(Q)
+        f = self.feq(Q, t)
         return f - self.feq0 if self.shifted else f
 
     def source_total(self, Q, t):
-        S = self.sys.source(Q)
+        S = source_at(self.sys, Q, self.xx, t)
         if self.mms is not None:
             Sm = self.mms(t + 0.5 * self.dt)          # all K components, or the conserved ones
             S = S + Sm if Sm.shape[0] == self.sys.K else torch.cat([S[: self.sys.n_cons] + Sm, S[self.sys.n_cons:]])
@@ -107,7 +115,7 @@ class Scheme:
     def collide(self, f, t):
         """Post-collision populations at every node (right-hand side of Eq. lbe_update)."""
         Q = self.moments(f)
-        fe = self.feq(Q)
+        fe = self.feq(Q, t)
         if self.shifted:
             fe = fe - self.feq0
         S = self.source_total(Q, t)

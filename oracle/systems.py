@@ -389,3 +389,100 @@ class MaxwellTM(System):
         z = 0 * ez
         return self.c * torch.stack([torch.stack([-hy, hx]), torch.stack([z, ez]),
                                      torch.stack([-ez, z])])
+
+
+class HomogenizedNsf3D(System):
+    """3D homogenized compressible Navier-Stokes-Fourier (Sec. 3, HCNSF; supplement, HCNSF
+    system), with prescribed porosity alpha(x, t) and solid velocity u_s(x, t).
+
+    Q = (rho, m(3), E, G_11, G_22, G_T(3), G_00, G_01, G_02, G_12), the paper's order, where
+    G_ab ~ (sym grad u)_ab and G_T ~ grad T, T = p / rho (gas constant 1),
+    p = (gamma-1)(E - |m|^2/(2 rho)),  tau_v = mu (2 G - 2/3 tr(G) I),
+    Phi_rho = m,  Phi_m = m (x) u + p I - alpha tau_v,
+    Phi_E = (E + p) u - alpha tau_v u - alpha kappa G_T,
+    Phi_{G_ab, c} = G_ab u_c - (delta_ac u_b + delta_bc u_a) / (2 tau_grad)   (sym(I (x) u)),
+    Phi_{G_T,b, c} = G_T,b u_c - delta_bc T / tau_grad,
+    S_m = (1-alpha)/eta (rho u_s - m),  S_E = S_m . u,  S_G = -G / tau_grad.
+
+    `fields(xx, t)` returns (alpha, u_s,0, u_s,1, u_s,2) at node coordinates xx and time t;
+    flux and source take those values as `cf`.
+    """
+    name = "hcnsf"
+    K = 14
+    D = 3
+    n_cons = 5
+    prescribed = True
+    # (a, b) of the symmetric-gradient components, by position in Q
+    SYM = {5: (1, 1), 6: (2, 2), 10: (0, 0), 11: (0, 1), 12: (0, 2), 13: (1, 2)}
+
+    def __init__(self, gamma, mu, kappa, eta, tau_grad, fields):
+        self.gamma, self.mu, self.kappa, self.eta = float(gamma), float(mu), float(kappa), float(eta)
+        self.tau_grad = float(tau_grad)
+        self.fields = fields
+
+    def _parts(self, Q):
+        rho, m, E = Q[0], Q[1:4], Q[4]
+        u = m / rho
+        p = (self.gamma - 1.0) * (E - 0.5 * (m[0] * u[0] + m[1] * u[1] + m[2] * u[2]))
+        G = [[None] * 3 for _ in range(3)]
+        for k, (a, b) in self.SYM.items():
+            G[a][b] = G[b][a] = Q[k]
+        return rho, m, E, u, p, G, Q[7:10]
+
+    def flux(self, Q, cf):
+        alpha = cf[0]
+        rho, m, E, u, p, G, GT = self._parts(Q)
+        tr = G[0][0] + G[1][1] + G[2][2]
+        tv = [[self.mu * (2.0 * G[a][b] - (2.0 / 3.0) * tr * (1.0 if a == b else 0.0)) for b in range(3)]
+              for a in range(3)]
+        T = p / rho
+        itg = 1.0 / self.tau_grad
+        rows = [None] * self.K
+        rows[0] = torch.stack([m[0], m[1], m[2]])
+        for a in range(3):
+            rows[1 + a] = torch.stack([m[a] * u[b] + (p if a == b else 0 * p) - alpha * tv[a][b]
+                                       for b in range(3)])
+        rows[4] = torch.stack([(E + p) * u[b] - alpha * (tv[b][0] * u[0] + tv[b][1] * u[1] + tv[b][2] * u[2])
+                               - alpha * self.kappa * GT[b] for b in range(3)])
+        for k, (a, b) in self.SYM.items():
+            rows[k] = torch.stack([Q[k] * u[c] - 0.5 * itg * ((u[b] if a == c else 0 * u[b])
+                                                              + (u[a] if b == c else 0 * u[a]))
+                                   for c in range(3)])
+        for b in range(3):
+            rows[7 + b] = torch.stack([GT[b] * u[c] - (T * itg if b == c else 0 * T) for c in range(3)])
+        return torch.stack(rows)
+
+    def source(self, Q, cf):
+        alpha, us = cf[0], cf[1:4]
+        rho, m, E, u, p, G, GT = self._parts(Q)
+        drag = (1.0 - alpha) / self.eta
+        S = torch.zeros_like(Q)
+        for a in range(3):
+            S[1 + a] = drag * (rho * us[a] - m[a])
+        S[4] = S[1] * u[0] + S[2] * u[1] + S[3] * u[2]
+        S[5:] = -Q[5:] / self.tau_grad
+        return S
+
+    def parents(self, Qc):
+        rho, m, E = Qc[0], Qc[1:4], Qc[4]
+        u = m / rho
+        p = (self.gamma - 1.0) * (E - 0.5 * (m[0] * u[0] + m[1] * u[1] + m[2] * u[2]))
+        return [u[0], u[1], u[2], p / rho]
+
+    def trackers_from_grads(self, dP):
+        sym = lambda a, b: 0.5 * (dP[a][b] + dP[b][a])
+        return [sym(1, 1), sym(2, 2), dP[3][0], dP[3][1], dP[3][2], sym(0, 0), sym(0, 1), sym(0, 2), sym(1, 2)]
+
+
+def flux_at(system, Q, xx, t):
+    """Phi(Q), or Phi(Q; c(x, t)) for a system with prescribed coefficient fields."""
+    if getattr(system, "prescribed", False):
+        return system.flux(Q, system.fields(xx, t))
+    return system.flux(Q)
+
+
+def source_at(system, Q, xx, t):
+    """S(Q), or S(Q; c(x, t)) for a system with prescribed coefficient fields."""
+    if getattr(system, "prescribed", False):
+        return system.source(Q, system.fields(xx, t))
+    return system.source(Q)

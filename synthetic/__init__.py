@@ -331,7 +331,8 @@ def adr_exact_stack(case: AdrCase):
 PRIMITIVES = {"adr": ("u",), "nsf": ("rho", "u", "v", "p"),
               "mhd": ("rho", "u_x", "u_y", "u_z", "B_x", "B_y", "B_z", "p"),
               "burgers": ("u",), "euler": ("rho", "u", "v", "p"), "maxwell": ("E_z", "H_x", "H_y"),
-              "nsf12": ("rho", "u", "v", "p"), "mhd18": ("rho", "u", "v", "p", "B_x", "B_y")}
+              "nsf12": ("rho", "u", "v", "p"), "mhd18": ("rho", "u", "v", "p", "B_x", "B_y"),
+              "hcnsf": ("rho", "u_x", "u_y", "u_z", "p")}
 
 
 @dataclass
@@ -361,6 +362,9 @@ class ModeTable:
             rho, u, v, p, bx, by = V
             E = p / (g - 1.0) + 0.5 * rho * (u * u + v * v) + 0.5 * (bx * bx + by * by)
             return torch.stack([rho, rho * u, rho * v, E, bx, by])
+        if self.family == "hcnsf":
+            rho, u, p = V[0], V[1:4], V[4]
+            return torch.stack([rho] + [rho * c for c in u] + [p / (g - 1.0) + 0.5 * rho * sum(c * c for c in u)])
         if self.family in ("nsf", "euler", "nsf12"):
             rho, u, v, p = V
             return torch.stack([rho, rho * u, rho * v, p / (g - 1.0) + 0.5 * rho * (u * u + v * v)])
@@ -401,6 +405,14 @@ class ModeTable:
         elif self.family == "mhd":
             G = lambda c, b: self.gradient(xs, t, 4 + c, b)
             tr = [G(2, 1) - G(1, 2), G(0, 2) - G(2, 0), G(1, 0) - G(0, 1)]
+        elif self.family == "hcnsf":
+            # sym grad u and grad T (T = p/rho) in the paper's order
+            V = self.primitives(xs, t)
+            rho, p = V[0], V[4]
+            Gs = [[self.gradient(xs, t, q, b) for b in range(3)] for q in range(5)]
+            sym = lambda a, b: 0.5 * (Gs[1 + a][b] + Gs[1 + b][a])
+            gT = [(Gs[4][b] - p / rho * Gs[0][b]) / rho for b in range(3)]
+            tr = [sym(1, 1), sym(2, 2)] + gT + [sym(0, 0), sym(0, 1), sym(0, 2), sym(1, 2)]
         elif self.family in ("nsf12", "mhd18"):
             # gradients of the conserved fields by the product rule
             V = self.primitives(xs, t)
@@ -445,6 +457,27 @@ def _product_modes(p, amp, fx, fy, kx, ky, omega, psi):
     if (fx, fy) == ("sin", "sin"):
         return [(p, minus, h, q, 0.0, omega, psi), (p, plus, -h, q, 0.0, omega, psi)]
     return [(p, plus, h, q, 0.0, omega, psi), (p, minus, h, q, 0.0, omega, psi)]
+
+
+def _trig_product(p, amp, factors, omega, psi):
+    """amp prod_d f_d(2 pi k_d x_d) cos(omega t + psi), f_d in {sin, cos}, as sine modes:
+    cos a = sin(a + pi/2) and sin a sin b = [sin(a - b + pi/2) - sin(a + b + pi/2)]/2, applied
+    factor by factor (a product of three factors becomes four modes)."""
+    q = 0.5 * math.pi
+
+    def factor(d, fn, kd):
+        return tuple(kd if e == d else 0 for e in range(3)), (0.0 if fn == "sin" else q)
+
+    k0, ph0 = factor(0, *factors[0])
+    terms = [(float(amp), k0, ph0)]                 # (amplitude, k, phase) of sin(2 pi k.x + phase)
+    for d in range(1, len(factors)):
+        k1, ph1 = factor(d, *factors[d])
+        out = []
+        for (a, k, ph) in terms:
+            out.append((0.5 * a, tuple(k[e] - k1[e] for e in range(3)), ph - ph1 + q))
+            out.append((-0.5 * a, tuple(k[e] + k1[e] for e in range(3)), ph + ph1 + q))
+        terms = out
+    return [(p, k, a, ph, 0.0, omega, psi) for (a, k, ph) in terms]
 
 
 def burgers_table(A=1.3):
@@ -693,3 +726,86 @@ def burgers_stability_grid(mach, omega, f=0.2):
     equilibria stay monotone in u exactly while Ma <= c_s; tau_LB = 1/omega."""
     cs = 1.0 / math.sqrt(3.0)
     return [(float(m), float(w), float(m) * cs / f, 1.0 / float(w)) for w in omega for m in mach]
+
+
+@dataclass
+class HcnsfPaperCase:
+    """The paper's 3D homogenized NSF manufactured flow (supplement, HCNSF MMS section) in the
+    units its scales divide out: rho0 = 1, c_s = sqrt(p0/rho0) = 1, p0 = 1, mean sound speed
+    c_bar = sqrt(gamma), drift U0 = Ma c_bar with Ma = 0.5, amplitude A = 0.2;
+    mu = kappa = 3.52 Pa s / (rho0 c_s L) and eta = 0.000348 s c_s / L with rho0 = 1.225 kg/m^3,
+    c_s = 287.4 m/s, L = 1 m.  The prescribed fields and the solid displacement are read in
+    the same units (amplitudes in c_s, time in L/c_s).
+    Recipe: acoustic f = 0.05, tau_R = 10 (double) or 20 (float), g_tau = 3; N = 32 .. 256."""
+    n: int
+    gamma: float = 1.4
+    A: float = 0.2
+    Ma: float = 0.5
+    f: float = 0.05
+    tau_R: float = 10.0
+    g_tau: float = 3.0
+    alpha_mean: float = 0.5
+    alpha_amp: float = 0.1
+    rot: float = 0.2
+    osc: float = 0.1
+    c: tuple = (0.1, -0.1, 0.05)
+
+    @property
+    def mu(self):
+        return 3.52 / (1.225 * 287.4)
+
+    @property
+    def kappa(self):
+        return 3.52 / (1.225 * 287.4)
+
+    @property
+    def eta(self):
+        return 0.000348 * 287.4
+
+    @property
+    def U0(self):
+        return self.Ma * math.sqrt(self.gamma)
+
+    @property
+    def dx(self):
+        return 1.0 / self.n
+
+    @property
+    def dt(self):
+        return self.f * self.dx
+
+    def reference_state(self):
+        U0 = self.U0
+        return [1.0, U0, U0, U0, 1.0 / (self.gamma - 1.0) + 1.5 * U0 * U0] + [0.0] * 9
+
+    def table(self):
+        """rho = 1 + A s0 c1 s2 cos t, u_x = U0 + A c0 s1 s2 sin t, u_y = U0 + A s0 c1 s2 sin t,
+        u_z = U0 + A s0 s1 c2 sin t, p = 1 + gamma (rho - 1) + A c0 s1 c2 sin t
+        (s_d = sin(2 pi x_d), c_d = cos(2 pi x_d))."""
+        A, g, s = self.A, self.gamma, -0.5 * math.pi
+        fac = lambda a, b, c: [(a, 1), (b, 1), (c, 1)]
+        modes = (_trig_product(0, A, fac("sin", "cos", "sin"), 1.0, 0.0)
+                 + _trig_product(1, A, fac("cos", "sin", "sin"), 1.0, s)
+                 + _trig_product(2, A, fac("sin", "cos", "sin"), 1.0, s)
+                 + _trig_product(3, A, fac("sin", "sin", "cos"), 1.0, s)
+                 + _trig_product(4, g * A, fac("sin", "cos", "sin"), 1.0, 0.0)
+                 + _trig_product(4, A, fac("cos", "sin", "cos"), 1.0, s))
+        U0 = self.U0
+        return ModeTable("hcnsf", [1.0, U0, U0, U0, 1.0], modes, gamma=g)
+
+    def prescribed(self, xx, t):
+        """(alpha, u_s,x, u_s,y, u_s,z) at coordinates xx and time t: u_s is a rotation
+        (amplitude rot) plus the translation c plus an oscillation (amplitude osc); alpha =
+        a_mean + a_amp [sin k xi_0 + sin k xi_1 + sin k xi_2 + 2 sin k xi_0 sin k xi_1 sin k xi_2],
+        xi = x - d, d = r(x) sin t + c t with r(x) the rotation's spatial pattern."""
+        t = t if torch.is_tensor(t) else torch.full_like(xx[0], float(t))
+        s = [torch.sin(TWO_PI * x) for x in xx]
+        c = [torch.cos(TWO_PI * x) for x in xx]
+        st, ct = torch.sin(t), torch.cos(t)
+        r = [self.rot * s[0] * c[1] * c[2], -self.rot * c[0] * s[1] * c[2], self.rot * c[0] * c[1] * s[2]]
+        us = [r[0] * ct + self.c[0] + self.osc * st * c[2],
+              r[1] * ct + self.c[1] + self.osc * ct * c[0],
+              r[2] * st + self.c[2] + self.osc * st * c[1]]
+        sx = [torch.sin(TWO_PI * (xx[d] - r[d] * st - self.c[d] * t)) for d in range(3)]
+        alpha = self.alpha_mean + self.alpha_amp * (sx[0] + sx[1] + sx[2] + 2.0 * sx[0] * sx[1] * sx[2])
+        return [alpha] + us

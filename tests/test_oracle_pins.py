@@ -654,3 +654,122 @@ def test_mhd18_flux_and_source_match_the_paper_expanded_system():
         for c, mc in enumerate((m0, m1)):
             torch.testing.assert_close(Phi[6 + k, c], Gk * mc / r - (V / tg if b == c else 0.0), rtol=1e-12, atol=1e-12)
         torch.testing.assert_close(Src[6 + k], -Gk / tg, rtol=1e-13, atol=1e-14)
+
+
+# --------------------------------------------- 3D homogenized NSF (prescribed alpha, u_s)
+
+def _hcnsf_state(rnd):
+    r, m0, m1, m2, E = rnd(0.8, 1.2), rnd(-0.5, 0.5), rnd(-0.5, 0.5), rnd(-0.5, 0.5), rnd(2.0, 3.0)
+    G11, G22, A0, A1, A2, G00, S01, S02, S12 = (rnd(-1, 1) for _ in range(9))
+    Q = torch.stack([r, m0, m1, m2, E, G11, G22, A0, A1, A2, G00, S01, S02, S12])
+    return Q, (r, m0, m1, m2, E, G11, G22, A0, A1, A2, G00, S01, S02, S12)
+
+
+def test_hcnsf_flux_and_source_match_the_paper_expanded_system():
+    """Supplement, HCNSF system (N = 14, T = p/rho): every flux component Phi_{i,j} and source
+    S_i of the expanded listing, multiplied out, at random states and random prescribed
+    alpha, u_s, against HomogenizedNsf3D (the paper's component order)."""
+    g, mu, K, eta, tg = 1.4, 0.03, 0.05, 0.11, 0.29
+    rnd = _uniform_draws(13)
+    al, us0, us1, us2 = rnd(0.0, 1.0), rnd(-0.3, 0.3), rnd(-0.3, 0.3), rnd(-0.3, 0.3)
+    sysm = S.HomogenizedNsf3D(g, mu, K, eta, tg, fields=None)
+    Q, (r, m0, m1, m2, E, G11, G22, A0, A1, A2, G00, S01, S02, S12) = _hcnsf_state(rnd)
+    cf = [al, us0, us1, us2]
+    Phi, Src = sysm.flux(Q, cf), sysm.source(Q, cf)
+    am = al * mu
+    msq = m0 ** 2 + m1 ** 2 + m2 ** 2
+    base = (g - 1) * E - g * msq / (2 * r) + msq / (2 * r)
+    want = {(0, 0): m0, (0, 1): m1, (0, 2): m2,
+            (1, 0): -4 * am * G00 / 3 + 2 * am * (G11 + G22) / 3 + m0 ** 2 / r + base,
+            (2, 1): -4 * am * G11 / 3 + 2 * am * (G00 + G22) / 3 + m1 ** 2 / r + base,
+            (3, 2): -4 * am * G22 / 3 + 2 * am * (G00 + G11) / 3 + m2 ** 2 / r + base,
+            (1, 1): -2 * am * S01 + m0 * m1 / r, (2, 0): -2 * am * S01 + m0 * m1 / r,
+            (1, 2): -2 * am * S02 + m0 * m2 / r, (3, 0): -2 * am * S02 + m0 * m2 / r,
+            (2, 2): -2 * am * S12 + m1 * m2 / r, (3, 1): -2 * am * S12 + m1 * m2 / r}
+    cube = (1 - g) / (2 * r ** 2)
+    want[(4, 0)] = (g * E * m0 / r - al * K * A0 + 2 * am * (G11 + G22) * m0 / (3 * r) - 4 * am * G00 * m0 / (3 * r)
+                    - 2 * am * (S01 * m1 + S02 * m2) / r + cube * (m0 ** 3 + m0 * m1 ** 2 + m0 * m2 ** 2))
+    want[(4, 1)] = (g * E * m1 / r - al * K * A1 + 2 * am * (G00 + G22) * m1 / (3 * r) - 4 * am * G11 * m1 / (3 * r)
+                    - 2 * am * (S01 * m0 + S12 * m2) / r + cube * (m1 ** 3 + m1 * m0 ** 2 + m1 * m2 ** 2))
+    want[(4, 2)] = (g * E * m2 / r - al * K * A2 + 2 * am * (G00 + G11) * m2 / (3 * r) - 4 * am * G22 * m2 / (3 * r)
+                    - 2 * am * (S02 * m0 + S12 * m1) / r + cube * (m2 ** 3 + m2 * m0 ** 2 + m2 * m1 ** 2))
+    u = (m0 / r, m1 / r, m2 / r)
+    T = (g - 1) * (E - msq / (2 * r)) / r
+    # trackers: listing rows 5..13 (G_u11, G_u22, G_aux 0..2, G_u00, S_u01, S_u02, S_u12)
+    for k, Gk, hit in ((5, G11, {1: u[1]}), (6, G22, {2: u[2]}), (10, G00, {0: u[0]}),
+                       (11, S01, {0: u[1] / 2, 1: u[0] / 2}), (12, S02, {0: u[2] / 2, 2: u[0] / 2}),
+                       (13, S12, {1: u[2] / 2, 2: u[1] / 2})):
+        for c in range(3):
+            want[(k, c)] = Gk * u[c] - hit.get(c, 0.0) / tg
+    for b, Ab in enumerate((A0, A1, A2)):
+        for c in range(3):
+            want[(7 + b, c)] = Ab * u[c] - (T / tg if b == c else 0.0)
+    for (i, j), v in want.items():
+        torch.testing.assert_close(Phi[i, j], v if torch.is_tensor(v) else torch.full_like(r, v),
+                                   rtol=1e-12, atol=1e-12)
+    assert len(want) == 42
+    drag = (1 - al) / eta
+    want_S = [0 * r, drag * (us0 * r - m0), drag * (us1 * r - m1), drag * (us2 * r - m2),
+              drag * (us0 * m0 + us1 * m1 + us2 * m2 - msq / r)]
+    want_S += [-Gk / tg for Gk in (G11, G22, A0, A1, A2, G00, S01, S02, S12)]
+    torch.testing.assert_close(Src, torch.stack(want_S), rtol=1e-12, atol=1e-13)
+
+
+def test_hcnsf_pure_fluid_reduces_to_the_2d_nsf_system():
+    """Sec. 3, HCNSF: alpha = 1 recovers plain compressible NSF.  At a state uniform in z
+    with m_z = 0 and trackers of the same velocity-gradient and temperature-gradient fields,
+    the conserved fluxes in x and y equal those of the 2D NSF system with primitive trackers
+    (gas constant 1, so T = p/rho), and the drag source vanishes."""
+    g, mu, K, tg = 1.4, 0.04, 0.06, 0.3
+    rnd = _uniform_draws(14)
+    r, m0, m1, E = rnd(0.8, 1.2), rnd(-0.5, 0.5), rnd(-0.5, 0.5), rnd(2.0, 3.0)
+    L00, L01, L10, L11, T0, T1 = (rnd(-1, 1) for _ in range(6))
+    z = 0 * r
+    Q3 = torch.stack([r, m0, m1, z, E, L11, z, T0, T1, z, L00, 0.5 * (L01 + L10), z, z])
+    one = torch.ones_like(r)
+    h = S.HomogenizedNsf3D(g, mu, K, 0.1, tg, fields=None)
+    P3 = h.flux(Q3, [one, rnd(-1, 1), rnd(-1, 1), rnd(-1, 1)])
+    S3 = h.source(Q3, [one, rnd(-1, 1), rnd(-1, 1), rnd(-1, 1)])
+    n = S.NsfPrimitive(g, 1.0, mu, K, tg)
+    P2 = n.flux(torch.stack([r, m0, m1, E, L00, L01, L10, L11, T0, T1]))
+    for (k3, k2) in ((0, 0), (1, 1), (2, 2), (4, 3)):
+        torch.testing.assert_close(P3[k3, :2], P2[k2], rtol=1e-13, atol=1e-14)
+    assert float(S3[:5].abs().max()) == 0.0
+
+
+def test_hcnsf_drag_relaxes_a_uniform_state_geometrically():
+    """Sec. 3, HCNSF source: at a uniform state only the drag acts, and one step of
+    Eq. lbe_update adds dt S to each moment: m^{n+1} - rho u_s = (1 - dt (1-alpha)/eta)
+    (m^n - rho u_s), E^{n+1} = E^n + dt (1-alpha)/eta (rho u_s - m^n) . u^n, rho unchanged."""
+    al, us, eta = 0.3, (0.2, -0.1, 0.05), 0.1
+    sysm = S.HomogenizedNsf3D(1.4, 0.01, 0.01, eta, 0.3,
+                              fields=lambda xx, t: [torch.full_like(xx[0], al)] + [torch.full_like(xx[0], v) for v in us])
+    shape, dx, dt = (3, 4, 5), 0.2, 0.01
+    sch = oracle.Scheme(sysm, oracle.LATTICES["D3Q7"], shape, dx, dt, torch.tensor([0.8] * 5 + [4.0] * 9, dtype=F64))
+    q = torch.tensor([1.1, 0.4, -0.2, 0.3, 3.0] + [0.0] * 9, dtype=F64)
+    Q = q.reshape(14, 1, 1, 1).expand(14, *shape).contiguous()
+    Q1 = sch.moments(sch.step(sch.init(Q), 0.0))
+    k = dt * (1 - al) / eta
+    for a in range(3):
+        torch.testing.assert_close(Q1[1 + a], torch.full(shape, (1 - k) * float(q[1 + a]) + k * 1.1 * us[a], dtype=F64),
+                                   rtol=1e-14, atol=1e-15)
+    dE = k * sum((1.1 * us[a] - float(q[1 + a])) * float(q[1 + a]) / 1.1 for a in range(3))
+    torch.testing.assert_close(Q1[4], torch.full(shape, 3.0 + dE, dtype=F64), rtol=1e-14, atol=1e-15)
+    torch.testing.assert_close(Q1[0], torch.full(shape, 1.1, dtype=F64), rtol=1e-15, atol=0)
+    assert float(Q1[5:].abs().max()) < 1e-16
+
+
+def test_hcnsf_exact_trackers_are_the_symmetric_velocity_and_temperature_gradients():
+    """Supplement, HCNSF MMS: the exact augmented state carries G_u = sym grad u and G_T =
+    grad(p/rho); the mode table's analytic trackers equal the oracle's forward-mode ones, and
+    the prescribed porosity stays inside [0, 1] as the paper states."""
+    case = syn.HcnsfPaperCase(n=8)
+    sysm = S.HomogenizedNsf3D(case.gamma, case.mu, case.kappa, case.eta, 0.1, fields=case.prescribed)
+    xs = syn.coords((8, 8, 8))
+    t = torch.full_like(xs[0], 0.6)
+    from oracle.mms import exact_augmented
+    torch.testing.assert_close(case.table().augmented(xs, t), exact_augmented(sysm, case.table().exact, xs, t),
+                               rtol=0, atol=1e-13)
+    for tt in (0.0, 0.4, 1.0, 2.5):
+        al = case.prescribed(syn.coords((16, 16, 16)), tt)[0]
+        assert float(al.min()) >= 0.0 and float(al.max()) <= 1.0
