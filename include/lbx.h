@@ -61,6 +61,14 @@ typedef enum {
  *                     G_Bx(2), G_By(2))                                         K = 18, 2D
  *                    the paper's own MHD: viscous, heat-conducting (T = p/rho), resistive,
  *                    Powell source -(tr G_B)(0, B, u.B, u)
+ *   HCNSF_3D         (rho, m_x, m_y, m_z, E, G_11, G_22, G_T(3), G_00, G_01, G_02, G_12)
+ *                                                                            K = 14, 3D
+ *                    3D homogenized compressible NSF (Sec. 3, HCNSF) in the paper's order:
+ *                    G ~ sym grad u, G_T ~ grad T (T = p/rho), porosity alpha and solid
+ *                    velocity u_s prescribed (lbx_prescribed); Phi_m = m u + p I - alpha tau_v,
+ *                    Phi_E = (E + p) u - alpha tau_v u - alpha kappa G_T,
+ *                    S_m = (1 - alpha)/eta (rho u_s - m), S_E = S_m . u.  The background Q0
+ *                    must have zero tracker components.
  * Trackers G_{V,b} ~ dV/dx_b follow Eq. gradient_advection with tau_grad = g_tau dt. */
 typedef enum {
     LBX_ADR_CASCADE = 1,
@@ -70,7 +78,8 @@ typedef enum {
     LBX_EULER = 5,
     LBX_MAXWELL_TM = 6,
     LBX_NSF_CONS_TRACK = 7,
-    LBX_MHD_POWELL_2D = 8
+    LBX_MHD_POWELL_2D = 8,
+    LBX_HCNSF_3D = 9
 } lbx_family;
 
 typedef enum { LBX_D2Q5 = 1, LBX_D2Q9 = 2, LBX_D3Q7 = 3, LBX_D3Q19 = 4 } lbx_lattice;
@@ -109,6 +118,9 @@ typedef enum { LBX_FP64 = 1, LBX_FP32_SHIFT = 2, LBX_FP16_SCALED = 3 } lbx_preci
  *                                                    Q = (rho, rho u, rho v, p/(gamma-1) +
  *                                                        rho|u|^2/2 + |B|^2/2, B, gradients
  *                                                        of the six conserved fields)
+ *                   HCNSF_3D (rho, u_x, u_y, u_z, p) Q = (rho, rho u, p/(gamma-1) + rho|u|^2/2,
+ *                                                        sym grad u, grad(p/rho)), the
+ *                                                        paper's order
  *                   BURGERS (u), MAXWELL_TM (E_z, H_x, H_y): Q = V
  *                   EULER (rho, u, v, p)             Q = (rho, rho u, rho v,
  *                                                        p/(gamma-1) + rho|u|^2/2)
@@ -118,6 +130,24 @@ typedef enum { LBX_FP64 = 1, LBX_FP32_SHIFT = 2, LBX_FP16_SCALED = 3 } lbx_preci
  *                 relaxation lag; mms_conserved_only = 1 forces the conserved components
  *                 alone.  The table is copied by lbx_scheme_derive. */
 typedef enum { LBX_MMS_NONE = 0, LBX_MMS_ADR_SEPARABLE = 1, LBX_MMS_FOURIER = 2 } lbx_mms;
+
+/* Prescribed coefficient fields of HCNSF_3D (Sec. 3, HCNSF; supplement, HCNSF MMS): the
+ * porosity alpha (1 fluid, 0 solid) and the solid velocity u_s, evaluated in the step kernel
+ * at every node x = (i, j, l) dx from closed forms, at the time level t^n = n dt of the state
+ * they multiply (t + dt/2 inside the manufactured forcing, whose flux divergence includes
+ * the fields' gradient):
+ *   NONE      alpha = 1, u_s = 0 (plain compressible NSF);
+ *   UNIFORM   alpha = pf[0], u_s = (pf[1], pf[2], pf[3]);
+ *   ADVECTED  a moving solid: with s_d = sin(2 pi x_d), c_d = cos(2 pi x_d), the rotation
+ *             pattern r = rot (s_0 c_1 c_2, -c_0 s_1 c_2, c_0 c_1 s_2), translation c and
+ *             oscillation osc,
+ *               u_s = (r_0 cos t + c_0 + osc sin t c_2, r_1 cos t + c_1 + osc cos t c_0,
+ *                      r_2 sin t + c_2 + osc sin t c_1),
+ *               alpha = a_mean + a_amp [z_0 + z_1 + z_2 + 2 z_0 z_1 z_2], z_d = sin(2 pi xi_d),
+ *               xi = x - r sin t - c t;
+ *             pf = (a_mean, a_amp, rot, osc, c_0, c_1, c_2).  The paper's values are
+ *             (0.5, 0.1, 0.2, 0.1, 0.1, -0.1, 0.05), for which alpha stays in [0, 1]. */
+typedef enum { LBX_PRESCRIBED_NONE = 0, LBX_PRESCRIBED_UNIFORM = 1, LBX_PRESCRIBED_ADVECTED = 2 } lbx_prescribed;
 
 #define LBX_MMS_MAX_MODES 64
 /* One term of a manufactured primitive field:
@@ -135,7 +165,8 @@ typedef struct {
      *   NSF          {gamma, R_gas, mu, kappa}
      *   MHD          {gamma, eta}
      *   BURGERS      {}            EULER {gamma}            MAXWELL_TM {c}
-     *   NSF_CONS_TRACK {gamma, R_gas, mu, kappa}   MHD_POWELL_2D {gamma, mu, kappa, eta} */
+     *   NSF_CONS_TRACK {gamma, R_gas, mu, kappa}   MHD_POWELL_2D {gamma, mu, kappa, eta}
+     *   HCNSF_3D     {gamma, mu, kappa, eta}  (eta > 0: drag time scale) */
     double params[8];
     /* Reference (background) state Q0 [K] for the shifted storage modes; F0 = Phi(Q0). */
     double Q0[24];
@@ -157,6 +188,8 @@ typedef struct {
     int mms_n_modes;       /* FOURIER: 1 .. LBX_MMS_MAX_MODES                           */
     double mms_mean[8];    /* FOURIER: mean of each primitive                           */
     int mms_conserved_only; /* FOURIER: nonzero leaves the tracker components unforced */
+    int prescribed;        /* lbx_prescribed (HCNSF_3D only; NONE for every other family) */
+    double prescribed_params[8]; /* pf of the prescribed fields                          */
 } lbx_scheme_desc;
 
 typedef struct lbx_system lbx_system;

@@ -29,4 +29,14 @@ template <typename T> __host__ __device__ inline Dual<T> operator/(const Dual<T>
   return Dual<T>(q, (a.d - q * b.d) * inv);
 }
 
+// sin(pi a) and cos(pi a) of a dual number (the derivative carries the factor pi).
+template <typename T>
+__device__ inline void sincospi_dual(const Dual<T>& a, Dual<T>* s, Dual<T>* c) {
+  T sv, cv;
+  sincospi(a.v, &sv, &cv);
+  const T pi = T(3.141592653589793238462643383279502884);
+  *s = Dual<T>(sv, pi * cv * a.d);
+  *c = Dual<T>(cv, -pi * sv * a.d);
+}
+
 }  // namespace lbx

@@ -59,11 +59,15 @@ struct KParams {
   int mms_n;
   int mms_trackers;            // nonzero: the tracker components are forced as well
   T mms_mean[8];               // mean of each primitive
+  int pf_kind;                 // prescribed coefficient fields (HCNSF): 0 none, 1 uniform, 2 advected
+  T pf[8];                     // their parameters (see prescribed_fields)
 };
 
+// Whether the step reads the step index: manufactured forcing or time-dependent prescribed
+// coefficient fields.
 template <typename T>
-__host__ __device__ __forceinline__ bool has_forcing(const KParams<T>& p) {
-  return p.mms_tab != nullptr || p.mms_modes != nullptr;
+__host__ __device__ __forceinline__ bool time_dependent(const KParams<T>& p) {
+  return p.mms_tab != nullptr || p.mms_modes != nullptr || p.pf_kind == 2;
 }
 
 // Element index of population (k, i) at `cell` (see the storage layout above).
@@ -147,6 +151,70 @@ __device__ __forceinline__ T adr_mms(const KParams<T>& p, int x, int y, long lon
   const T* tb = p.mms_tab;
   const T sxv = tb[x], cxv = tb[p.nx + x], syv = tb[2 * p.nx + y], cyv = tb[2 * p.nx + p.ny + y];
   return e * (p.mms_c0 * sxv * cyv + p.mms_cx * cxv * cyv - p.mms_cy * sxv * syv);
+}
+
+// Prescribed coefficient fields of the homogenized NSF family (Sec. 3, HCNSF; supplement,
+// HCNSF MMS) at coordinates x and time t: cf = (alpha, u_s,x, u_s,y, u_s,z).
+//   kind 0  pure fluid: alpha = 1, u_s = 0;
+//   kind 1  uniform: alpha = pf[0], u_s = (pf[1], pf[2], pf[3]);
+//   kind 2  advected solid: with s_d = sin(2 pi x_d), c_d = cos(2 pi x_d), rotation pattern
+//           r = rot (s0 c1 c2, -c0 s1 c2, c0 c1 s2), translation c = pf[4..6], oscillation osc:
+//             u_s = (r_0 cos t + c_0 + osc sin t c2, r_1 cos t + c_1 + osc cos t c0,
+//                    r_2 sin t + c_2 + osc sin t c1),
+//             alpha = a_mean + a_amp [z0 + z1 + z2 + 2 z0 z1 z2], z_d = sin(2 pi xi_d),
+//             xi = x - d, d = r sin t + c t  (the solid displacement);
+//           pf = (a_mean, a_amp, rot, osc, c_0, c_1, c_2).
+// Generic in the coordinate type: dual coordinates give the fields' spatial derivative
+// (the manufactured forcing differentiates the flux through alpha).
+template <typename T>
+__device__ __forceinline__ void sc_pi(T a, T* s, T* c) { sincospi(a, s, c); }
+template <typename T>
+__device__ __forceinline__ void sc_pi(Dual<T> a, Dual<T>* s, Dual<T>* c) { sincospi_dual(a, s, c); }
+
+template <typename T, typename U>
+__device__ __forceinline__ void prescribed_fields(const KParams<T>& p, const U (&x)[3], T t, U (&cf)[4]) {
+  if (p.pf_kind == 1) {
+    for (int a = 0; a < 4; ++a) cf[a] = U(p.pf[a]);
+    return;
+  }
+  if (p.pf_kind != 2) {
+    cf[0] = U(T(1));
+    cf[1] = cf[2] = cf[3] = U(T(0));
+    return;
+  }
+  U s[3], c[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) sc_pi(U(T(2)) * x[d], &s[d], &c[d]);
+  T st, ct;
+  sincos(t, &st, &ct);
+  const T rot = p.pf[2], osc = p.pf[3];
+  const U r[3] = {U(rot) * s[0] * c[1] * c[2], U(-rot) * c[0] * s[1] * c[2], U(rot) * c[0] * c[1] * s[2]};
+  cf[1] = r[0] * U(ct) + U(p.pf[4]) + U(osc * st) * c[2];
+  cf[2] = r[1] * U(ct) + U(p.pf[5]) + U(osc * ct) * c[0];
+  cf[3] = r[2] * U(st) + U(p.pf[6]) + U(osc * st) * c[1];
+  U z[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    U zc;
+    sc_pi(U(T(2)) * (x[d] - r[d] * U(st) - U(p.pf[4 + d] * t)), &z[d], &zc);
+  }
+  cf[0] = U(p.pf[0]) + U(p.pf[1]) * (z[0] + z[1] + z[2] + U(T(2)) * z[0] * z[1] * z[2]);
+}
+
+// Flux and source at a node at state time t (the family's eval()), with the prescribed
+// coefficient fields at the node for families that have them.
+template <template <typename> class SysT, typename T>
+__device__ __forceinline__ void eval_node(const KParams<T>& p, int x, int y, int z, T t, const T* dQ,
+                                          T (&Phi)[SysT<T>::K][SysT<T>::D], T (&Src)[SysT<T>::K]) {
+  using Sys = SysT<T>;
+  if constexpr (NcfOf<Sys>::value > 0) {
+    const T xc[3] = {T(x) * p.dx, T(y) * p.dx, T(z) * p.dx};
+    T cf[NcfOf<Sys>::value];
+    prescribed_fields(p, xc, t, cf);
+    Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf);
+  } else {
+    Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
+  }
 }
 
 // Manufactured forcing of a FOURIER table (Sec. 4): S_MMS = d_t Q_ex + div Phi(Q_ex) - S(Q_ex)
@@ -235,7 +303,16 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
     D1 dQd[K], Phi[K][D], S[K];
 #pragma unroll
     for (int k2 = 0; k2 < K; ++k2) dQd[k2] = Qd[k2] - q0[k2];
-    SysD::eval(pd, q0, dQd, Phi, S);
+    if constexpr (NcfOf<SysD>::value > 0) {
+      // the coefficient fields at x with d/dx_b seeded: div Phi includes their gradient
+      D1 xd[3], cfd[NcfOf<SysD>::value];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) xd[d] = D1(xc[d], d == b ? T(1) : T(0));
+      prescribed_fields(p, xd, t, cfd);
+      SysD::eval(pd, q0, dQd, Phi, S, cfd);
+    } else {
+      SysD::eval(pd, q0, dQd, Phi, S);
+    }
 #pragma unroll
     for (int k2 = 0; k2 < K; ++k2) acc[k2] += Phi[k2][b].d - (b == 0 ? S[k2].v : T(0));
   }
@@ -404,7 +481,7 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
     dQ[k] = St::SHIFT ? xk : xk - p.Q0[k];
   }
   T Phi[K][D], Src[K];
-  Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
+  eval_node<SysT>(p, x, y, z, T(step) * p.dt, dQ, Phi, Src);
   if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y, step);
   if constexpr (FOURIER) {
     if (p.mms_modes != nullptr) mms_fourier<Lat, SysT, T>(p, x, y, z, step, Src);
@@ -637,7 +714,7 @@ __device__ __forceinline__ void step_node_split(const typename St::S* __restrict
     dQ[k] = St::SHIFT ? xk : xk - p.Q0[k];
   }
   T Phi[K][D], Src[K];
-  Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
+  eval_node<SysT>(p, x, y, z, T(step) * p.dt, dQ, Phi, Src);
   if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y, step);
 
   // a4 + a5 + a6: the arithmetic of finish_node with the sign of c' . phi set by the lane
@@ -703,7 +780,7 @@ __global__ void __launch_bounds__(COLS, SplitMode<Lat, SysT, St, COLS>::min_bloc
   const int xr = blockIdx.x * (COLS / 2) + (int)(threadIdx.x >> 1);
   const bool active = xr < p.nx;
   const int x = active ? xr : p.nx - 1;
-  const long long step = has_forcing(p) ? *p.step_ptr + p.step_rel : 0;
+  const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
   step_node_split<Lat, SysT, St, COLS>(A, B, p, x, blockIdx.y, blockIdx.z, step, (int)(threadIdx.x & 1), active);
 }
 
@@ -859,7 +936,7 @@ __global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_block
     return;
   }
   const unsigned int cell = ((unsigned int)z * (unsigned int)ny + (unsigned int)y) * (unsigned int)nx + x;
-  const long long step = has_forcing(p) ? *p.step_ptr + p.step_rel : 0;
+  const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
   finish_node<Lat, SysT, St>(
       B, p, x, y, z, cell, step, true,
       [&](int kp, int i, T& a, T& b) { lds_pair(rowv + (size_t)(kp * Q + i) * M::ROWP + t + M::shift(i, EP), a, b); },
@@ -875,7 +952,7 @@ __global__ void __launch_bounds__(COLS, StepMode<Lat, SysT, St, COLS>::min_block
     k_step(const typename St::S* __restrict__ A, typename St::S* __restrict__ B, const KParams<typename St::C> p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
-  const long long step = has_forcing(p) ? *p.step_ptr + p.step_rel : 0;
+  const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
   step_node<Lat, SysT, St, MODE, COLS, FOURIER>(A, B, p, x, blockIdx.y, blockIdx.z, step);
 }
 
@@ -924,7 +1001,7 @@ __global__ void k_init(const double* __restrict__ Qf, typename St::S* __restrict
   double dQ[K];
   for (int k = 0; k < K; ++k) dQ[k] = Qf[(size_t)k * plane + cell] - p.Q0[k];
   double Phi[K][D], Src[K];
-  Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
+  eval_node<SysT>(p, x, y, z, 0.0, dQ, Phi, Src);      // the initial state is at t = 0
   // destination of population i: the pull at node x reads x - c_i, so the node y = x
   // stores f_i(y + c_i); here node x writes its own f_i to x - c_i.
   int dxs[3] = {x == p.nx - 1 ? 0 : x + 1, x, x == 0 ? p.nx - 1 : x - 1};

@@ -45,6 +45,7 @@ static int family_K(int f) {
     case LBX_MAXWELL_TM: return 3;
     case LBX_NSF_CONS_TRACK: return 12;
     case LBX_MHD_POWELL_2D: return 18;
+    case LBX_HCNSF_3D: return 14;
   }
   return 0;
 }
@@ -55,10 +56,11 @@ static int family_NC(int f) {
     case LBX_MHD_J_TRACK: return 8;
     case LBX_NSF_CONS_TRACK: return 4;
     case LBX_MHD_POWELL_2D: return 6;
+    case LBX_HCNSF_3D: return 5;
     default: return family_K(f);
   }
 }
-static int family_D(int f) { return f == LBX_MHD_J_TRACK ? 3 : 2; }
+static int family_D(int f) { return (f == LBX_MHD_J_TRACK || f == LBX_HCNSF_3D) ? 3 : 2; }
 // Primitive fields of a FOURIER manufactured solution (lbx_mms).
 static int family_nprim(int f) {
   switch (f) {
@@ -70,6 +72,7 @@ static int family_nprim(int f) {
     case LBX_MAXWELL_TM: return 3;
     case LBX_NSF_CONS_TRACK: return 4;
     case LBX_MHD_POWELL_2D: return 6;
+    case LBX_HCNSF_3D: return 5;
   }
   return 0;
 }
@@ -85,6 +88,8 @@ static const char* NAMES_NSF12[] = {"rho", "m_x", "m_y", "E", "G_rho_x", "G_rho_
 static const char* NAMES_MHD18[] = {"rho", "m_x", "m_y", "E", "B_x", "B_y", "G_rho_x", "G_rho_y", "G_mx_x",
                                     "G_mx_y", "G_my_x", "G_my_y", "G_E_x", "G_E_y", "G_Bx_x", "G_Bx_y",
                                     "G_By_x", "G_By_y"};
+static const char* NAMES_HCNSF[] = {"rho", "m_x", "m_y", "m_z", "E", "G_u11", "G_u22", "G_T_x", "G_T_y",
+                                    "G_T_z", "G_u00", "G_u01", "G_u02", "G_u12"};
 
 extern "C" lbx_status lbx_system_declare(const lbx_system_desc* desc, lbx_system** out) {
   if (!desc || !out) return fail(LBX_ERR_ARG, "lbx_system_declare: null argument");
@@ -99,10 +104,23 @@ extern "C" lbx_status lbx_system_declare(const lbx_system_desc* desc, lbx_system
   memcpy(s->params, desc->params, sizeof(s->params));
   memcpy(s->Q0, desc->Q0, sizeof(s->Q0));
   if ((s->family == LBX_NSF_PRIM_TRACK || s->family == LBX_EULER || s->family == LBX_MHD_J_TRACK ||
-       s->family == LBX_NSF_CONS_TRACK || s->family == LBX_MHD_POWELL_2D) &&
+       s->family == LBX_NSF_CONS_TRACK || s->family == LBX_MHD_POWELL_2D || s->family == LBX_HCNSF_3D) &&
       !(s->Q0[0] > 0.0)) {
     delete s;
     return fail(LBX_ERR_ARG, "lbx_system_declare: reference density Q0[0] must be > 0");
+  }
+  if (s->family == LBX_HCNSF_3D) {
+    // the step kernel's delta form multiplies no background quantity by alpha: Phi(Q0)
+    // must not depend on the prescribed fields, i.e. the background trackers are zero
+    for (int k = s->NC; k < s->K; ++k)
+      if (s->Q0[k] != 0.0) {
+        delete s;
+        return fail(LBX_ERR_ARG, "lbx_system_declare: HCNSF_3D needs Q0[%d] = 0 (tracker background)", k);
+      }
+    if (!(s->params[3] > 0.0)) {
+      delete s;
+      return fail(LBX_ERR_ARG, "lbx_system_declare: HCNSF_3D needs eta > 0");
+    }
   }
   *out = s;
   return LBX_OK;
@@ -127,6 +145,7 @@ extern "C" const char* lbx_component_name(const lbx_system* s, int k) {
     case LBX_MAXWELL_TM: return NAMES_MAX[k];
     case LBX_NSF_CONS_TRACK: return NAMES_NSF12[k];
     case LBX_MHD_POWELL_2D: return NAMES_MHD18[k];
+    case LBX_HCNSF_3D: return NAMES_HCNSF[k];
   }
   return nullptr;
 }
@@ -217,6 +236,15 @@ extern "C" lbx_status lbx_scheme_derive(const lbx_system* sys, const lbx_scheme_
           !std::isfinite(md.omega) || !std::isfinite(md.psi))
         return fail(LBX_ERR_ARG, "lbx_scheme_derive: mode %d is not finite", m);
     }
+  }
+  if (d->prescribed != LBX_PRESCRIBED_NONE) {
+    if (sys->family != LBX_HCNSF_3D)
+      return fail(LBX_ERR_ARG, "lbx_scheme_derive: prescribed fields belong to HCNSF_3D only");
+    if (d->prescribed != LBX_PRESCRIBED_UNIFORM && d->prescribed != LBX_PRESCRIBED_ADVECTED)
+      return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown prescribed fields %d", d->prescribed);
+    for (int i = 0; i < 8; ++i)
+      if (!std::isfinite(d->prescribed_params[i]))
+        return fail(LBX_ERR_ARG, "lbx_scheme_derive: prescribed_params[%d] is not finite", i);
   }
   const bool has_trackers = sys->K > sys->NC;
   if (has_trackers && !(d->g_tau > 0.0)) return fail(LBX_ERR_ARG, "lbx_scheme_derive: g_tau must be > 0");
@@ -398,6 +426,27 @@ static void background_flux(const lbx_scheme* s, double F0[KMAX][3]) {
       F0[2][0] = -c * Q[0];
       break;
     }
+    case LBX_HCNSF_3D: {
+      // zero background trackers: no dissipative flux, alpha drops out
+      const double g = P[0], rho = Q[0];
+      double u[3], ke = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        u[a] = Q[1 + a] / rho;
+        ke += 0.5 * Q[1 + a] * u[a];
+      }
+      const double p = (g - 1.0) * (Q[4] - ke), T = p / rho;
+      for (int b = 0; b < 3; ++b) {
+        F0[0][b] = Q[1 + b];
+        for (int a = 0; a < 3; ++a) F0[1 + a][b] = Q[1 + a] * u[b] + (a == b ? p : 0.0);
+        F0[4][b] = (Q[4] + p) * u[b];
+      }
+      for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b)
+          for (int c = 0; c < 3; ++c)
+            F0[SysHCNSF<double>::gidx(a, b)][c] = -0.5 * itg * ((a == c ? u[b] : 0.0) + (b == c ? u[a] : 0.0));
+      for (int b = 0; b < 3; ++b) F0[7 + b][b] = -T * itg;
+      break;
+    }
     case LBX_NSF_CONS_TRACK:
     case LBX_MHD_POWELL_2D: {
       const bool mhd = y.family == LBX_MHD_POWELL_2D;
@@ -494,6 +543,16 @@ static void pack_prm(const lbx_scheme* s, double prm[NPRM]) {
       prm[19] = P[0];
       break;
     }
+    case LBX_HCNSF_3D: {
+      const double g = P[0], rho = Q[0];
+      double ke = 0.0;
+      for (int a = 0; a < 3; ++a) ke += 0.5 * Q[1 + a] * Q[1 + a] / rho;
+      const double p0 = (g - 1.0) * (Q[4] - ke);
+      prm[0] = g - 1.0; prm[1] = P[1]; prm[2] = P[2]; prm[3] = 1.0 / P[3]; prm[4] = itg;
+      for (int a = 0; a < 3; ++a) prm[5 + a] = Q[1 + a] / rho;
+      prm[8] = Q[4] + p0; prm[9] = p0 / rho; prm[10] = g;
+      break;
+    }
   }
 }
 
@@ -536,6 +595,8 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
     p.mms_trackers = s.d.mms_conserved_only == 0;
     for (int q = 0; q < 8; ++q) p.mms_mean[q] = (T)s.d.mms_mean[q];
   }
+  p.pf_kind = s.d.prescribed;
+  for (int i = 0; i < 8; ++i) p.pf[i] = (T)s.d.prescribed_params[i];
 }
 
 // ------------------------------------------------------------------------ dispatch
@@ -747,6 +808,9 @@ bool lbx::find_ops(int family, int lattice, int precision, Ops* o) {
     case LBX_MHD_POWELL_2D:
       if (lattice == LBX_D2Q5) return pick_store<LatD2Q5, SysMHD18>(precision, o);
       if (lattice == LBX_D2Q9) return pick_store<LatD2Q9, SysMHD18>(precision, o);
+      return false;
+    case LBX_HCNSF_3D:
+      if (lattice == LBX_D3Q7) return pick_store<LatD3Q7, SysHCNSF>(precision, o);
       return false;
   }
   return false;
@@ -985,7 +1049,7 @@ static cudaError_t enqueue_steps(lbx_state* st, int64_t n, bool start_a) {
     if (e != cudaSuccess) return e;
     a = !a;
   }
-  if (st->sch.d.mms != LBX_MMS_NONE) return launch_advance(st->d_step, n, st->stream);
+  if (time_dependent(st->sch)) return launch_advance(st->d_step, n, st->stream);
   return cudaSuccess;
 }
 
@@ -1111,7 +1175,7 @@ extern "C" lbx_status lbx_step(lbx_state* st, int64_t n) {
     cudaError_t e = enqueue_steps(st, n, st->cur_a);
     if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_step: launch failed: %s", cudaGetErrorString(e));
   }
-  if (st->sch.d.mms == LBX_MMS_NONE) st->step_dirty = true;
+  if (!time_dependent(st->sch)) st->step_dirty = true;
   if (n & 1) st->cur_a = !st->cur_a;
   st->step += n;
   return LBX_OK;

@@ -29,6 +29,12 @@ struct lbx_scheme {
 
 namespace lbx {
 
+// Whether the step kernels read the step index (manufactured forcing, or prescribed
+// coefficient fields that move with time); the device counter then advances every step.
+inline bool time_dependent(const lbx_scheme& s) {
+  return s.d.mms != LBX_MMS_NONE || s.d.prescribed == LBX_PRESCRIBED_ADVECTED;
+}
+
 struct Ops {
   cudaError_t (*step)(const lbx_state*, const void* A, void* B, int rel, cudaStream_t);
   cudaError_t (*init)(const lbx_state*, const double* Q, void* A, unsigned long long* maxbits, int write);

@@ -537,4 +537,111 @@ struct SysMaxwell {
   __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) { return fabs(p[0]); }
 };
 
+// ------------------------------------------------------ homogenized NSF (3D, prescribed)
+// 3D homogenized compressible NSF (Sec. 3, HCNSF): porosity alpha(x, t) and solid velocity
+// u_s(x, t) are prescribed coefficient fields, passed per node as cf = (alpha, u_s).
+// Q = (rho, m(3), E, G_11, G_22, G_T(3), G_00, G_01, G_02, G_12) in the paper's order, G the
+// tracked symmetric velocity gradient and G_T the tracked grad T, T = p/rho (gas constant 1):
+// tau_v = mu (2 G - 2/3 tr(G) I), Phi_m = m u + p I - alpha tau_v,
+// Phi_E = (E + p) u - alpha tau_v u - alpha kappa G_T,
+// Phi_{G_ab, c} = G_ab u_c - (delta_ac u_b + delta_bc u_a)/(2 tau_grad),
+// Phi_{G_T,b, c} = G_T,b u_c - delta_bc T/tau_grad,
+// S_m = (1-alpha)/eta (rho u_s - m), S_E = S_m . u, S_G = -G/tau_grad.
+// The background's tracker components are zero (checked by the host), so alpha never
+// multiplies a background quantity and Phi(Q0) is the same at every node.
+// p: 0 gamma-1, 1 mu, 2 kappa, 3 1/eta, 4 1/tau_grad, 5-7 u0, 8 E0+p0, 9 T0, 10 gamma
+template <typename T>
+struct SysHCNSF {
+  static constexpr int K = 14, NC = 5, D = 3, FAMILY = 9, NPRIM = 5, NCF = 4;
+  // position in Q of the symmetric-gradient component (a, b)
+  __host__ __device__ static constexpr int gidx(int a, int b) {
+    return a > b ? gidx(b, a) : (a == b ? (a == 0 ? 10 : 4 + a) : (a == 0 ? 10 + b : 13));
+  }
+  // primitives: rho, u_x, u_y, u_z, p
+  template <typename U>
+  __host__ __device__ static void augment(const T* p, const U (&V)[NPRIM], const U (&G)[NPRIM][3], U (&Q)[K]) {
+    const U rho = V[0];
+    Q[0] = rho;
+    U ke = U(0);
+    for (int a = 0; a < 3; ++a) {
+      Q[1 + a] = rho * V[1 + a];
+      ke = ke + V[1 + a] * V[1 + a];
+    }
+    Q[4] = V[4] / p[0] + U(0.5) * rho * ke;
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b) Q[gidx(a, b)] = U(0.5) * (G[1 + a][b] + G[1 + b][a]);
+    const U Tm = V[4] / rho;
+    for (int b = 0; b < 3; ++b) Q[7 + b] = (G[4][b] - Tm * G[0][b]) / rho;
+  }
+  template <typename CF>
+  __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K],
+                                       const CF (&cf)[NCF]) {
+    const T gm1 = p[0], mu = p[1], kap = p[2], ieta = p[3], itg = p[4];
+    const T EP0 = p[8], T0 = p[9];
+    const T alpha = cf[0];
+    const T drho = dQ[0], rho = Q0[0] + drho, irho = T(1) / rho;
+    T dm[3], m0[3], du[3], u[3];
+    for (int a = 0; a < 3; ++a) {
+      dm[a] = dQ[1 + a];
+      m0[a] = Q0[1 + a];
+      du[a] = (dm[a] - p[5 + a] * drho) * irho;
+      u[a] = p[5 + a] + du[a];
+    }
+    const T dke = T(0.5) * (dm[0] * u[0] + dm[1] * u[1] + dm[2] * u[2] + m0[0] * du[0] + m0[1] * du[1] + m0[2] * du[2]);
+    const T dE = dQ[4], dp = gm1 * (dE - dke);
+    const T dT = (dp - T0 * drho) * irho;
+    T G[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) G[a][b] = dQ[gidx(a, b)];
+    const T tr3 = T(2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]);
+    T atv[3][3];                                    // alpha tau_v
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) atv[a][b] = alpha * mu * (T(2) * G[a][b] - (a == b ? tr3 : T(0)));
+    for (int b = 0; b < 3; ++b) dPhi[0][b] = dm[b];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        dPhi[1 + a][b] = dm[a] * u[b] + m0[a] * du[b] + (a == b ? dp : T(0)) - atv[a][b];
+    for (int b = 0; b < 3; ++b)
+      dPhi[4][b] = (dE + dp) * u[b] + EP0 * du[b] - (atv[b][0] * u[0] + atv[b][1] * u[1] + atv[b][2] * u[2]) -
+                   alpha * kap * dQ[7 + b];
+    const T hitg = T(0.5) * itg;
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b) {
+        const int k = gidx(a, b);
+        for (int c = 0; c < 3; ++c)
+          dPhi[k][c] = dQ[k] * u[c] - ((a == c ? du[b] : T(0)) + (b == c ? du[a] : T(0))) * hitg;
+      }
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) dPhi[7 + b][c] = dQ[7 + b] * u[c] - (b == c ? dT * itg : T(0));
+    const T drag = (T(1) - alpha) * ieta;
+    S[0] = T(0);
+    for (int a = 0; a < 3; ++a) S[1 + a] = drag * rho * (cf[1 + a] - u[a]);
+    S[4] = S[1] * u[0] + S[2] * u[1] + S[3] * u[2];
+    for (int k = 5; k < K; ++k) S[k] = -(Q0[k] + dQ[k]) * itg;
+  }
+  // |u| + sqrt(c^2 + (4/3 mu + (gamma-1) kappa) / (rho tau_g)), the NSF bound at alpha = 1
+  // (alpha <= 1 only scales the dissipative terms down).
+  __host__ __device__ static T max_speed(const T* p, const T* Q0, const T* dQ) {
+    const T rho = Q0[0] + dQ[0];
+    T u2 = T(0);
+    for (int a = 0; a < 3; ++a) {
+      const T ua = (Q0[1 + a] + dQ[1 + a]) / rho;
+      u2 += ua * ua;
+    }
+    const T pr = p[0] * ((Q0[4] + dQ[4]) - T(0.5) * rho * u2);
+    const T s2 = p[10] * pr / rho + (T(4.0 / 3.0) * p[1] + p[0] * p[2]) * p[4] / rho;
+    return sqrt(u2) + sqrt(s2);
+  }
+};
+
+// Number of prescribed coefficient values a family's eval() takes per node (0: none).
+template <class S, class = void>
+struct NcfOf {
+  static constexpr int value = 0;
+};
+template <class S>
+struct NcfOf<S, decltype(void(S::NCF))> {
+  static constexpr int value = S::NCF;
+};
+
 }  // namespace lbx

@@ -18,13 +18,14 @@ _lib = C.CDLL(LIB_PATH)
 
 # ------------------------------------------------------------------------- constants
 ADR_CASCADE, NSF_PRIM_TRACK, MHD_J_TRACK, BURGERS, EULER, MAXWELL_TM = 1, 2, 3, 4, 5, 6
-NSF_CONS_TRACK, MHD_POWELL_2D = 7, 8
+NSF_CONS_TRACK, MHD_POWELL_2D, HCNSF_3D = 7, 8, 9
 D2Q5, D2Q9, D3Q7, D3Q19 = 1, 2, 3, 4
 ACOUSTIC, DIFFUSIVE = 1, 2
 FP64, FP32_SHIFT, FP16_SCALED = 1, 2, 3
 MMS_NONE, MMS_ADR_SEPARABLE, MMS_FOURIER = 0, 1, 2
 MMS_MAX_MODES = 64
 STAGE_AUTO, STAGE_THREAD, STAGE_LANES2, STAGE_BULK = 0, 1, 2, 3
+PRESCRIBED_NONE, PRESCRIBED_UNIFORM, PRESCRIBED_ADVECTED = 0, 1, 2
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_SUBCHAR", 5: "ERR_NONFINITE",
           6: "ERR_TIMEOUT", 7: "ERR_STATE", 8: "ERR_IO", 9: "ERR_UNSUPPORTED"}
@@ -52,7 +53,8 @@ class SchemeDesc(C.Structure):
                 ("g_tau", C.c_double), ("precision", C.c_int), ("mms", C.c_int),
                 ("mms_amp", C.c_double), ("allow_subchar_violation", C.c_int),
                 ("mms_modes", C.POINTER(MmsMode)), ("mms_n_modes", C.c_int), ("mms_mean", C.c_double * 8),
-                ("mms_conserved_only", C.c_int)]
+                ("mms_conserved_only", C.c_int), ("prescribed", C.c_int),
+                ("prescribed_params", C.c_double * 8)]
 
 
 _P = C.c_void_p
@@ -179,9 +181,11 @@ class Scheme:
 
     def __init__(self, system: System, lattice, extent, scaling, f, tau_lb=0.0, tau_R=0.0,
                  g_tau=0.0, precision=FP64, mms=MMS_NONE, mms_amp=0.0,
-                 allow_subchar_violation=False, mms_modes=None, mms_mean=None, mms_conserved_only=False):
+                 allow_subchar_violation=False, mms_modes=None, mms_mean=None, mms_conserved_only=False,
+                 prescribed=PRESCRIBED_NONE, prescribed_params=()):
         """mms_modes: sequence of (p, (kx, ky[, kz]), amp, phase, sigma, omega, psi) for
-        MMS_FOURIER; mms_mean: the primitives' means."""
+        MMS_FOURIER; mms_mean: the primitives' means; prescribed, prescribed_params: the
+        HCNSF coefficient fields (lbx_prescribed)."""
         d = SchemeDesc()
         d.lattice = lattice
         ext = list(extent) + [1] * (3 - len(extent))
@@ -205,6 +209,9 @@ class Scheme:
         for i, v in enumerate(mms_mean or []):
             d.mms_mean[i] = float(v)
         d.mms_conserved_only = int(bool(mms_conserved_only))
+        d.prescribed = int(prescribed)
+        for i, v in enumerate(prescribed_params):
+            d.prescribed_params[i] = float(v)
         h = _P()
         check(_lib.lbx_scheme_derive(system._h, C.byref(d), C.byref(h)))
         self._h = h

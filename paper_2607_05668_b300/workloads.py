@@ -46,7 +46,7 @@ def mhd_scheme(case, precision=L.FP32_SHIFT, lattice=L.D3Q19):
 # ------------------------------------------------------------- forced (manufactured) runs
 _FAMILY = {"adr": L.ADR_CASCADE, "nsf": L.NSF_PRIM_TRACK, "mhd": L.MHD_J_TRACK,
            "burgers": L.BURGERS, "euler": L.EULER, "maxwell": L.MAXWELL_TM,
-           "nsf12": L.NSF_CONS_TRACK, "mhd18": L.MHD_POWELL_2D}
+           "nsf12": L.NSF_CONS_TRACK, "mhd18": L.MHD_POWELL_2D, "hcnsf": L.HCNSF_3D}
 
 
 def table_system(table, params, Q0):
@@ -55,12 +55,14 @@ def table_system(table, params, Q0):
 
 
 def forced_scheme(table, system, lattice, extent, scaling, f, precision=L.FP64, tau_lb=0.0,
-                  tau_R=0.0, g_tau=0.0, conserved_only=False):
+                  tau_R=0.0, g_tau=0.0, conserved_only=False, prescribed=L.PRESCRIBED_NONE,
+                  prescribed_params=()):
     """A scheme carrying the FOURIER forcing of `table` (.lbx_modes(), .mean): every
     component, or the conserved ones with conserved_only."""
     return L.Scheme(system, lattice, extent, scaling, f, tau_lb=tau_lb, tau_R=tau_R, g_tau=g_tau,
                     precision=precision, mms=L.MMS_FOURIER, mms_modes=table.lbx_modes(),
-                    mms_mean=list(table.mean), mms_conserved_only=conserved_only)
+                    mms_mean=list(table.mean), mms_conserved_only=conserved_only,
+                    prescribed=prescribed, prescribed_params=prescribed_params)
 
 
 # ------------------------------------------------------------- the paper's own cascades
@@ -87,3 +89,29 @@ def mhd18_scheme(case, precision=L.FP32_SHIFT, lattice=L.D2Q5):
     """The paper's MHD recipe: acoustic dt = f dx, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
     return L.Scheme(mhd18_system(case), lattice, (case.n, case.n), L.ACOUSTIC, case.f,
                     tau_R=case.tau_R, g_tau=case.g_tau, precision=precision)
+
+
+# ------------------------------------------------- 3D homogenized NSF (prescribed fields)
+def hcnsf_system(case):
+    """14-component 3D homogenized NSF (case: gamma, mu, kappa, eta, a background state with
+    zero trackers)."""
+    return L.System(L.HCNSF_3D, params=(case.gamma, case.mu, case.kappa, case.eta),
+                    Q0=case.reference_state())
+
+
+def hcnsf_prescribed(case):
+    """The case's advected-solid porosity and solid velocity (lbx_prescribed ADVECTED)."""
+    return L.PRESCRIBED_ADVECTED, (case.alpha_mean, case.alpha_amp, case.rot, case.osc) + tuple(case.c)
+
+
+def hcnsf_scheme(case, precision=L.FP32_SHIFT, forced=False, extent=None):
+    """The paper's HCNSF recipe on D3Q7: acoustic dt = f dx, tau_LB = 1/2 + tau_R dt, trackers
+    g_tau, prescribed fields of the moving solid; forced: the case's manufactured flow."""
+    kind, pf = hcnsf_prescribed(case)
+    ext = extent or (case.n, case.n, case.n)
+    if forced:
+        return forced_scheme(case.table(), hcnsf_system(case), L.D3Q7, ext, L.ACOUSTIC, case.f,
+                             precision=precision, tau_R=case.tau_R, g_tau=case.g_tau,
+                             prescribed=kind, prescribed_params=pf)
+    return L.Scheme(hcnsf_system(case), L.D3Q7, ext, L.ACOUSTIC, case.f, tau_R=case.tau_R,
+                    g_tau=case.g_tau, precision=precision, prescribed=kind, prescribed_params=pf)

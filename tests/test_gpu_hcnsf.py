@@ -1,0 +1,144 @@
+"""3D homogenized NSF (LBX_HCNSF_3D, D3Q7) on the GPU against the CPU oracle
+(HomogenizedNsf3D): the paper's moving-solid porosity and solid velocity evaluated in the
+step kernel, with and without the manufactured forcing of the paper's HCNSF flow."""
+import math
+
+import pytest
+import torch
+
+import oracle
+import synthetic as syn
+from oracle.mms import make_mms
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+lbx = pytest.importorskip("paper_2607_05668_b300.lbx")
+from paper_2607_05668_b300 import workloads as W  # noqa: E402
+
+F64 = torch.float64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def _oracle(case, shape, fields, forced):
+    osys = oracle.systems.HomogenizedNsf3D(case.gamma, case.mu, case.kappa, case.eta, case.g_tau * case.dt,
+                                           fields=fields)
+    xs = syn.coords(shape)
+    tab = case.table()
+    return osys, oracle.Scheme(osys, oracle.LATTICES["D3Q7"], shape, case.dx, case.dt,
+                               oracle.tau_vector(osys, case.dt, tau_R=case.tau_R, g_tau=case.g_tau),
+                               mms=make_mms(osys, tab.exact, xs, dt=case.dt) if forced else None)
+
+
+def _run(N, steps, precision=lbx.FP64, forced=True, staging=None):
+    case = syn.HcnsfPaperCase(n=N)
+    shape = (N, N, N)
+    Q = case.table().augmented(syn.coords(shape), 0.0)
+    st = lbx.State(W.hcnsf_scheme(case, precision, forced=forced), Q)
+    if staging is not None:
+        st.set_staging(staging)
+    st.step(steps)
+    _, och = _oracle(case, shape, case.prescribed, forced)
+    Qo = och.moments(och.run(och.init(Q), steps))
+    return case, st, Qo
+
+
+@pytest.mark.parametrize("forced", [True, False])
+@pytest.mark.parametrize("N", [20, 24])
+def test_hcnsf_fp64_matches_oracle(N, forced):
+    """20 nodes per row: per-thread staging (20 % 8 != 0); 24: bulk row copies.  The tracker
+    populations carry V / tau_grad (tau_grad = 3 dt) in their equilibrium, so their rounding
+    differences show amplified relative to the tracker fields, which start at zero."""
+    case, st, Qo = _run(N, 10, forced=forced)
+    Qg = st.moments()
+    err = H.rel_linf_per_field(Qg, Qo)
+    assert err[:5].max() <= 1e-12, err.tolist()
+    assert err[5:].max() <= 1e-10, err.tolist()
+
+
+@pytest.mark.parametrize("staging", [lbx.STAGE_THREAD, lbx.STAGE_LANES2, lbx.STAGE_BULK])
+def test_hcnsf_stagings_agree(staging):
+    case, st, Qo = _run(16, 6, staging=staging)
+    err = H.rel_linf_per_field(st.moments(), Qo)
+    assert err[:5].max() <= 1e-12 and err[5:].max() <= 1e-10, err.tolist()
+
+
+def test_hcnsf_ragged_box_unforced_matches_oracle():
+    """A 20 x 12 x 10 box (nodes x = (i, j, l) dx, dx = 1/20 on every axis) with smooth
+    periodic initial data: the prescribed fields move with t = n dt in the step kernel."""
+    case = syn.HcnsfPaperCase(n=20)
+    shape = (10, 12, 20)
+    Q = case.table().augmented(syn.coords(shape), 0.0)
+    st = lbx.State(W.hcnsf_scheme(case, lbx.FP64, extent=(20, 12, 10)), Q)
+    st.step(9)
+    _, och = _oracle(case, shape, case.prescribed, False)
+    Qo = och.moments(och.run(och.init(Q), 9))
+    err = H.rel_linf_per_field(st.moments(), Qo)
+    assert err[:5].max() <= 1e-12 and err[5:].max() <= 1e-10, err.tolist()
+
+
+@pytest.mark.parametrize("prec,bound", [(lbx.FP32_SHIFT, 1e-4), (lbx.FP16_SCALED, 3e-2)])
+def test_hcnsf_reduced_precision_against_fp64_oracle(prec, bound):
+    case, st, Qo = _run(24, 30, precision=prec)
+    e = H.fluct_rel_l2(st.moments(), Qo, case.reference_state())
+    assert e[:5].max() <= bound, e
+
+
+def test_hcnsf_uniform_drag_decays_geometrically():
+    """Sec. 3, HCNSF source with uniform alpha and u_s: at a uniform state one step adds
+    dt (1 - alpha)/eta (rho u_s - m) to the momentum and that times u to the energy."""
+    case = syn.HcnsfPaperCase(n=8)
+    al, us = 0.3, (0.2, -0.1, 0.05)
+    sys_ = W.hcnsf_system(case)
+    sch = lbx.Scheme(sys_, lbx.D3Q7, (8, 8, 8), lbx.ACOUSTIC, case.f, tau_R=case.tau_R, g_tau=case.g_tau,
+                     prescribed=lbx.PRESCRIBED_UNIFORM, prescribed_params=(al,) + us)
+    q = torch.tensor([1.1, 0.4, -0.2, 0.3, 3.0] + [0.0] * 9, dtype=F64)
+    Q = q.reshape(14, 1, 1, 1).expand(14, 8, 8, 8).contiguous()
+    st = lbx.State(sch, Q)
+    st.step(1)
+    Q1 = st.moments()
+    k = case.dt * (1 - al) / case.eta
+    for a in range(3):
+        want = (1 - k) * float(q[1 + a]) + k * 1.1 * us[a]
+        assert float((Q1[1 + a] - want).abs().max()) <= 1e-15
+    dE = k * sum((1.1 * us[a] - float(q[1 + a])) * float(q[1 + a]) / 1.1 for a in range(3))
+    assert float((Q1[4] - (3.0 + dE)).abs().max()) <= 4e-15
+    assert float(Q1[5:].abs().max()) <= 1e-15
+
+
+def test_hcnsf_rejects_a_tracker_background_and_foreign_prescribed_fields():
+    case = syn.HcnsfPaperCase(n=8)
+    Q0 = case.reference_state()
+    Q0[7] = 0.1
+    with pytest.raises(lbx.LbxError):
+        lbx.System(lbx.HCNSF_3D, params=(case.gamma, case.mu, case.kappa, case.eta), Q0=Q0)
+    nsys = lbx.System(lbx.EULER, params=(1.4,), Q0=[1.0, 0.1, 0.1, 2.5])
+    with pytest.raises(lbx.LbxError):
+        lbx.Scheme(nsys, lbx.D2Q5, (8, 8), lbx.ACOUSTIC, 0.05, tau_R=1.0, prescribed=lbx.PRESCRIBED_UNIFORM,
+                   prescribed_params=(0.5, 0, 0, 0))
+
+
+@pytest.mark.parametrize("prec", [lbx.FP64, lbx.FP32_SHIFT])
+def test_hcnsf_paper_flow_is_second_order(prec):
+    """The paper's HCNSF flow and recipe (double tau_R = 10, float tau_R = 20) to t = 1 at
+    N = 32, 64, 128: pairwise orders of the relative L2 errors of rho, rho u and E (the
+    paper's Table 3 EOCs over N = 32 .. 256: 1.78 - 1.97)."""
+    errs = []
+    for N in (32, 64, 128):
+        case = syn.HcnsfPaperCase(n=N, tau_R=10.0 if prec == lbx.FP64 else 20.0)
+        xs = syn.coords((N, N, N))
+        tab = case.table()
+        st = lbx.State(W.hcnsf_scheme(case, prec, forced=True), tab.augmented(xs, 0.0))
+        n = int(round(1.0 / case.dt))
+        st.step(n)
+        Qex = tab.exact(*xs, torch.full_like(xs[0], n * case.dt))
+        Qg = st.moments()
+        errs.append([float(torch.sqrt(((Qg[k] - Qex[k]) ** 2).sum() / (Qex[k] ** 2).sum())) for k in range(5)])
+    orders = [[math.log2(errs[i][k] / errs[i + 1][k]) for k in range(5)] for i in range(2)]
+    print("errors", errs, "orders", orders)
+    assert all(1.6 < o < 2.5 for row in orders for o in row), orders
