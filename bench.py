@@ -7,7 +7,7 @@ around rho = 1, T = 1, Mach 0.3.  A step is one collide-and-stream pass over the
 grid (one kernel launch).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload nsf|mhd|adr|nsf12|mhd18] [--precision fp32|fp64|fp16]
+                  [--workload nsf|mhd|adr|nsf12|mhd18|hcnsf] [--precision fp32|fp64|fp16]
 
 --impl reference times the CPU FP64 oracle on bounded samples of the same workload.
 Under torchrun (N > 1) every rank advances its own replica (weak scaling, no exchange)
@@ -160,6 +160,8 @@ def make_case(workload, n=None):
         return syn.NsfPaperCase(n=n or 1024)
     if workload == "mhd18":
         return syn.MhdPaper2DCase(n=n or 512)
+    if workload == "hcnsf":
+        return syn.HcnsfPaperCase(n=n or 256)
     raise ValueError(workload)
 
 
@@ -168,6 +170,8 @@ def fields(workload, case):
         return case.table("nsf12").augmented(syn.coords((case.n, case.n)), 0.0)
     if workload == "mhd18":
         return case.table().augmented(syn.coords((case.n, case.n)), 0.0)
+    if workload == "hcnsf":
+        return case.table().augmented(syn.coords((case.n, case.n, case.n)), 0.0)
     return {"nsf": syn.nsf_fields, "mhd": syn.mhd_fields, "adr": syn.adr_fields}[workload](case)
 
 
@@ -181,19 +185,24 @@ def scheme(W, L, workload, case, prec):
         return W.nsf12_scheme(case, p)
     if workload == "mhd18":
         return W.mhd18_scheme(case, p)
+    if workload == "hcnsf":
+        return W.hcnsf_scheme(case, p)
     return W.adr_scheme(case, p)
 
 
 def kq(workload):
-    return {"nsf": (10, 9), "mhd": (11, 19), "adr": (3, 5), "nsf12": (12, 5), "mhd18": (18, 5)}[workload]
+    return {"nsf": (10, 9), "mhd": (11, 19), "adr": (3, 5), "nsf12": (12, 5), "mhd18": (18, 5),
+            "hcnsf": (14, 7)}[workload]
 
 
-LATTICE_NAME = {"nsf": "d2q9", "mhd": "d3q19", "adr": "d2q5", "nsf12": "d2q5", "mhd18": "d2q5"}
+LATTICE_NAME = {"nsf": "d2q9", "mhd": "d3q19", "adr": "d2q5", "nsf12": "d2q5", "mhd18": "d2q5",
+                "hcnsf": "d3q7"}
+DIM3 = ("mhd", "hcnsf")
 
 
 def config_of(workload, case, precision, K, q, ws=1):
     """The workload description both arms report."""
-    dim = 3 if workload == "mhd" else 2
+    dim = 3 if workload in DIM3 else 2
     grid = "x".join([str(case.n)] * dim)
     bytes_launch = 2 * K * q * STORE_BYTES[precision] * case.n ** dim
     return {"workload": f"{workload}_{LATTICE_NAME[workload]}_{grid}_{precision}", "grid": [case.n] * dim,
@@ -204,7 +213,7 @@ def config_of(workload, case, precision, K, q, ws=1):
 
 
 def cells(workload, case):
-    return case.n ** (3 if workload == "mhd" else 2)
+    return case.n ** (3 if workload in DIM3 else 2)
 
 
 
@@ -321,12 +330,14 @@ def run_variants(L, W, args, stream, peak, probe_fp64=None):
                                ("mhd", "fp32", 256, 50), ("mhd", "fp16", 256, 50),
                                ("nsf12", "fp32", 1024, 500), ("nsf12", "fp16", 1024, 500),
                                ("nsf12", "fp64", 1024, 100), ("mhd18", "fp32", 512, 500),
-                               ("mhd18", "fp64", 512, 100), ("adr", "fp64", 64, 500)):
+                               ("mhd18", "fp64", 512, 100), ("hcnsf", "fp32", 256, 100),
+                               ("hcnsf", "fp16", 256, 100), ("hcnsf", "fp64", 256, 20),
+                               ("adr", "fp64", 64, 500)):
         # the 64^2 case is launch-latency bound: its 500 steps replay as one CUDA graph
         r, st = measure_grid(L, W, wl, prec, n, steps, 5 if wl != "adr" else 500, stream, graph=(wl == "adr"))
         st.close()
         r["frac_of_hbm_peak"] = r["gbs"] / peak
-        ncell = n ** (3 if wl == "mhd" else 2)
+        ncell = n ** (3 if wl in DIM3 else 2)
         r["traffic_per_launch"] = profile_traffic(f"{wl}_{prec}", ncell)
         r["traffic_kernel"] = profile_kernel(f"{wl}_{prec}")
         if prec == "fp64":
@@ -461,6 +472,10 @@ def _oracle_scheme(workload, case, shape):
     elif workload == "mhd18":
         sysm = S.MhdPowell2D(case.gamma, case.mu, case.kappa, case.eta, case.g_tau * case.dt)
         lat = "D2Q5"
+    elif workload == "hcnsf":
+        sysm = S.HomogenizedNsf3D(case.gamma, case.mu, case.kappa, case.eta, case.g_tau * case.dt,
+                                  fields=case.prescribed)
+        lat = "D3Q7"
     else:
         sysm = S.AdrCascade(case.a_phys, case.nu, case.g_tau * case.dt)
         lat = "D2Q5"
@@ -472,7 +487,7 @@ def _oracle_scheme(workload, case, shape):
 def _oracle_sample(workload, case, rows):
     """The oracle on a periodic slab of `rows` rows of the full grid (same per-node work)."""
     Q = fields(workload, case)
-    Qs = Q[..., :rows, :].contiguous() if workload != "mhd" else Q[:, :rows].contiguous()
+    Qs = Q[..., :rows, :].contiguous() if workload not in DIM3 else Q[:, :rows].contiguous()
     shape = tuple(Qs.shape[1:])
     sch = _oracle_scheme(workload, case, shape)
     return sch, sch.init(Qs), int(Qs[0].numel())
@@ -480,7 +495,7 @@ def _oracle_sample(workload, case, rows):
 
 def cpu_baseline(args, case, budget_s=15.0):
     cores = torch.get_num_threads()
-    rows = 64 if args.workload != "mhd" else 8
+    rows = 64 if args.workload not in DIM3 else 8
     sch, f, n = _oracle_sample(args.workload, case, rows)
     f = sch.step(f, 0.0)                      # warm up
     t0 = time.perf_counter()
@@ -502,13 +517,13 @@ def run_reference(args):
     K, q = kq(args.workload)
     # each step is one oracle step on a slab sized so the whole run stays within minutes
     budget = 150.0
-    sch, f, n = _oracle_sample(args.workload, case, 8 if args.workload != "mhd" else 2)
+    sch, f, n = _oracle_sample(args.workload, case, 8 if args.workload not in DIM3 else 2)
     t0 = time.perf_counter()
     f = sch.step(f, 0.0)
     per_step = time.perf_counter() - t0
     total = args.steps + args.warmup
     rows = max(2, min(case.n, int(8 * budget / max(per_step * total, 1e-9))))
-    if args.workload == "mhd":
+    if args.workload in DIM3:
         rows = max(2, min(case.n, rows // 4))
     sch, f, n = _oracle_sample(args.workload, case, rows)
     for _ in range(args.warmup):
@@ -537,7 +552,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nsf", choices=["nsf", "mhd", "adr", "nsf12", "mhd18"])
+    ap.add_argument("--workload", default="nsf", choices=["nsf", "mhd", "adr", "nsf12", "mhd18", "hcnsf"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
     ap.add_argument("--n", type=int, default=None, help="grid size override")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

@@ -145,9 +145,26 @@ typedef enum { LBX_MMS_NONE = 0, LBX_MMS_ADR_SEPARABLE = 1, LBX_MMS_FOURIER = 2 
  *                      r_2 sin t + c_2 + osc sin t c_1),
  *               alpha = a_mean + a_amp [z_0 + z_1 + z_2 + 2 z_0 z_1 z_2], z_d = sin(2 pi xi_d),
  *               xi = x - r sin t - c t;
- *             pf = (a_mean, a_amp, rot, osc, c_0, c_1, c_2).  The paper's values are
- *             (0.5, 0.1, 0.2, 0.1, 0.1, -0.1, 0.05), for which alpha stays in [0, 1]. */
+ *             pf = (a_mean, a_amp, rot, osc, c_0, c_1, c_2, theta).  The paper's values are
+ *             (0.5, 0.1, 0.2, 0.1, 0.1, -0.1, 0.05), for which alpha stays in [0, 1].  theta
+ *             shifts the fields' time level inside the drag source to t^n + theta dt (the
+ *             flux keeps t^n; theta = 1/2 puts the source at the step's midpoint). */
 typedef enum { LBX_PRESCRIBED_NONE = 0, LBX_PRESCRIBED_UNIFORM = 1, LBX_PRESCRIBED_ADVECTED = 2 } lbx_prescribed;
+
+/* Population storage of a state:
+ *   TWO_BUFFERS  two buffers A, B; each step pulls from one and writes the other;
+ *   IN_PLACE     one buffer (half the memory).  Steps alternate between two kinds whose reads
+ *                and writes of a node cover the same addresses (kind 1 pulls from the
+ *                neighbours and stores each post-collision population into the slot of the
+ *                opposite velocity it just emptied; kind 2 reads the node's own swapped
+ *                slots and stores in the standard slots).  After an even number of steps the
+ *                populations are bitwise those of TWO_BUFFERS.  After an odd number the
+ *                layout is the pair's intermediate one: every call that reads or writes the
+ *                populations (moments, populations, norms, sums, finite and sub-characteristic
+ *                checks, save, load) fails with LBX_ERR_STATE until one more step is taken.
+ *                Per-thread staging with 128-thread blocks for staged systems; no bulk
+ *                copies, tuning, batches or adjoint. */
+typedef enum { LBX_STREAM_TWO_BUFFERS = 0, LBX_STREAM_IN_PLACE = 1 } lbx_streaming;
 
 #define LBX_MMS_MAX_MODES 64
 /* One term of a manufactured primitive field:
@@ -190,6 +207,7 @@ typedef struct {
     int mms_conserved_only; /* FOURIER: nonzero leaves the tracker components unforced */
     int prescribed;        /* lbx_prescribed (HCNSF_3D only; NONE for every other family) */
     double prescribed_params[8]; /* pf of the prescribed fields                          */
+    int streaming;         /* lbx_streaming                                             */
 } lbx_scheme_desc;
 
 typedef struct lbx_system lbx_system;
@@ -229,7 +247,9 @@ lbx_status lbx_lattice_velocities(int lattice, int* q, int* c, double* w);
  * Q: float64 [K][cells], on the host (q_on_device = 0) or device (1).
  * stream: a cudaStream_t (NULL = the legacy default stream).
  * f_buf_a, f_buf_b: NULL to let the library allocate the two population buffers, or
- * two device buffers of lbx_state_buffer_bytes() bytes each, owned by the caller.
+ * two device buffers of lbx_state_buffer_bytes() bytes each, owned by the caller.  An
+ * IN_PLACE scheme uses f_buf_a alone (f_buf_b must be NULL): NULL lets the library
+ * allocate its one buffer.
  * Runs the sub-characteristic check and fails with LBX_ERR_SUBCHAR on a violation
  * unless the scheme allows it.  On failure *out is NULL and nothing is leaked. */
 lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_device, void* stream,

@@ -15,7 +15,8 @@ Steps, in the paper's order and notation:
 
 Prescribed coefficient fields c(x, t) (HCNSF porosity and solid velocity) are evaluated
 at the node coordinates x = (i, j, l) dx and at the time level of the state they multiply:
-t^n in the equilibrium flux and the state source of step n, t = 0 at initialisation.
+t^n in the equilibrium flux and the state source of step n, t = 0 at initialisation;
+`source_theta` moves the source's fields to t^n + theta dt.
 
 Arrays: populations f are [K, q, *grid], fields Q are [K, *grid], grid = (nz,) ny, nx.
 The streaming here pushes post-collision values to x + c_i with torch.roll, exactly as
@@ -62,7 +63,7 @@ def tau_vector(system, dt, tau_cons=None, tau_R=None, g_tau=None):
 
 class Scheme:
     def __init__(self, system, lattice: Lattice, shape, dx, dt, tau, mms=None,
-                 shifted=False, Q0=None):
+                 shifted=False, Q0=None, source_theta=0.0):
         self.sys = system
         self.lat = lattice
         self.shape = tuple(shape)
@@ -74,6 +75,7 @@ class Scheme:
         self.cs2 = float(lattice.cs2)
         self.mms = mms
         self.shifted = shifted
+        self.source_theta = float(source_theta)
         self.Q0 = None if Q0 is None else torch.as_tensor(Q0, dtype=F64)
         # node coordinates (x, y[, z]), x fastest, for prescribed coefficient fields
         axes = [torch.arange(n, dtype=F64) * self.dx for n in self.shape]
@@ -106,7 +108,7 @@ class Scheme:
         return f - self.feq0 if self.shifted else f
 
     def source_total(self, Q, t):
-        S = source_at(self.sys, Q, self.xx, t)
+        S = source_at(self.sys, Q, self.xx, t + self.source_theta * self.dt)
         if self.mms is not None:
             Sm = self.mms(t + 0.5 * self.dt)          # all K components, or the conserved ones
             S = S + Sm if Sm.shape[0] == self.sys.K else torch.cat([S[: self.sys.n_cons] + Sm, S[self.sys.n_cons:]])

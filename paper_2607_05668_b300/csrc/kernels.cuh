@@ -29,6 +29,9 @@
 
 namespace lbx {
 
+// Largest mode table (LBX_MMS_MAX_MODES; the host checks that the two agree).
+constexpr int MMS_MAX_MODES = 64;
+
 // One manufactured mode on the device (lbx_mms_mode with 2 pi k precomputed).
 struct MmsMode {
   double k2pi[3];
@@ -61,6 +64,7 @@ struct KParams {
   T mms_mean[8];               // mean of each primitive
   int pf_kind;                 // prescribed coefficient fields (HCNSF): 0 none, 1 uniform, 2 advected
   T pf[8];                     // their parameters (see prescribed_fields)
+  T pf_src_dt;                 // time offset of the fields inside the source (0 or a fraction of dt)
 };
 
 // Whether the step reads the step index: manufactured forcing or time-dependent prescribed
@@ -211,10 +215,36 @@ __device__ __forceinline__ void eval_node(const KParams<T>& p, int x, int y, int
     const T xc[3] = {T(x) * p.dx, T(y) * p.dx, T(z) * p.dx};
     T cf[NcfOf<Sys>::value];
     prescribed_fields(p, xc, t, cf);
-    Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf);
+    if (p.pf_src_dt != T(0) && p.pf_kind == 2) {
+      T cs[NcfOf<Sys>::value];
+      prescribed_fields(p, xc, t + p.pf_src_dt, cs);
+      Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cs);
+    } else {
+      Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cf);
+    }
   } else {
     Sys::eval(p.prm, p.Q0, dQ, Phi, Src);
   }
+}
+
+// Time factor of a mode at t: g = exp(sigma t) cos(omega t + psi) and its derivative.
+template <typename T>
+__device__ __forceinline__ void mms_time_factor(const MmsMode& md, T t, T& g, T& gt) {
+  T st, ct;
+  sincos(T(md.omega) * t + T(md.psi), &st, &ct);
+  const T e = exp(T(md.sigma) * t);
+  g = e * ct;
+  gt = T(md.sigma) * g - T(md.omega) * e * st;
+}
+
+// The time factors of every mode at t + dt/2 of `step`, computed once per block into shared
+// memory (all threads of a block take the same step); ends with a block barrier.
+template <typename T>
+__device__ __forceinline__ void mms_time_table(const KParams<T>& p, long long step, T* tf) {
+  const T t = (T(step) + T(0.5)) * p.dt;
+  if (p.mms_modes != nullptr)
+    for (int m = (int)threadIdx.x; m < p.mms_n; m += (int)blockDim.x) mms_time_factor(p.mms_modes[m], t, tf[2 * m], tf[2 * m + 1]);
+  __syncthreads();
 }
 
 // Manufactured forcing of a FOURIER table (Sec. 4): S_MMS = d_t Q_ex + div Phi(Q_ex) - S(Q_ex)
@@ -228,7 +258,7 @@ __device__ __forceinline__ void eval_node(const KParams<T>& p, int x, int y, int
 // runs only in forced verification runs and must not cost the step kernels registers.
 template <class Lat, template <typename> class SysT, typename T>
 __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int z, long long step,
-                                         T* __restrict__ Src) {
+                                         T* __restrict__ Src, const T* __restrict__ tfac) {
   using D1 = Dual<T>;
   using SysD = SysT<D1>;
   constexpr int K = SysD::K, NC = SysD::NC, NP = SysD::NPRIM, D = Lat::D;
@@ -253,11 +283,14 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
     T th = T(md.phase);
 #pragma unroll
     for (int d = 0; d < D; ++d) th += k[d] * xc[d];
-    T sn, cs, st, ct;
+    T sn, cs, g, gt;
     sincos(th, &sn, &cs);
-    sincos(T(md.omega) * t + T(md.psi), &st, &ct);
-    const T e = exp(T(md.sigma) * t);
-    const T g = e * ct, gt = T(md.sigma) * g - T(md.omega) * e * st;
+    if (tfac != nullptr) {
+      g = tfac[2 * m];
+      gt = tfac[2 * m + 1];
+    } else {
+      mms_time_factor(md, t, g, gt);
+    }
     const T a = T(md.amp);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -309,7 +342,7 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
 #pragma unroll
       for (int d = 0; d < 3; ++d) xd[d] = D1(xc[d], d == b ? T(1) : T(0));
       prescribed_fields(p, xd, t, cfd);
-      SysD::eval(pd, q0, dQd, Phi, S, cfd);
+      SysD::eval(pd, q0, dQd, Phi, S, cfd, cfd);
     } else {
       SysD::eval(pd, q0, dQd, Phi, S);
     }
@@ -444,10 +477,16 @@ __device__ __forceinline__ double to_c(double v) { return v; }
 // divided by s_k): X, phi and dt S are divided by s_k once per component.
 // Moments, flux and source, equilibrium, BGK and store for one node whose populations
 // are available through get_pair(kp, i, a, b) / get_odd(i) (registers or a staged column).
-template <class Lat, template <typename> class SysT, class St, bool FOURIER = false, class GetPair, class GetOdd>
+// Destination of the post-collision populations: DstSelf stores population (k, i) of the
+// node at (k, i, cell); another functor maps (k, i) to an element index (in-place steps).
+struct DstSelf {};
+
+template <class Lat, template <typename> class SysT, class St, bool FOURIER = false, class GetPair, class GetOdd,
+          class Dst = DstSelf>
 __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, const KParams<typename St::C>& p,
                                             int x, int y, int z, unsigned int cell, long long step, bool active,
-                                            GetPair get_pair, GetOdd get_odd) {
+                                            GetPair get_pair, GetOdd get_odd,
+                                            const typename St::C* tfac = nullptr, Dst dst = Dst()) {
   using T = typename St::C;
   using V = typename PairOf<typename St::S>::V;
   using Sys = SysT<T>;
@@ -484,10 +523,16 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
   eval_node<SysT>(p, x, y, z, T(step) * p.dt, dQ, Phi, Src);
   if (Sys::FAMILY == 1 && p.mms_tab != nullptr) Src[0] += adr_mms(p, x, y, step);
   if constexpr (FOURIER) {
-    if (p.mms_modes != nullptr) mms_fourier<Lat, SysT, T>(p, x, y, z, step, Src);
+    if (p.mms_modes != nullptr) mms_fourier<Lat, SysT, T>(p, x, y, z, step, Src, tfac);
   }
 
   // a4 + a5 + a6: equilibrium (Eq. feq), BGK with source (Eq. lbe_update), store
+  auto out_idx = [&](int k, int i) -> unsigned int {
+    if constexpr (std::is_same<Dst, DstSelf>::value)
+      return eidx<K, Q>(k, i, cell, plane);
+    else
+      return dst(k, i);
+  };
   auto out_of = [&](int k, int i, T f) -> T {
     const T inv_s = St::SCALE ? p.inv_scale[k] : T(1);
     const int sg = Lat::c(i, 0) != 0 ? Lat::c(i, 0) : (Lat::c(i, 1) != 0 ? Lat::c(i, 1) : Lat::c(i, 2));
@@ -511,13 +556,13 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
       T a, b;
       get_pair(kp, i, a, b);
       const T oa = out_of(2 * kp, i, a), ob = out_of(2 * kp + 1, i, b);
-      if (active) st_pair(reinterpret_cast<V*>(B + eidx<K, Q>(2 * kp, i, cell, plane)), oa, ob);
+      if (active) st_pair(reinterpret_cast<V*>(B + out_idx(2 * kp, i)), oa, ob);
     }
   if constexpr (ODD) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const T o = out_of(K - 1, i, get_odd(i));
-      if (active) st_out(B + eidx<K, Q>(K - 1, i, cell, plane), o);
+      if (active) st_out(B + out_idx(K - 1, i), o);
     }
   }
 }
@@ -545,7 +590,7 @@ __device__ __forceinline__ void stage_node(const typename St::S* __restrict__ A,
 template <class Lat, template <typename> class SysT, class St, int MODE, int COLS = 128, bool FOURIER = false>
 __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
                                           const KParams<typename St::C>& p, int x, int y, int z,
-                                          long long step) {
+                                          long long step, const typename St::C* tfac = nullptr) {
   using T = typename St::C;
   using S = typename St::S;
   using V = typename PairOf<S>::V;
@@ -573,7 +618,7 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
           a = fv[2 * kp][i];
           b = fv[2 * kp + 1][i];
         },
-        [&](int i) -> T { return fv[ODD ? K - 1 : 0][i]; });
+        [&](int i) -> T { return fv[ODD ? K - 1 : 0][i]; }, tfac);
   } else {
     // a1: stage every population of the node in this thread's shared-memory column
     extern __shared__ __align__(16) unsigned char lbx_smem[];
@@ -583,7 +628,7 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
     stage_wait();
     finish_node<Lat, SysT, St, FOURIER>(
         B, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); },
-        [&](int i) -> T { return lds_c(colo + i * COLS); });
+        [&](int i) -> T { return lds_c(colo + i * COLS); }, tfac);
   }
 }
 
@@ -951,9 +996,117 @@ template <class Lat, template <typename> class SysT, class St, int MODE, int COL
 __global__ void __launch_bounds__(COLS, StepMode<Lat, SysT, St, COLS>::min_blocks)
     k_step(const typename St::S* __restrict__ A, typename St::S* __restrict__ B, const KParams<typename St::C> p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= p.nx) return;
   const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
-  step_node<Lat, SysT, St, MODE, COLS, FOURIER>(A, B, p, x, blockIdx.y, blockIdx.z, step);
+  if constexpr (FOURIER) {
+    // the modes' time factors, shared by the block (before any thread leaves)
+    __shared__ typename St::C tf[2 * MMS_MAX_MODES];
+    mms_time_table(p, step, tf);
+    if (x >= p.nx) return;
+    step_node<Lat, SysT, St, MODE, COLS, FOURIER>(A, B, p, x, blockIdx.y, blockIdx.z, step,
+                                                  p.mms_modes != nullptr ? tf : nullptr);
+  } else {
+    if (x >= p.nx) return;
+    step_node<Lat, SysT, St, MODE, COLS, FOURIER>(A, B, p, x, blockIdx.y, blockIdx.z, step);
+  }
+}
+
+// ------------------------------------------------------------ in-place (one buffer)
+// Single-buffer streaming: steps alternate between two kinds so that every node reads and
+// then writes one set of addresses that no other node touches, which makes the update safe
+// in place.  With i' the velocity opposite to i:
+//   kind 1 (from the standard layout, F[k][i][x] = post-collision f*_i of node x): node x
+//          pulls f_i(x) = F[k][i][x - c_i] and stores its post-collision f*_i into the slot it
+//          emptied for the opposite direction, F[k][i'][x + c_i] (x + c_i = x - c_{i'});
+//   kind 2 node x reads f_i(x) = F[k][i'][x] (its own node, swapped slots) and stores f*_i
+//          in F[k][i][x], which is the standard layout again.
+// A kind-1 step followed by a kind-2 step moves every population exactly as two pull steps
+// between two buffers, with the same arithmetic (finish_node), so the populations after an
+// even number of steps are bitwise those of the two-buffer kernels, in half the memory.
+template <class Lat>
+__host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+}
+template <class Lat>
+__host__ __device__ constexpr bool opp_valid() {
+  for (int i = 0; i < Lat::Q; ++i)
+    for (int d = 0; d < 3; ++d)
+      if (Lat::c(opp<Lat>(i), d) != -Lat::c(i, d)) return false;
+  return true;
+}
+
+// plain (coherent) loads: the in-place kernels write the buffer they read
+__device__ __forceinline__ double2 ld_pair_rw(const double2* p) { return *p; }
+__device__ __forceinline__ float2 ld_pair_rw(const float2* p) { return *p; }
+__device__ __forceinline__ __half2 ld_pair_rw(const __half2* p) { return *p; }
+
+template <class Lat, template <typename> class SysT, class St, int MODE, int COLS, bool FOURIER, int KIND>
+__device__ __forceinline__ void step_node_inplace(typename St::S* F, const KParams<typename St::C>& p, int x,
+                                                  int y, int z, long long step, const typename St::C* tfac) {
+  using T = typename St::C;
+  using S = typename St::S;
+  using V = typename PairOf<S>::V;
+  constexpr int K = SysT<T>::K, Q = Lat::Q, KP = K / 2;
+  constexpr bool ODD = (K & 1) != 0;
+  static_assert(opp_valid<Lat>(), "velocities must come as rest, then (+c, -c) pairs");
+  const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
+  const unsigned int plane = (unsigned int)p.ncell;
+  const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
+  // element read as population (k, i) of this node, and element receiving its f*_i
+  auto src = [&](int k, int i) -> unsigned int {
+    return KIND == 1 ? eidx<K, Q>(k, i, pi.src<Lat>(i, p.nx, p.ny), plane) : eidx<K, Q>(k, opp<Lat>(i), cell, plane);
+  };
+  auto dst = [&](int k, int i) -> unsigned int {
+    return KIND == 1 ? eidx<K, Q>(k, opp<Lat>(i), pi.src<Lat>(opp<Lat>(i), p.nx, p.ny), plane)
+                     : eidx<K, Q>(k, i, cell, plane);
+  };
+  if constexpr (MODE == MODE_REG) {
+    T fv[K][Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+#pragma unroll
+      for (int kp = 0; kp < KP; ++kp)
+        split(ld_pair_rw(reinterpret_cast<const V*>(F + src(2 * kp, i))), fv[2 * kp][i], fv[2 * kp + 1][i]);
+      if constexpr (ODD) fv[K - 1][i] = to_c(F[src(K - 1, i)]);
+    }
+    finish_node<Lat, SysT, St, FOURIER>(
+        F, p, x, y, z, cell, step, true,
+        [&](int kp, int i, T& a, T& b) {
+          a = fv[2 * kp][i];
+          b = fv[2 * kp + 1][i];
+        },
+        [&](int i) -> T { return fv[ODD ? K - 1 : 0][i]; }, tfac, dst);
+  } else {
+    extern __shared__ __align__(16) unsigned char lbx_smem[];
+    V* colv = reinterpret_cast<V*>(lbx_smem) + threadIdx.x;
+    S* colo = reinterpret_cast<S*>(reinterpret_cast<V*>(lbx_smem) + KP * Q * COLS) + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+#pragma unroll
+      for (int kp = 0; kp < KP; ++kp) stage_pair(colv + (kp * Q + i) * COLS, reinterpret_cast<const V*>(F + src(2 * kp, i)));
+      if constexpr (ODD) stage(colo + i * COLS, F + src(K - 1, i));
+    }
+    stage_wait();
+    finish_node<Lat, SysT, St, FOURIER>(
+        F, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); },
+        [&](int i) -> T { return lds_c(colo + i * COLS); }, tfac, dst);
+  }
+}
+
+template <class Lat, template <typename> class SysT, class St, int MODE, int COLS, bool FOURIER, int KIND>
+__global__ void __launch_bounds__(COLS, StepMode<Lat, SysT, St, COLS>::min_blocks)
+    k_step_inplace(typename St::S* F, const KParams<typename St::C> p) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
+  if constexpr (FOURIER) {
+    __shared__ typename St::C tf[2 * MMS_MAX_MODES];
+    mms_time_table(p, step, tf);
+    if (x >= p.nx) return;
+    step_node_inplace<Lat, SysT, St, MODE, COLS, FOURIER, KIND>(F, p, x, blockIdx.y, blockIdx.z, step,
+                                                                 p.mms_modes != nullptr ? tf : nullptr);
+  } else {
+    if (x >= p.nx) return;
+    step_node_inplace<Lat, SysT, St, MODE, COLS, FOURIER, KIND>(F, p, x, blockIdx.y, blockIdx.z, step, nullptr);
+  }
 }
 
 // Many independent 2D grids in one persistent launch.  Instance j's populations start at

@@ -34,6 +34,8 @@ lbx_status lbx::fail(lbx_status s, const char* fmt, ...) {
 extern "C" const char* lbx_last_error(void) { return g_err.c_str(); }
 extern "C" int lbx_version(void) { return 100; }
 
+static_assert(lbx::MMS_MAX_MODES == LBX_MMS_MAX_MODES, "device mode-table bound");
+
 // ------------------------------------------------------------------------- systems
 static int family_K(int f) {
   switch (f) {
@@ -246,6 +248,8 @@ extern "C" lbx_status lbx_scheme_derive(const lbx_system* sys, const lbx_scheme_
       if (!std::isfinite(d->prescribed_params[i]))
         return fail(LBX_ERR_ARG, "lbx_scheme_derive: prescribed_params[%d] is not finite", i);
   }
+  if (d->streaming != LBX_STREAM_TWO_BUFFERS && d->streaming != LBX_STREAM_IN_PLACE)
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown streaming %d", d->streaming);
   const bool has_trackers = sys->K > sys->NC;
   if (has_trackers && !(d->g_tau > 0.0)) return fail(LBX_ERR_ARG, "lbx_scheme_derive: g_tau must be > 0");
   auto* s = new lbx_scheme();
@@ -597,6 +601,7 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
   }
   p.pf_kind = s.d.prescribed;
   for (int i = 0; i < 8; ++i) p.pf[i] = (T)s.d.prescribed_params[i];
+  p.pf_src_dt = (T)(s.d.prescribed == LBX_PRESCRIBED_ADVECTED ? s.d.prescribed_params[7] * s.dt : 0.0);
 }
 
 // ------------------------------------------------------------------------ dispatch
@@ -755,6 +760,24 @@ struct OpsImpl {
     return cudaGetLastError();
   }
   static const void* batch_fn() { return (const void*)k_step_batch<Lat, SysT, St, MODE>; }
+
+  // In-place steps: 128-thread blocks, per-thread staging for staged systems.
+  template <bool FOURIER, int KIND>
+  static cudaError_t launch_inplace(const lbx_state* st, void* F, const KParams<C>& p, cudaStream_t strm) {
+    const size_t bytes = StepMode<Lat, SysT, St, 128>::smem_bytes;
+    static cudaError_t prep = prepare((const void*)k_step_inplace<Lat, SysT, St, MODE, 128, FOURIER, KIND>, bytes);
+    if (prep != cudaSuccess) return prep;
+    dim3 b = MODE == MODE_REG ? block(st->sch) : dim3(128, 1, 1), g = grid(st->sch, b);
+    k_step_inplace<Lat, SysT, St, MODE, 128, FOURIER, KIND><<<g, b, bytes, strm>>>((S*)F, p);
+    return cudaGetLastError();
+  }
+  static cudaError_t step_inplace(const lbx_state* st, void* F, int kind, int rel, cudaStream_t strm) {
+    KParams<C> p = st->pc<C>();
+    p.step_rel = rel;
+    if (p.mms_modes != nullptr)
+      return kind == 1 ? launch_inplace<true, 1>(st, F, p, strm) : launch_inplace<true, 2>(st, F, p, strm);
+    return kind == 1 ? launch_inplace<false, 1>(st, F, p, strm) : launch_inplace<false, 2>(st, F, p, strm);
+  }
   // staged kernels keep a fixed 128-column layout: larger blocks cannot launch
   static size_t smem_bytes(int threads) { return (MODE == MODE_SMEM && threads > 128) ? (size_t)1 << 30 : smem(threads); }
 };
@@ -765,7 +788,7 @@ static Ops make_ops() {
   return Ops{I::step,       I::init,     I::gather,
              I::scatter,    I::reduce,   I::step_fn,
              I::REG,        I::batch_step, I::batch_fn, I::smem_bytes,
-             sizeof(BatchInst<typename St::C>), sizeof(typename St::S)};
+             sizeof(BatchInst<typename St::C>), sizeof(typename St::S), I::step_inplace};
 }
 
 template <class Lat, template <typename> class SysT>
@@ -861,6 +884,7 @@ void lbx::refresh_params(lbx_state* st) {
 }
 
 lbx_status lbx::run_reduce(lbx_state* st, const double* Qref, int mode, double* host_out) {
+  if (lbx_status s = require_standard_layout(st, "lbx reduction")) return s;
   const int K = st->sch.sys.K;
   if (cudaError_t e = st->ops.reduce(st, st->cur(), Qref, st->d_partials, st->red_blocks, mode))
     return fail(LBX_ERR_CUDA, "reduce launch: %s", cudaGetErrorString(e));
@@ -889,11 +913,15 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
                                void* f_buf_a, void* f_buf_b, lbx_state** out) {
   if (!sch || !Q || !out) return fail(LBX_ERR_ARG, "lbx_init: null argument");
   *out = nullptr;
-  if ((f_buf_a == nullptr) != (f_buf_b == nullptr))
+  const bool inplace = sch->d.streaming == LBX_STREAM_IN_PLACE;
+  if (inplace && f_buf_b != nullptr)
+    return fail(LBX_ERR_ARG, "lbx_init: an in-place state takes one population buffer (f_buf_b must be NULL)");
+  if (!inplace && (f_buf_a == nullptr) != (f_buf_b == nullptr))
     return fail(LBX_ERR_ARG, "lbx_init: pass both population buffers or neither");
   auto* st = new lbx_state();
   st->sch = *sch;
   st->stream = (cudaStream_t)stream;
+  st->inplace = inplace;
   if (!find_ops(sch->sys.family, sch->d.lattice, sch->d.precision, &st->ops)) {
     delete st;
     return fail(LBX_ERR_UNSUPPORTED, "lbx_init: family %d on lattice %d not compiled", sch->sys.family,
@@ -922,8 +950,10 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
   } else {
     CKI(cudaMalloc(&st->fa, bytes));
     st->own_a = true;
-    CKI(cudaMalloc(&st->fb, bytes));
-    st->own_b = true;
+    if (!inplace) {
+      CKI(cudaMalloc(&st->fb, bytes));
+      st->own_b = true;
+    }
   }
   CKI(cudaMalloc(&st->d_step, sizeof(long long)));
   CKI(cudaMemsetAsync(st->d_step, 0, sizeof(long long), st->stream));
@@ -1045,7 +1075,11 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
 static cudaError_t enqueue_steps(lbx_state* st, int64_t n, bool start_a) {
   bool a = start_a;
   for (int64_t r = 0; r < n; ++r) {
-    cudaError_t e = st->ops.step(st, a ? st->fa : st->fb, a ? st->fb : st->fa, (int)r, st->stream);
+    cudaError_t e;
+    if (st->inplace)   // kinds alternate 1, 2 from the start of a pair
+      e = st->ops.step_inplace(st, st->fa, ((st->half + r) & 1) ? 2 : 1, (int)r, st->stream);
+    else
+      e = st->ops.step(st, a ? st->fa : st->fb, a ? st->fb : st->fa, (int)r, st->stream);
     if (e != cudaSuccess) return e;
     a = !a;
   }
@@ -1087,7 +1121,7 @@ extern "C" lbx_status lbx_state_tune(lbx_state* st, int trials, int* staging, in
   const int old_staging = st->staging, old_block = st->block;
   int best_s = old_staging, best_b = old_block;
   double best = -1.0;
-  if (!st->ops.reg) {
+  if (!st->ops.reg && !st->inplace) {   // in place there is no scratch buffer and one launch shape
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     if (cudaError_t e = cudaEventCreate(&e1)) {
@@ -1133,8 +1167,8 @@ extern "C" lbx_status lbx_state_tune(lbx_state* st, int trials, int* staging, in
     st->staging = best_s;
     st->block = best_b;
   }
-  if (staging) *staging = st->ops.reg ? LBX_STAGE_AUTO : st->staging;
-  if (block) *block = st->ops.reg ? 128 : st->block;
+  if (staging) *staging = (st->ops.reg || st->inplace) ? LBX_STAGE_AUTO : st->staging;
+  if (block) *block = (st->ops.reg || st->inplace) ? 128 : st->block;
   if (ms_per_step) *ms_per_step = best;
   return LBX_OK;
 }
@@ -1153,7 +1187,7 @@ extern "C" lbx_status lbx_step(lbx_state* st, int64_t n) {
   if (st->nonfinite) return fail(LBX_ERR_NONFINITE, "lbx_step: state holds non-finite values");
   if (n == 0) return LBX_OK;
   if (st->use_graph) {
-    const auto key = std::make_pair((long long)n, st->cur_a ? 1 : 0);
+    const auto key = std::make_pair((long long)n, st->inplace ? 2 + st->half : (st->cur_a ? 1 : 0));
     auto it = st->graphs.find(key);
     if (it == st->graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -1176,8 +1210,19 @@ extern "C" lbx_status lbx_step(lbx_state* st, int64_t n) {
     if (e != cudaSuccess) return fail(LBX_ERR_CUDA, "lbx_step: launch failed: %s", cudaGetErrorString(e));
   }
   if (!time_dependent(st->sch)) st->step_dirty = true;
-  if (n & 1) st->cur_a = !st->cur_a;
+  if (st->inplace)
+    st->half ^= (int)(n & 1);
+  else if (n & 1)
+    st->cur_a = !st->cur_a;
   st->step += n;
+  return LBX_OK;
+}
+
+// An in-place state between the two steps of a pair holds the pair's intermediate layout:
+// calls that read or write populations refuse it.
+lbx_status lbx::require_standard_layout(const lbx_state* st, const char* who) {
+  if (st->inplace && st->half)
+    return fail(LBX_ERR_STATE, "%s: in-place state after an odd number of steps (take one more step)", who);
   return LBX_OK;
 }
 
@@ -1194,6 +1239,7 @@ static lbx_status sync_step_counter(lbx_state* st) {
 
 extern "C" lbx_status lbx_moments(lbx_state* st, double* Q_out, int out_on_device) {
   if (!st || !Q_out) return fail(LBX_ERR_ARG, "lbx_moments: null argument");
+  if (lbx_status s = require_standard_layout(st, "lbx_moments")) return s;
   const size_t bytes = sizeof(double) * st->sch.sys.K * (size_t)st->sch.ncell;
   if (out_on_device) {
     if (cudaError_t e = st->ops.gather(st, st->cur(), Q_out, nullptr))
@@ -1259,6 +1305,7 @@ extern "C" lbx_status lbx_error_norms(lbx_state* st, const double* Q_ref, int re
 
 extern "C" lbx_status lbx_get_populations(lbx_state* st, double* f_out) {
   if (!st || !f_out) return fail(LBX_ERR_ARG, "lbx_get_populations: null argument");
+  if (lbx_status s = require_standard_layout(st, "lbx_get_populations")) return s;
   const size_t bytes = sizeof(double) * st->sch.sys.K * st->sch.q * (size_t)st->sch.ncell;
   double* d = nullptr;
   CK(cudaMalloc(&d, bytes));
@@ -1272,6 +1319,7 @@ extern "C" lbx_status lbx_get_populations(lbx_state* st, double* f_out) {
 
 extern "C" lbx_status lbx_set_populations(lbx_state* st, const double* f_in) {
   if (!st || !f_in) return fail(LBX_ERR_ARG, "lbx_set_populations: null argument");
+  if (lbx_status s = require_standard_layout(st, "lbx_set_populations")) return s;
   const size_t bytes = sizeof(double) * st->sch.sys.K * st->sch.q * (size_t)st->sch.ncell;
   double* d = nullptr;
   CK(cudaMalloc(&d, bytes));

@@ -51,6 +51,8 @@ struct Ops {
   size_t (*smem_bytes)(int threads);   // dynamic shared memory of a step launch
   size_t inst_bytes;   // sizeof(BatchInst<C>)
   size_t elem_bytes;   // storage bytes per population value
+  // in-place step of the given kind (1 or 2) on the single buffer F (see k_step_inplace)
+  cudaError_t (*step_inplace)(const lbx_state*, void* F, int kind, int rel, cudaStream_t);
 };
 
 lbx_status fail(lbx_status s, const char* fmt, ...);
@@ -68,6 +70,8 @@ struct lbx_state {
   void* fb = nullptr;
   bool own_a = false, own_b = false;
   bool cur_a = true;            // current populations live in fa
+  bool inplace = false;         // one buffer (fa), in-place streaming in step pairs
+  int half = 0;                 // in place: 1 after a pair's first step (layout not standard)
   long long step = 0;
   bool step_dirty = false;      // host counter ahead of the device counter
   bool nonfinite = false;
@@ -103,6 +107,7 @@ namespace lbx {
 void refresh_params(lbx_state* st);
 lbx_status run_reduce(lbx_state* st, const double* Qref, int mode, double* host_out);
 lbx_status ensure_step_counter(lbx_state* st);
+lbx_status require_standard_layout(const lbx_state* st, const char* who);
 void feq0_table(const lbx_scheme& s, double* out);                 // f^eq(Q0) [K][q]
 cudaError_t launch_advance(long long* step, long long n, cudaStream_t s);
 }  // namespace lbx

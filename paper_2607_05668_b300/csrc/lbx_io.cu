@@ -75,6 +75,7 @@ struct CkptHeader {
 
 extern "C" lbx_status lbx_save(lbx_state* st, const char* path) {
   if (!st || !path) return fail(LBX_ERR_ARG, "lbx_save: null argument");
+  if (lbx_status s = require_standard_layout(st, "lbx_save")) return s;
   const size_t bytes = lbx_state_buffer_bytes(&st->sch);
   std::vector<unsigned char> buf(bytes);
   CK(cudaMemcpyAsync(buf.data(), st->cur(), bytes, cudaMemcpyDeviceToHost, st->stream));
@@ -144,6 +145,7 @@ extern "C" lbx_status lbx_load(lbx_state* st, const char* path) {
   CK(cudaStreamSynchronize(st->stream));
   st->step_dirty = false;
   st->nonfinite = false;
+  st->half = 0;                 // a checkpoint holds the standard layout
   return LBX_OK;
 }
 

@@ -573,9 +573,11 @@ struct SysHCNSF {
     const U Tm = V[4] / rho;
     for (int b = 0; b < 3; ++b) Q[7 + b] = (G[4][b] - Tm * G[0][b]) / rho;
   }
+  // cf: the prescribed fields in the flux; cs: those in the drag source (the same values
+  // unless the source takes them at another time level)
   template <typename CF>
   __host__ __device__ static void eval(const T* p, const T* Q0, const T* dQ, T (&dPhi)[K][D], T (&S)[K],
-                                       const CF (&cf)[NCF]) {
+                                       const CF (&cf)[NCF], const CF (&cs)[NCF]) {
     const T gm1 = p[0], mu = p[1], kap = p[2], ieta = p[3], itg = p[4];
     const T EP0 = p[8], T0 = p[9];
     const T alpha = cf[0];
@@ -613,9 +615,9 @@ struct SysHCNSF {
       }
     for (int b = 0; b < 3; ++b)
       for (int c = 0; c < 3; ++c) dPhi[7 + b][c] = dQ[7 + b] * u[c] - (b == c ? dT * itg : T(0));
-    const T drag = (T(1) - alpha) * ieta;
+    const T drag = (T(1) - cs[0]) * ieta;
     S[0] = T(0);
-    for (int a = 0; a < 3; ++a) S[1 + a] = drag * rho * (cf[1 + a] - u[a]);
+    for (int a = 0; a < 3; ++a) S[1 + a] = drag * rho * (cs[1 + a] - u[a]);
     S[4] = S[1] * u[0] + S[2] * u[1] + S[3] * u[2];
     for (int k = 5; k < K; ++k) S[k] = -(Q0[k] + dQ[k]) * itg;
   }

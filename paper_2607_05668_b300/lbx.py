@@ -26,6 +26,7 @@ MMS_NONE, MMS_ADR_SEPARABLE, MMS_FOURIER = 0, 1, 2
 MMS_MAX_MODES = 64
 STAGE_AUTO, STAGE_THREAD, STAGE_LANES2, STAGE_BULK = 0, 1, 2, 3
 PRESCRIBED_NONE, PRESCRIBED_UNIFORM, PRESCRIBED_ADVECTED = 0, 1, 2
+STREAM_TWO_BUFFERS, STREAM_IN_PLACE = 0, 1
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_SUBCHAR", 5: "ERR_NONFINITE",
           6: "ERR_TIMEOUT", 7: "ERR_STATE", 8: "ERR_IO", 9: "ERR_UNSUPPORTED"}
@@ -54,7 +55,7 @@ class SchemeDesc(C.Structure):
                 ("mms_amp", C.c_double), ("allow_subchar_violation", C.c_int),
                 ("mms_modes", C.POINTER(MmsMode)), ("mms_n_modes", C.c_int), ("mms_mean", C.c_double * 8),
                 ("mms_conserved_only", C.c_int), ("prescribed", C.c_int),
-                ("prescribed_params", C.c_double * 8)]
+                ("prescribed_params", C.c_double * 8), ("streaming", C.c_int)]
 
 
 _P = C.c_void_p
@@ -182,10 +183,11 @@ class Scheme:
     def __init__(self, system: System, lattice, extent, scaling, f, tau_lb=0.0, tau_R=0.0,
                  g_tau=0.0, precision=FP64, mms=MMS_NONE, mms_amp=0.0,
                  allow_subchar_violation=False, mms_modes=None, mms_mean=None, mms_conserved_only=False,
-                 prescribed=PRESCRIBED_NONE, prescribed_params=()):
+                 prescribed=PRESCRIBED_NONE, prescribed_params=(), streaming=STREAM_TWO_BUFFERS):
         """mms_modes: sequence of (p, (kx, ky[, kz]), amp, phase, sigma, omega, psi) for
         MMS_FOURIER; mms_mean: the primitives' means; prescribed, prescribed_params: the
-        HCNSF coefficient fields (lbx_prescribed)."""
+        HCNSF coefficient fields (lbx_prescribed); streaming: STREAM_TWO_BUFFERS or
+        STREAM_IN_PLACE (one population buffer, lbx_streaming)."""
         d = SchemeDesc()
         d.lattice = lattice
         ext = list(extent) + [1] * (3 - len(extent))
@@ -212,6 +214,7 @@ class Scheme:
         d.prescribed = int(prescribed)
         for i, v in enumerate(prescribed_params):
             d.prescribed_params[i] = float(v)
+        d.streaming = int(streaming)
         h = _P()
         check(_lib.lbx_scheme_derive(system._h, C.byref(d), C.byref(h)))
         self._h = h
@@ -242,7 +245,8 @@ class State:
         self.K = scheme.system.K
         self._stream = _stream_handle(stream)
         h = _P()
-        bufs = (None, None) if buffers is None else (buffers[0].data_ptr(), buffers[1].data_ptr())
+        bufs = (None, None) if buffers is None else tuple(b.data_ptr() if b is not None else None
+                                                          for b in (list(buffers) + [None])[:2])
         self._buffers = buffers
         if isinstance(Q, torch.Tensor) and Q.is_cuda:
             Qc = Q.detach().to(torch.float64).contiguous()

@@ -749,6 +749,7 @@ class HcnsfPaperCase:
     rot: float = 0.2
     osc: float = 0.1
     c: tuple = (0.1, -0.1, 0.05)
+    theta: float = 0.0       # time level of the prescribed fields in the drag source: t^n + theta dt
 
     @property
     def mu(self):

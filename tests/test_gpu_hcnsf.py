@@ -32,11 +32,12 @@ def _oracle(case, shape, fields, forced):
     tab = case.table()
     return osys, oracle.Scheme(osys, oracle.LATTICES["D3Q7"], shape, case.dx, case.dt,
                                oracle.tau_vector(osys, case.dt, tau_R=case.tau_R, g_tau=case.g_tau),
-                               mms=make_mms(osys, tab.exact, xs, dt=case.dt) if forced else None)
+                               mms=make_mms(osys, tab.exact, xs, dt=case.dt) if forced else None,
+                               source_theta=case.theta)
 
 
-def _run(N, steps, precision=lbx.FP64, forced=True, staging=None):
-    case = syn.HcnsfPaperCase(n=N)
+def _run(N, steps, precision=lbx.FP64, forced=True, staging=None, theta=0.0):
+    case = syn.HcnsfPaperCase(n=N, theta=theta)
     shape = (N, N, N)
     Q = case.table().augmented(syn.coords(shape), 0.0)
     st = lbx.State(W.hcnsf_scheme(case, precision, forced=forced), Q)
@@ -59,6 +60,13 @@ def test_hcnsf_fp64_matches_oracle(N, forced):
     err = H.rel_linf_per_field(Qg, Qo)
     assert err[:5].max() <= 1e-12, err.tolist()
     assert err[5:].max() <= 1e-10, err.tolist()
+
+
+def test_hcnsf_source_at_the_midpoint_matches_oracle():
+    """theta = 1/2: the drag source takes the prescribed fields at t^n + dt/2."""
+    case, st, Qo = _run(16, 8, theta=0.5)
+    err = H.rel_linf_per_field(st.moments(), Qo)
+    assert err[:5].max() <= 1e-12 and err[5:].max() <= 1e-10, err.tolist()
 
 
 @pytest.mark.parametrize("staging", [lbx.STAGE_THREAD, lbx.STAGE_LANES2, lbx.STAGE_BULK])
