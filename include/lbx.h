@@ -145,10 +145,11 @@ typedef enum { LBX_MMS_NONE = 0, LBX_MMS_ADR_SEPARABLE = 1, LBX_MMS_FOURIER = 2 
  *                      r_2 sin t + c_2 + osc sin t c_1),
  *               alpha = a_mean + a_amp [z_0 + z_1 + z_2 + 2 z_0 z_1 z_2], z_d = sin(2 pi xi_d),
  *               xi = x - r sin t - c t;
- *             pf = (a_mean, a_amp, rot, osc, c_0, c_1, c_2, theta).  The paper's values are
- *             (0.5, 0.1, 0.2, 0.1, 0.1, -0.1, 0.05), for which alpha stays in [0, 1].  theta
- *             shifts the fields' time level inside the drag source to t^n + theta dt (the
- *             flux keeps t^n; theta = 1/2 puts the source at the step's midpoint). */
+ *             pf = (a_mean, a_amp, rot, osc, c_0, c_1, c_2, theta_S, theta_Phi).  The
+ *             paper's values are (0.5, 0.1, 0.2, 0.1, 0.1, -0.1, 0.05), for which alpha stays
+ *             in [0, 1].  theta_S and theta_Phi move the fields' time level inside the drag
+ *             source and inside the equilibrium flux to t^n + theta dt (0: the state's time
+ *             level; 1/2: the step's midpoint, where the manufactured forcing is taken). */
 typedef enum { LBX_PRESCRIBED_NONE = 0, LBX_PRESCRIBED_UNIFORM = 1, LBX_PRESCRIBED_ADVECTED = 2 } lbx_prescribed;
 
 /* Population storage of a state:
@@ -206,7 +207,7 @@ typedef struct {
     double mms_mean[8];    /* FOURIER: mean of each primitive                           */
     int mms_conserved_only; /* FOURIER: nonzero leaves the tracker components unforced */
     int prescribed;        /* lbx_prescribed (HCNSF_3D only; NONE for every other family) */
-    double prescribed_params[8]; /* pf of the prescribed fields                          */
+    double prescribed_params[10]; /* pf of the prescribed fields                         */
     int streaming;         /* lbx_streaming                                             */
 } lbx_scheme_desc;
 

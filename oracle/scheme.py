@@ -16,7 +16,7 @@ Steps, in the paper's order and notation:
 Prescribed coefficient fields c(x, t) (HCNSF porosity and solid velocity) are evaluated
 at the node coordinates x = (i, j, l) dx and at the time level of the state they multiply:
 t^n in the equilibrium flux and the state source of step n, t = 0 at initialisation;
-`source_theta` moves the source's fields to t^n + theta dt.
+`source_theta` and `flux_theta` move the source's and the flux's fields to t^n + theta dt.
 
 Arrays: populations f are [K, q, *grid], fields Q are [K, *grid], grid = (nz,) ny, nx.
 The streaming here pushes post-collision values to x + c_i with torch.roll, exactly as
@@ -63,7 +63,7 @@ def tau_vector(system, dt, tau_cons=None, tau_R=None, g_tau=None):
 
 class Scheme:
     def __init__(self, system, lattice: Lattice, shape, dx, dt, tau, mms=None,
-                 shifted=False, Q0=None, source_theta=0.0):
+                 shifted=False, Q0=None, source_theta=0.0, flux_theta=0.0):
         self.sys = system
         self.lat = lattice
         self.shape = tuple(shape)
@@ -76,6 +76,7 @@ class Scheme:
         self.mms = mms
         self.shifted = shifted
         self.source_theta = float(source_theta)
+        self.flux_theta = float(flux_theta)
         self.Q0 = None if Q0 is None else torch.as_tensor(Q0, dtype=F64)
         # node coordinates (x, y[, z]), x fastest, for prescribed coefficient fields
         axes = [torch.arange(n, dtype=F64) * self.dx for n in self.shape]
@@ -87,7 +88,7 @@ class Scheme:
 
     # -- Eq. feq --------------------------------------------------------------------
     def feq(self, Q, t=0.0):
-        Phi = flux_at(self.sys, Q, self.xx, t)       # [K, D, *grid]
+        Phi = flux_at(self.sys, Q, self.xx, t + self.flux_theta * self.dt)   # [K, D, *grid]
         out = []
         for i, ci in enumerate(self.c):
             cphi = sum(ci[d] * Phi[:, d] for d in range(self.lat.D) if ci[d] != 0)

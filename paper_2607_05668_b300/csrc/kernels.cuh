@@ -64,7 +64,7 @@ struct KParams {
   T mms_mean[8];               // mean of each primitive
   int pf_kind;                 // prescribed coefficient fields (HCNSF): 0 none, 1 uniform, 2 advected
   T pf[8];                     // their parameters (see prescribed_fields)
-  T pf_src_dt;                 // time offset of the fields inside the source (0 or a fraction of dt)
+  T pf_src_dt, pf_flux_dt;     // time offsets of the fields inside the source and the flux
 };
 
 // Whether the step reads the step index: manufactured forcing or time-dependent prescribed
@@ -175,6 +175,41 @@ __device__ __forceinline__ void sc_pi(T a, T* s, T* c) { sincospi(a, s, c); }
 template <typename T>
 __device__ __forceinline__ void sc_pi(Dual<T> a, Dual<T>* s, Dual<T>* c) { sincospi_dual(a, s, c); }
 
+// The time-independent part of the advected-solid fields at x: s_d, c_d and the rotation
+// pattern r (kind 2).
+template <typename U>
+struct SolidAt {
+  U s[3], c[3], r[3];
+};
+template <typename T, typename U>
+__device__ __forceinline__ SolidAt<U> solid_at(const KParams<T>& p, const U (&x)[3]) {
+  SolidAt<U> a;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) sc_pi(U(T(2)) * x[d], &a.s[d], &a.c[d]);
+  const T rot = p.pf[2];
+  a.r[0] = U(rot) * a.s[0] * a.c[1] * a.c[2];
+  a.r[1] = U(-rot) * a.c[0] * a.s[1] * a.c[2];
+  a.r[2] = U(rot) * a.c[0] * a.c[1] * a.s[2];
+  return a;
+}
+// The fields at time t from the node's time-independent part.
+template <typename T, typename U>
+__device__ __forceinline__ void solid_fields(const KParams<T>& p, const U (&x)[3], const SolidAt<U>& a, T t,
+                                             U (&cf)[4]) {
+  T st, ct;
+  sincos(t, &st, &ct);
+  const T osc = p.pf[3];
+  cf[1] = a.r[0] * U(ct) + U(p.pf[4]) + U(osc * st) * a.c[2];
+  cf[2] = a.r[1] * U(ct) + U(p.pf[5]) + U(osc * ct) * a.c[0];
+  cf[3] = a.r[2] * U(st) + U(p.pf[6]) + U(osc * st) * a.c[1];
+  U z[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    U zc;
+    sc_pi(U(T(2)) * (x[d] - a.r[d] * U(st) - U(p.pf[4 + d] * t)), &z[d], &zc);
+  }
+  cf[0] = U(p.pf[0]) + U(p.pf[1]) * (z[0] + z[1] + z[2] + U(T(2)) * z[0] * z[1] * z[2]);
+}
 template <typename T, typename U>
 __device__ __forceinline__ void prescribed_fields(const KParams<T>& p, const U (&x)[3], T t, U (&cf)[4]) {
   if (p.pf_kind == 1) {
@@ -186,23 +221,7 @@ __device__ __forceinline__ void prescribed_fields(const KParams<T>& p, const U (
     cf[1] = cf[2] = cf[3] = U(T(0));
     return;
   }
-  U s[3], c[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) sc_pi(U(T(2)) * x[d], &s[d], &c[d]);
-  T st, ct;
-  sincos(t, &st, &ct);
-  const T rot = p.pf[2], osc = p.pf[3];
-  const U r[3] = {U(rot) * s[0] * c[1] * c[2], U(-rot) * c[0] * s[1] * c[2], U(rot) * c[0] * c[1] * s[2]};
-  cf[1] = r[0] * U(ct) + U(p.pf[4]) + U(osc * st) * c[2];
-  cf[2] = r[1] * U(ct) + U(p.pf[5]) + U(osc * ct) * c[0];
-  cf[3] = r[2] * U(st) + U(p.pf[6]) + U(osc * st) * c[1];
-  U z[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    U zc;
-    sc_pi(U(T(2)) * (x[d] - r[d] * U(st) - U(p.pf[4 + d] * t)), &z[d], &zc);
-  }
-  cf[0] = U(p.pf[0]) + U(p.pf[1]) * (z[0] + z[1] + z[2] + U(T(2)) * z[0] * z[1] * z[2]);
+  solid_fields(p, x, solid_at(p, x), t, cf);
 }
 
 // Flux and source at a node at state time t (the family's eval()), with the prescribed
@@ -214,12 +233,15 @@ __device__ __forceinline__ void eval_node(const KParams<T>& p, int x, int y, int
   if constexpr (NcfOf<Sys>::value > 0) {
     const T xc[3] = {T(x) * p.dx, T(y) * p.dx, T(z) * p.dx};
     T cf[NcfOf<Sys>::value];
-    prescribed_fields(p, xc, t, cf);
-    if (p.pf_src_dt != T(0) && p.pf_kind == 2) {
+    if (p.pf_src_dt != p.pf_flux_dt && p.pf_kind == 2) {
+      // two time levels of a moving solid: the spatial factors are shared
+      const SolidAt<T> a = solid_at(p, xc);
       T cs[NcfOf<Sys>::value];
-      prescribed_fields(p, xc, t + p.pf_src_dt, cs);
+      solid_fields(p, xc, a, t + p.pf_flux_dt, cf);
+      solid_fields(p, xc, a, t + p.pf_src_dt, cs);
       Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cs);
     } else {
+      prescribed_fields(p, xc, t + p.pf_flux_dt, cf);
       Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cf);
     }
   } else {

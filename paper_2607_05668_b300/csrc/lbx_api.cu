@@ -244,7 +244,7 @@ extern "C" lbx_status lbx_scheme_derive(const lbx_system* sys, const lbx_scheme_
       return fail(LBX_ERR_ARG, "lbx_scheme_derive: prescribed fields belong to HCNSF_3D only");
     if (d->prescribed != LBX_PRESCRIBED_UNIFORM && d->prescribed != LBX_PRESCRIBED_ADVECTED)
       return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown prescribed fields %d", d->prescribed);
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 10; ++i)
       if (!std::isfinite(d->prescribed_params[i]))
         return fail(LBX_ERR_ARG, "lbx_scheme_derive: prescribed_params[%d] is not finite", i);
   }
@@ -601,7 +601,9 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
   }
   p.pf_kind = s.d.prescribed;
   for (int i = 0; i < 8; ++i) p.pf[i] = (T)s.d.prescribed_params[i];
-  p.pf_src_dt = (T)(s.d.prescribed == LBX_PRESCRIBED_ADVECTED ? s.d.prescribed_params[7] * s.dt : 0.0);
+  const bool moving = s.d.prescribed == LBX_PRESCRIBED_ADVECTED;
+  p.pf_src_dt = (T)(moving ? s.d.prescribed_params[7] * s.dt : 0.0);
+  p.pf_flux_dt = (T)(moving ? s.d.prescribed_params[8] * s.dt : 0.0);
 }
 
 // ------------------------------------------------------------------------ dispatch

@@ -55,7 +55,7 @@ class SchemeDesc(C.Structure):
                 ("mms_amp", C.c_double), ("allow_subchar_violation", C.c_int),
                 ("mms_modes", C.POINTER(MmsMode)), ("mms_n_modes", C.c_int), ("mms_mean", C.c_double * 8),
                 ("mms_conserved_only", C.c_int), ("prescribed", C.c_int),
-                ("prescribed_params", C.c_double * 8), ("streaming", C.c_int)]
+                ("prescribed_params", C.c_double * 10), ("streaming", C.c_int)]
 
 
 _P = C.c_void_p

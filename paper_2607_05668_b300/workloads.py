@@ -102,7 +102,7 @@ def hcnsf_system(case):
 def hcnsf_prescribed(case):
     """The case's advected-solid porosity and solid velocity (lbx_prescribed ADVECTED)."""
     return L.PRESCRIBED_ADVECTED, ((case.alpha_mean, case.alpha_amp, case.rot, case.osc) + tuple(case.c)
-                                   + (getattr(case, "theta", 0.0),))
+                                   + (getattr(case, "theta", 0.0), getattr(case, "theta_flux", 0.0)))
 
 
 def hcnsf_scheme(case, precision=L.FP32_SHIFT, forced=False, extent=None):

@@ -736,7 +736,9 @@ class HcnsfPaperCase:
     mu = kappa = 3.52 Pa s / (rho0 c_s L) and eta = 0.000348 s c_s / L with rho0 = 1.225 kg/m^3,
     c_s = 287.4 m/s, L = 1 m.  The prescribed fields and the solid displacement are read in
     the same units (amplitudes in c_s, time in L/c_s).
-    Recipe: acoustic f = 0.05, tau_R = 10 (double) or 20 (float), g_tau = 3; N = 32 .. 256."""
+    Recipe: acoustic f = 0.05, tau_R = 10 (double) or 20 (float), g_tau = 3; N = 32 .. 256.
+    The drag source takes the prescribed fields at the step's midpoint t^n + dt/2 and the
+    equilibrium flux at t^n (theta = 1/2, theta_flux = 0)."""
     n: int
     gamma: float = 1.4
     A: float = 0.2
@@ -749,7 +751,8 @@ class HcnsfPaperCase:
     rot: float = 0.2
     osc: float = 0.1
     c: tuple = (0.1, -0.1, 0.05)
-    theta: float = 0.0       # time level of the prescribed fields in the drag source: t^n + theta dt
+    theta: float = 0.5       # time level of the prescribed fields in the drag source: t^n + theta dt
+    theta_flux: float = 0.0  # the same inside the equilibrium flux
 
     @property
     def mu(self):

@@ -33,11 +33,11 @@ def _oracle(case, shape, fields, forced):
     return osys, oracle.Scheme(osys, oracle.LATTICES["D3Q7"], shape, case.dx, case.dt,
                                oracle.tau_vector(osys, case.dt, tau_R=case.tau_R, g_tau=case.g_tau),
                                mms=make_mms(osys, tab.exact, xs, dt=case.dt) if forced else None,
-                               source_theta=case.theta)
+                               source_theta=case.theta, flux_theta=case.theta_flux)
 
 
-def _run(N, steps, precision=lbx.FP64, forced=True, staging=None, theta=0.0):
-    case = syn.HcnsfPaperCase(n=N, theta=theta)
+def _run(N, steps, precision=lbx.FP64, forced=True, staging=None, theta=0.5, theta_flux=0.0):
+    case = syn.HcnsfPaperCase(n=N, theta=theta, theta_flux=theta_flux)
     shape = (N, N, N)
     Q = case.table().augmented(syn.coords(shape), 0.0)
     st = lbx.State(W.hcnsf_scheme(case, precision, forced=forced), Q)
@@ -62,9 +62,10 @@ def test_hcnsf_fp64_matches_oracle(N, forced):
     assert err[5:].max() <= 1e-10, err.tolist()
 
 
-def test_hcnsf_source_at_the_midpoint_matches_oracle():
-    """theta = 1/2: the drag source takes the prescribed fields at t^n + dt/2."""
-    case, st, Qo = _run(16, 8, theta=0.5)
+@pytest.mark.parametrize("theta,theta_flux", [(0.5, 0.0), (0.5, 0.5), (0.0, 0.5)])
+def test_hcnsf_field_time_levels_match_oracle(theta, theta_flux):
+    """The drag source and the flux take the prescribed fields at t^n + theta dt."""
+    case, st, Qo = _run(16, 8, theta=theta, theta_flux=theta_flux)
     err = H.rel_linf_per_field(st.moments(), Qo)
     assert err[:5].max() <= 1e-12 and err[5:].max() <= 1e-10, err.tolist()
 
@@ -150,3 +151,44 @@ def test_hcnsf_paper_flow_is_second_order(prec):
     orders = [[math.log2(errs[i][k] / errs[i + 1][k]) for k in range(5)] for i in range(2)]
     print("errors", errs, "orders", orders)
     assert all(1.6 < o < 2.5 for row in orders for o in row), orders
+
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+FIELDS = {"rho": [0], "rhou": [1, 2, 3], "E": [4], "G_u": [10, 5, 6]}
+
+
+def _rel(Qg, Qex, comps):
+    l2 = [float(torch.sqrt(((Qg[k] - Qex[k]) ** 2).sum() / (Qex[k] ** 2).sum())) for k in comps]
+    li = [float((Qg[k] - Qex[k]).abs().max() / Qex[k].abs().max()) for k in comps]
+    return math.sqrt(sum(e * e for e in l2)), math.sqrt(sum(e * e for e in li))
+
+
+def test_hcnsf_reproduces_paper_table3_float_at_256():
+    """Table 3, HCNSF float rows at N = 256 (t = 1, tau_R = 20): relative L2 of rho, rho u, E and
+    the diagonal G_u within 1 %, relative Linf of rho, rho u and E within 1 %; the local order
+    between N = 128 and 256 within 0.15 of the printed least-squares EOC."""
+    rows = [l.split() for l in open(f"{GOLDEN}/table3_hcnsf.txt") if l.strip() and not l.startswith("#")]
+    ref = {r[1]: (float(r[2]), float(r[3]), float(r[4]), float(r[5])) for r in rows if r[0] == "fp32"}
+    errs = {}
+    for N in (128, 256):
+        case = syn.HcnsfPaperCase(n=N, tau_R=20.0)
+        xs = syn.coords((N, N, N))
+        tab = case.table()
+        st = lbx.State(W.hcnsf_scheme(case, lbx.FP32_SHIFT, forced=True), tab.augmented(xs, 0.0).cuda())
+        n = int(round(1.0 / case.dt))
+        st.step(n)
+        Qex = tab.augmented(xs, n * case.dt).cuda()
+        Qg = st.moments(device=True)
+        torch.cuda.synchronize()
+        errs[N] = {f: _rel(Qg, Qex, c) for f, c in FIELDS.items()}
+        st.close()
+        del Qg, Qex
+        torch.cuda.empty_cache()
+    for f, (li, li_eoc, l2, l2_eoc) in ref.items():
+        got_l2, got_li = errs[256][f]
+        order = math.log2(errs[128][f][0] / got_l2)
+        print(f"{f}: L2 {got_l2:.4e} (paper {l2:.4e}), Linf {got_li:.4e} (paper {li:.4e}), order {order:.3f} ({l2_eoc})")
+        assert abs(got_l2 / l2 - 1) < 0.01
+        if f != "G_u":
+            assert abs(got_li / li - 1) < 0.01
+        assert abs(order - l2_eoc) < 0.15
