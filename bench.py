@@ -175,18 +175,20 @@ def fields(workload, case):
     return {"nsf": syn.nsf_fields, "mhd": syn.mhd_fields, "adr": syn.adr_fields}[workload](case)
 
 
-def scheme(W, L, workload, case, prec):
+def scheme(W, L, workload, case, prec, inplace=False):
     p = PREC[prec]
+    sm = L.STREAM_IN_PLACE if inplace else L.STREAM_TWO_BUFFERS
     if workload == "nsf":
-        return W.nsf_scheme(case, p)
+        return W.nsf_scheme(case, p, streaming=sm)
     if workload == "mhd":
-        return W.mhd_scheme(case, p)
+        return W.mhd_scheme(case, p, streaming=sm)
     if workload == "nsf12":
         return W.nsf12_scheme(case, p)
     if workload == "mhd18":
         return W.mhd18_scheme(case, p)
     if workload == "hcnsf":
-        return W.hcnsf_scheme(case, p)
+        return W.hcnsf_scheme(case, p, streaming=sm)
+    assert not inplace
     return W.adr_scheme(case, p)
 
 
@@ -237,12 +239,13 @@ def launch_desc(L, rep):
             "tuned_ms_per_step": rep["ms_per_step"]}
 
 
-def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=False):
-    """Time one grid workload; returns a dict of rate, ms per step and GB/s."""
+def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=False, inplace=False):
+    """Time one grid workload; returns a dict of rate, ms per step and GB/s.  inplace: one
+    population buffer (the steps run in pairs, so `steps` must be even)."""
     case = make_case(workload, n)
     K, q = kq(workload)
     ncell = cells(workload, case)
-    st = L.State(scheme(W, L, workload, case, precision), fields(workload, case).cuda(), stream=stream)
+    st = L.State(scheme(W, L, workload, case, precision, inplace), fields(workload, case).cuda(), stream=stream)
     launch = st.tune()
     if graph:
         st.use_graph(True)
@@ -252,7 +255,9 @@ def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=Fals
     nbytes = 2 * K * q * STORE_BYTES[precision] * ncell
     out = {"lup_s": ncell / (ms * 1e-3), "ms_per_step": ms, "gbs": nbytes / (ms * 1e-3) / 1e9,
            "bytes_per_launch": nbytes, "finite": st.check_finite(), "graph": graph,
-           "launch": launch_desc(L, launch)}
+           "launch": launch_desc(L, launch) if not inplace else
+           {"kernel": "k_step_inplace (one buffer, kinds 1 and 2 alternating)", "block": 128},
+           "population_buffers": 1 if inplace else 2}
     return out, st
 
 
@@ -332,14 +337,18 @@ def run_variants(L, W, args, stream, peak, probe_fp64=None):
                                ("nsf12", "fp64", 1024, 100), ("mhd18", "fp32", 512, 500),
                                ("mhd18", "fp64", 512, 100), ("hcnsf", "fp32", 256, 100),
                                ("hcnsf", "fp16", 256, 100), ("hcnsf", "fp64", 256, 20),
-                               ("adr", "fp64", 64, 500)):
+                               ("adr", "fp64", 64, 500), ("nsf", "fp32", 1024, "inplace"),
+                               ("mhd", "fp32", 256, "inplace"), ("hcnsf", "fp32", 256, "inplace")):
+        inplace = steps == "inplace"
+        steps = {"nsf": 1000, "mhd": 50, "hcnsf": 100}[wl] if inplace else steps
         # the 64^2 case is launch-latency bound: its 500 steps replay as one CUDA graph
-        r, st = measure_grid(L, W, wl, prec, n, steps, 5 if wl != "adr" else 500, stream, graph=(wl == "adr"))
+        r, st = measure_grid(L, W, wl, prec, n, steps, 6 if wl != "adr" else 500, stream, graph=(wl == "adr"),
+                             inplace=inplace)
         st.close()
         r["frac_of_hbm_peak"] = r["gbs"] / peak
         ncell = n ** (3 if wl in DIM3 else 2)
-        r["traffic_per_launch"] = profile_traffic(f"{wl}_{prec}", ncell)
-        r["traffic_kernel"] = profile_kernel(f"{wl}_{prec}")
+        r["traffic_per_launch"] = None if inplace else profile_traffic(f"{wl}_{prec}", ncell)
+        r["traffic_kernel"] = None if inplace else profile_kernel(f"{wl}_{prec}")
         if prec == "fp64":
             fl = profile_entry(f"{wl}_fp64_flops")
             if fl:
@@ -347,7 +356,7 @@ def run_variants(L, W, args, stream, peak, probe_fp64=None):
                 r["alu_roofline"] = {"bound": "alu", "achieved": ach, "unit": "GFLOP/s",
                                      "fp64_flops_per_node": fl["fp64_flops_per_node"],
                                      "peak_probe": probe_fp64, "frac": ach / probe_fp64 if probe_fp64 else None}
-        v[f"{wl}_{prec}_{n}"] = r
+        v[f"{wl}_{prec}_{n}" + ("_inplace" if inplace else "")] = r
         torch.cuda.empty_cache()
     r = measure_batch(L, W, 200, 5, stream)
     r["frac_of_hbm_peak"] = r["gbs"] / peak

@@ -27,20 +27,20 @@ def nsf_system(case):
                     Q0=case.reference_state())
 
 
-def nsf_scheme(case, precision=L.FP64, lattice=L.D2Q9, tau_lb=0.0):
+def nsf_scheme(case, precision=L.FP64, lattice=L.D2Q9, tau_lb=0.0, streaming=L.STREAM_TWO_BUFFERS):
     """Diffusive refinement dt = f dx^2, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
     return L.Scheme(nsf_system(case), lattice, (case.n, case.n), L.DIFFUSIVE, case.f,
-                    tau_lb=tau_lb, tau_R=case.tau_R, g_tau=case.g_tau, precision=precision)
+                    tau_lb=tau_lb, tau_R=case.tau_R, g_tau=case.g_tau, precision=precision, streaming=streaming)
 
 
 def mhd_system(case):
     return L.System(L.MHD_J_TRACK, params=(case.gamma, case.eta), Q0=case.reference_state())
 
 
-def mhd_scheme(case, precision=L.FP32_SHIFT, lattice=L.D3Q19):
+def mhd_scheme(case, precision=L.FP32_SHIFT, lattice=L.D3Q19, streaming=L.STREAM_TWO_BUFFERS):
     """Acoustic refinement dt = f dx, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
     return L.Scheme(mhd_system(case), lattice, (case.n, case.n, case.n), L.ACOUSTIC, case.f,
-                    tau_R=case.tau_R, g_tau=case.g_tau, precision=precision)
+                    tau_R=case.tau_R, g_tau=case.g_tau, precision=precision, streaming=streaming)
 
 
 # ------------------------------------------------------------- forced (manufactured) runs
@@ -105,7 +105,7 @@ def hcnsf_prescribed(case):
                                    + (getattr(case, "theta", 0.0), getattr(case, "theta_flux", 0.0)))
 
 
-def hcnsf_scheme(case, precision=L.FP32_SHIFT, forced=False, extent=None):
+def hcnsf_scheme(case, precision=L.FP32_SHIFT, forced=False, extent=None, streaming=L.STREAM_TWO_BUFFERS):
     """The paper's HCNSF recipe on D3Q7: acoustic dt = f dx, tau_LB = 1/2 + tau_R dt, trackers
     g_tau, prescribed fields of the moving solid; forced: the case's manufactured flow."""
     kind, pf = hcnsf_prescribed(case)
@@ -115,4 +115,5 @@ def hcnsf_scheme(case, precision=L.FP32_SHIFT, forced=False, extent=None):
                              precision=precision, tau_R=case.tau_R, g_tau=case.g_tau,
                              prescribed=kind, prescribed_params=pf)
     return L.Scheme(hcnsf_system(case), L.D3Q7, ext, L.ACOUSTIC, case.f, tau_R=case.tau_R,
-                    g_tau=case.g_tau, precision=precision, prescribed=kind, prescribed_params=pf)
+                    g_tau=case.g_tau, precision=precision, prescribed=kind, prescribed_params=pf,
+                    streaming=streaming)

@@ -99,3 +99,37 @@ def test_init_without_device_fails_loudly():
     with pytest.raises(lbx.LbxError) as e:
         lbx.State(sch, np.ones((3, 8, 8)))
     assert e.value.name == "ERR_CUDA"
+
+
+def test_hcnsf_declaration_and_scheme_checks():
+    """3D homogenized NSF: 14 components in the paper's order, 5 conserved, D3Q7 with the
+    advected-solid fields; zero tracker background and eta > 0 required; prescribed fields
+    and in-place streaming validated on the host."""
+    lbx = _lbx()
+    Q0 = [1.0, 0.59, 0.59, 0.59, 3.03] + [0.0] * 9
+    s = lbx.System(lbx.HCNSF_3D, (1.4, 0.01, 0.01, 0.1), Q0)
+    assert (s.K, s.n_cons, s.dim) == (14, 5, 3)
+    assert s.names[5:8] == ["G_u11", "G_u22", "G_T_x"] and s.names[10] == "G_u00"
+    pf = (0.5, 0.1, 0.2, 0.1, 0.1, -0.1, 0.05, 0.5, 0.0)
+    sch = lbx.Scheme(s, lbx.D3Q7, (32, 32, 32), lbx.ACOUSTIC, 0.05, tau_R=10.0, g_tau=3.0,
+                     prescribed=lbx.PRESCRIBED_ADVECTED, prescribed_params=pf, streaming=lbx.STREAM_IN_PLACE)
+    assert sch.buffer_bytes == 14 * 7 * 32 ** 3 * 8 and sch.tau[5] == pytest.approx(4.0)
+    bad_q0 = list(Q0)
+    bad_q0[9] = 0.1
+    with pytest.raises(lbx.LbxError, match="tracker background"):
+        lbx.System(lbx.HCNSF_3D, (1.4, 0.01, 0.01, 0.1), bad_q0)
+    with pytest.raises(lbx.LbxError, match="eta"):
+        lbx.System(lbx.HCNSF_3D, (1.4, 0.01, 0.01, 0.0), Q0)
+    with pytest.raises(lbx.LbxError, match="dimension"):
+        lbx.Scheme(s, lbx.D2Q5, (8, 8), lbx.ACOUSTIC, 0.05, tau_R=10.0, g_tau=3.0)
+    with pytest.raises(lbx.LbxError, match="unknown prescribed"):
+        lbx.Scheme(s, lbx.D3Q7, (8, 8, 8), lbx.ACOUSTIC, 0.05, tau_R=10.0, g_tau=3.0, prescribed=7)
+    with pytest.raises(lbx.LbxError, match="not finite"):
+        lbx.Scheme(s, lbx.D3Q7, (8, 8, 8), lbx.ACOUSTIC, 0.05, tau_R=10.0, g_tau=3.0,
+                   prescribed=lbx.PRESCRIBED_UNIFORM, prescribed_params=(float("nan"),))
+    with pytest.raises(lbx.LbxError, match="unknown streaming"):
+        lbx.Scheme(s, lbx.D3Q7, (8, 8, 8), lbx.ACOUSTIC, 0.05, tau_R=10.0, g_tau=3.0, streaming=5)
+    e = lbx.System(lbx.EULER, (1.4,), (1.0, 0.1, 0.1, 2.5))
+    with pytest.raises(lbx.LbxError, match="HCNSF_3D only"):
+        lbx.Scheme(e, lbx.D2Q5, (8, 8), lbx.ACOUSTIC, 0.05, tau_R=1.0, prescribed=lbx.PRESCRIBED_UNIFORM,
+                   prescribed_params=(0.5, 0.0, 0.0, 0.0))
