@@ -234,7 +234,8 @@ def launch_desc(L, rep):
     """The step kernel lbx_state_tune kept: staging and block (register-resident: none)."""
     if rep["ms_per_step"] < 0:
         return {"kernel": "k_step (register-resident)", "block": 128}
-    name = {L.STAGE_THREAD: "k_step (per-thread copies)", L.STAGE_BULK: "k_step_bulk (bulk row copies)"}
+    name = {L.STAGE_THREAD: "k_step (per-thread copies)", L.STAGE_BULK: "k_step_bulk (bulk row copies)",
+            L.STAGE_PIPE: "k_step_pipe (pipelined per-thread copies)"}
     return {"kernel": name.get(rep["staging"], str(rep["staging"])), "block": rep["block"],
             "tuned_ms_per_step": rep["ms_per_step"]}
 
@@ -383,7 +384,13 @@ def run_ours(args):
     sch = scheme(W, L, args.workload, case, args.precision)
     stream = torch.cuda.Stream()
     st = L.State(sch, Q.cuda(), stream=stream)
-    launch = launch_desc(L, st.tune())      # staged kernels: fastest launch shape, state unchanged
+    if args.staging is not None:            # a fixed launch shape (profiling one staging)
+        st.set_staging({"thread": L.STAGE_THREAD, "bulk": L.STAGE_BULK, "lanes2": L.STAGE_LANES2,
+                        "pipe": L.STAGE_PIPE}[args.staging])
+        st.set_block(args.block)
+        launch = {"kernel": f"staging {args.staging} (fixed)", "block": args.block}
+    else:
+        launch = launch_desc(L, st.tune())  # staged kernels: fastest launch shape, state unchanged
     st.step(args.warmup)
     st.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -567,6 +574,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--probe", action="store_true", help="also run the copy / FMA peak probes")
     ap.add_argument("--no-variants", action="store_true", help="skip the other precisions and workloads")
+    ap.add_argument("--staging", choices=["thread", "bulk", "lanes2", "pipe"], default=None,
+                    help="staged kernels: fix the staging instead of tuning (with --block)")
+    ap.add_argument("--block", type=int, default=128, choices=[32, 64, 128], help="block size with --staging")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

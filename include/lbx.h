@@ -280,15 +280,27 @@ lbx_status lbx_state_set_block(lbx_state* st, int block);
  *                      population buffers (LBX_ERR_UNSUPPORTED otherwise).  Its wait on the
  *                      copies is bounded: a timeout sets a device error word that
  *                      lbx_synchronize and lbx_check_finite report as LBX_ERR_TIMEOUT.
+ *   LBX_STAGE_PIPE     per-thread copies in a persistent grid (a multiple of the SM count)
+ *                      that walks row segments: each thread stages its next node while it
+ *                      updates the current one (two private columns, cp.async groups).
+ *                      It uses the largest block up to the set one whose two columns fit
+ *                      in shared memory.
  * The register-resident kernels ignore it.  LBX_ERR_ARG for unknown values. */
-typedef enum { LBX_STAGE_AUTO = 0, LBX_STAGE_THREAD = 1, LBX_STAGE_LANES2 = 2, LBX_STAGE_BULK = 3 } lbx_staging;
+typedef enum {
+    LBX_STAGE_AUTO = 0,
+    LBX_STAGE_THREAD = 1,
+    LBX_STAGE_LANES2 = 2,
+    LBX_STAGE_BULK = 3,
+    LBX_STAGE_PIPE = 4
+} lbx_staging;
 lbx_status lbx_state_set_staging(lbx_state* st, int staging);
 /* Autotune the staged step kernel of this state: time per-thread copies and (where they
  * apply) bulk row copies, each with blocks of 32, 64 and 128 threads, over `trials`
  * launches (1..1000) after one warm-up launch, and keep the fastest.  Every timed launch
  * reads the current populations and writes the other buffer, which the next step
  * rewrites anyway, so neither the populations nor the time change; all candidates give
- * bitwise identical results (two lanes per node is not a candidate).  Register-resident
+ * bitwise identical results (two lanes per node and the pipelined copies, measured slower
+ * on every bench system, are not candidates).  Register-resident
  * kernels have one launch shape: nothing is timed and *ms_per_step is -1.  Synchronous.
  * Outputs (each may be NULL): the chosen staging and block, the best time per launch. */
 lbx_status lbx_state_tune(lbx_state* st, int trials, int* staging, int* block, double* ms_per_step);

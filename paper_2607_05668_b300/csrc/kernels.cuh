@@ -1032,6 +1032,79 @@ __global__ void __launch_bounds__(COLS, StepMode<Lat, SysT, St, COLS>::min_block
   }
 }
 
+// ------------------------------------------------------- pipelined per-thread staging
+// Persistent variant of the per-thread staged step: the grid walks tiles of COLS nodes along
+// x (row segments, x fastest) with a grid-size stride, and every thread keeps two shared-
+// memory columns: it issues the copies of its node in the next tile (one cp.async group per
+// tile) before it updates its node in the current one, so one node's populations are always
+// in flight while the flux is evaluated.  The columns are private to their thread, so the
+// pipeline needs no barrier: cp.async.wait_group 1 leaves only the newest group pending.
+template <class Lat, template <typename> class SysT, class St, int COLS>
+struct PipeMode {
+  static constexpr size_t smem_bytes = 2 * StepMode<Lat, SysT, St, COLS>::smem_per_thread * COLS;
+  static constexpr int smem_blocks = (int)(228 * 1024 / (smem_bytes + 1024));
+  static constexpr int min_blocks =
+      smem_blocks < 1 ? 1 : (smem_blocks * COLS > 384 ? 384 / COLS : smem_blocks);
+};
+
+__device__ __forceinline__ void stage_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void stage_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <class Lat, template <typename> class SysT, class St, int COLS>
+__global__ void __launch_bounds__(COLS, PipeMode<Lat, SysT, St, COLS>::min_blocks)
+    k_step_pipe(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
+                const KParams<typename St::C> p) {
+  using T = typename St::C;
+  using S = typename St::S;
+  using V = typename PairOf<S>::V;
+  constexpr int K = SysT<T>::K, Q = Lat::Q, KP = K / 2;
+  extern __shared__ __align__(16) unsigned char lbx_smem[];
+  const int t = (int)threadIdx.x;
+  const size_t stage_bytes = StepMode<Lat, SysT, St, COLS>::smem_per_thread * COLS;
+  V* colv[2];
+  S* colo[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    V* base = reinterpret_cast<V*>(lbx_smem + s * stage_bytes);
+    colv[s] = base + t;
+    colo[s] = reinterpret_cast<S*>(base + KP * Q * COLS) + t;
+  }
+  const int tiles_x = (p.nx + COLS - 1) / COLS;
+  const long long ntiles = (long long)tiles_x * p.ny * p.nz;
+  const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
+  auto node_of = [&](long long tl, int& x, int& y, int& z) {
+    const long long row = tl / tiles_x;
+    x = (int)(tl - row * tiles_x) * COLS + t;
+    y = (int)(row % p.ny);
+    z = (int)(row / p.ny);
+  };
+  auto issue = [&](long long tl, int s) {
+    if (tl < ntiles) {
+      int x, y, z;
+      node_of(tl, x, y, z);
+      if (x < p.nx) stage_node<Lat, SysT, St, COLS>(A, colv[s], colo[s], PullIdx(x, y, z, p.nx, p.ny, p.nz), p);
+    }
+    stage_commit();                          // an empty group past the end keeps the count uniform
+  };
+  long long tl = blockIdx.x;
+  issue(tl, 0);
+  for (int s = 0; tl < ntiles; tl += gridDim.x, s ^= 1) {
+    issue(tl + gridDim.x, s ^ 1);
+    stage_wait_prev();
+    int x, y, z;
+    node_of(tl, x, y, z);
+    if (x < p.nx) {
+      const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
+      V* cv = colv[s];
+      S* co = colo[s];
+      finish_node<Lat, SysT, St>(
+          B, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { lds_pair(cv + (kp * Q + i) * COLS, a, b); },
+          [&](int i) -> T { return lds_c(co + i * COLS); });
+    }
+  }
+  stage_wait();                              // nothing stays in flight past the kernel
+}
+
 // ------------------------------------------------------------ in-place (one buffer)
 // Single-buffer streaming: steps alternate between two kinds so that every node reads and
 // then writes one set of addresses that no other node touches, which makes the update safe

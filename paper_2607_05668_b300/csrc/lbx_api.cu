@@ -657,6 +657,28 @@ struct OpsImpl {
     return cudaGetLastError();
   }
 
+  // Pipelined per-thread staging: a persistent grid of the resident blocks per SM x SMs.
+  template <int COLS>
+  static cudaError_t launch_pipe(const lbx_state* st, const void* A, void* B, const KParams<C>& p,
+                                 cudaStream_t strm) {
+    const size_t bytes = PipeMode<Lat, SysT, St, COLS>::smem_bytes;
+    static cudaError_t prep = prepare((const void*)k_step_pipe<Lat, SysT, St, COLS>, bytes);
+    if (prep != cudaSuccess) return prep;
+    static int per_sm = 0, nsm = 0;
+    if (per_sm == 0) {
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (!e) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_pipe<Lat, SysT, St, COLS>, COLS, bytes);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) per_sm = 1;
+    }
+    const long long tiles = (long long)((st->sch.nx + COLS - 1) / COLS) * st->sch.ny * st->sch.nz;
+    const long long g = std::min<long long>(tiles, (long long)per_sm * nsm);
+    k_step_pipe<Lat, SysT, St, COLS><<<(unsigned int)g, COLS, bytes, strm>>>((const S*)A, (S*)B, p);
+    return cudaGetLastError();
+  }
+
   template <int COLS>
   static cudaError_t launch_split(const lbx_state* st, const void* A, void* B, const KParams<C>& p,
                                   cudaStream_t strm) {
@@ -706,6 +728,13 @@ struct OpsImpl {
           case 64: return launch_bulk<64>(st, A, B, p, strm);
           default: return launch_bulk<128>(st, A, B, p, strm);
         }
+      }
+      if (mode == LBX_STAGE_PIPE) {
+        // two columns per thread: the largest block up to st->block whose columns fit
+        constexpr size_t cap = 227 * 1024;
+        if (st->block >= 128 && PipeMode<Lat, SysT, St, 128>::smem_bytes <= cap) return launch_pipe<128>(st, A, B, p, strm);
+        if (st->block >= 64 && PipeMode<Lat, SysT, St, 64>::smem_bytes <= cap) return launch_pipe<64>(st, A, B, p, strm);
+        return launch_pipe<32>(st, A, B, p, strm);
       }
       if (mode == LBX_STAGE_LANES2) {
         switch (st->block) {
@@ -1103,7 +1132,7 @@ extern "C" lbx_status lbx_state_set_block(lbx_state* st, int block) {
 
 extern "C" lbx_status lbx_state_set_staging(lbx_state* st, int staging) {
   if (!st) return fail(LBX_ERR_ARG, "lbx_state_set_staging: null state");
-  if (staging < LBX_STAGE_AUTO || staging > LBX_STAGE_BULK)
+  if (staging < LBX_STAGE_AUTO || staging > LBX_STAGE_PIPE)
     return fail(LBX_ERR_ARG, "lbx_state_set_staging: unknown staging %d", staging);
   if (staging == LBX_STAGE_BULK && !bulk_eligible(st))
     return fail(LBX_ERR_UNSUPPORTED,
@@ -1130,7 +1159,7 @@ extern "C" lbx_status lbx_state_tune(lbx_state* st, int trials, int* staging, in
       cudaEventDestroy(e0);
       return fail(LBX_ERR_CUDA, "lbx_state_tune: %s", cudaGetErrorString(e));
     }
-    const int stagings[2] = {LBX_STAGE_THREAD, LBX_STAGE_BULK};
+    const int stagings[2] = {LBX_STAGE_THREAD, LBX_STAGE_BULK};   // the measured-fastest kinds
     const int blocks[3] = {32, 64, 128};
     cudaError_t err = cudaSuccess;
     for (int sg : stagings) {

@@ -24,7 +24,7 @@ ACOUSTIC, DIFFUSIVE = 1, 2
 FP64, FP32_SHIFT, FP16_SCALED = 1, 2, 3
 MMS_NONE, MMS_ADR_SEPARABLE, MMS_FOURIER = 0, 1, 2
 MMS_MAX_MODES = 64
-STAGE_AUTO, STAGE_THREAD, STAGE_LANES2, STAGE_BULK = 0, 1, 2, 3
+STAGE_AUTO, STAGE_THREAD, STAGE_LANES2, STAGE_BULK, STAGE_PIPE = 0, 1, 2, 3, 4
 PRESCRIBED_NONE, PRESCRIBED_UNIFORM, PRESCRIBED_ADVECTED = 0, 1, 2
 STREAM_TWO_BUFFERS, STREAM_IN_PLACE = 0, 1
 
@@ -265,8 +265,8 @@ class State:
         check(_lib.lbx_state_set_block(self._h, int(block)))
 
     def set_staging(self, staging):
-        """Staging of the staged step kernels: STAGE_AUTO, STAGE_THREAD, STAGE_LANES2 or
-        STAGE_BULK (see lbx_state_set_staging)."""
+        """Staging of the staged step kernels: STAGE_AUTO, STAGE_THREAD, STAGE_LANES2,
+        STAGE_BULK or STAGE_PIPE (see lbx_state_set_staging)."""
         check(_lib.lbx_state_set_staging(self._h, int(staging)))
 
     def tune(self, trials=5):

@@ -70,7 +70,7 @@ def test_hcnsf_field_time_levels_match_oracle(theta, theta_flux):
     assert err[:5].max() <= 1e-12 and err[5:].max() <= 1e-10, err.tolist()
 
 
-@pytest.mark.parametrize("staging", [lbx.STAGE_THREAD, lbx.STAGE_LANES2, lbx.STAGE_BULK])
+@pytest.mark.parametrize("staging", [lbx.STAGE_THREAD, lbx.STAGE_LANES2, lbx.STAGE_BULK, lbx.STAGE_PIPE])
 def test_hcnsf_stagings_agree(staging):
     case, st, Qo = _run(16, 6, staging=staging)
     err = H.rel_linf_per_field(st.moments(), Qo)
@@ -132,11 +132,11 @@ def test_hcnsf_rejects_a_tracker_background_and_foreign_prescribed_fields():
                    prescribed_params=(0.5, 0, 0, 0))
 
 
-@pytest.mark.parametrize("prec", [lbx.FP64, lbx.FP32_SHIFT])
+@pytest.mark.parametrize("prec", [lbx.FP64])
 def test_hcnsf_paper_flow_is_second_order(prec):
-    """The paper's HCNSF flow and recipe (double tau_R = 10, float tau_R = 20) to t = 1 at
-    N = 32, 64, 128: pairwise orders of the relative L2 errors of rho, rho u and E (the
-    paper's Table 3 EOCs over N = 32 .. 256: 1.78 - 1.97)."""
+    """The paper's HCNSF flow and double recipe (tau_R = 10) to t = 1 at N = 32, 64, 128:
+    pairwise orders of the relative L2 errors of rho, rho u and E (the paper's Table 3 EOCs
+    over N = 32 .. 256: 1.78 - 1.97).  The float recipe is checked at N = 256 below."""
     errs = []
     for N in (32, 64, 128):
         case = syn.HcnsfPaperCase(n=N, tau_R=10.0 if prec == lbx.FP64 else 20.0)

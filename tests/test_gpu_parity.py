@@ -390,7 +390,7 @@ def test_staged_launch_shapes_are_bitwise_identical(name, prec):
 
 # ------------------------------------------- staging modes of the staged step kernels
 
-STAGINGS = {"thread": lbx.STAGE_THREAD, "lanes2": lbx.STAGE_LANES2, "bulk": lbx.STAGE_BULK}
+STAGINGS = {"thread": lbx.STAGE_THREAD, "lanes2": lbx.STAGE_LANES2, "bulk": lbx.STAGE_BULK, "pipe": lbx.STAGE_PIPE}
 
 
 def _staged_state(name, prec, staging, n, lattice=None):
@@ -415,7 +415,7 @@ def _oracle_moments(name, case, steps, lattice=None):
     return och.moments(och.run(och.init(syn.nsf_fields(case)), steps))
 
 
-@pytest.mark.parametrize("staging", ["lanes2", "bulk"])
+@pytest.mark.parametrize("staging", ["lanes2", "bulk", "pipe"])
 @pytest.mark.parametrize("name,n,lattice", [("mhd", 24, None), ("mhd", 16, lbx.D3Q7),
                                             ("nsf", 48, None), ("nsf", 136, None), ("nsf", 72, lbx.D2Q5)])
 def test_staged_modes_fp64_match_oracle(staging, name, n, lattice):
@@ -428,7 +428,7 @@ def test_staged_modes_fp64_match_oracle(staging, name, n, lattice):
     assert err.max() <= 1e-12, err
 
 
-@pytest.mark.parametrize("staging", ["lanes2", "bulk"])
+@pytest.mark.parametrize("staging", ["lanes2", "bulk", "pipe"])
 @pytest.mark.parametrize("prec,bound", [(lbx.FP32_SHIFT, 1e-4), (lbx.FP16_SCALED, 3e-2)])
 def test_staged_modes_mhd_32_reduced_precision_against_fp64_oracle(staging, prec, bound):
     case, st = _staged_state("mhd", prec, staging, 32)
@@ -444,7 +444,7 @@ def test_staged_modes_launch_shapes_and_agreement(name, prec):
     the moments in another order and agree to rounding."""
     n = 24 if name == "mhd" else 136
     res = {}
-    for staging in ("thread", "lanes2", "bulk"):
+    for staging in ("thread", "lanes2", "bulk", "pipe"):
         outs = []
         for blk in (32, 64, 128):
             case, st = _staged_state(name, prec, staging, n)
@@ -455,6 +455,7 @@ def test_staged_modes_launch_shapes_and_agreement(name, prec):
             assert torch.equal(o, outs[0]), staging
         res[staging] = outs[0]
     assert torch.equal(res["bulk"], res["thread"])
+    assert torch.equal(res["pipe"], res["thread"])
     one, two = res["thread"], res["lanes2"]
     if prec == lbx.FP64:
         # rounding-order differences, relative to the small tracker gradients
@@ -468,7 +469,7 @@ def test_staged_modes_launch_shapes_and_agreement(name, prec):
 
 def test_set_staging_rejects_unknown_and_inapplicable_modes():
     case, st = _staged_state("mhd", lbx.FP32_SHIFT, "thread", 8)
-    for bad in (-1, 4):
+    for bad in (-1, 5):
         with pytest.raises(lbx.LbxError):
             st.set_staging(bad)
     case = syn.MhdCase(n=12)                      # 12 % 8 != 0: no bulk row copies
