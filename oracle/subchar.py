@@ -29,14 +29,17 @@ def directions(D, n):
     return np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], 1)
 
 
-def flux_jacobian(system, q):
-    """J[k, a, l] = d Phi_{k,a} / d Q_l at one node state q [K]."""
+def flux_jacobian(system, q, cf=None):
+    """J[k, a, l] = d Phi_{k,a} / d Q_l at one node state q [K] (with the node's prescribed
+    coefficients cf for systems that have them)."""
     q = torch.as_tensor(q, dtype=torch.float64)
-    return torch.autograd.functional.jacobian(lambda v: system.flux(v), q)
+    if cf is None:
+        return torch.autograd.functional.jacobian(lambda v: system.flux(v), q)
+    return torch.autograd.functional.jacobian(lambda v: system.flux(v, cf), q)
 
 
-def node_max_speed(system, q, dirs):
-    J = flux_jacobian(system, q).numpy()
+def node_max_speed(system, q, dirs, cf=None):
+    J = flux_jacobian(system, q, cf).numpy()
     best = 0.0
     for n in dirs:
         A = np.einsum("kal,a->kl", J, n)
@@ -44,14 +47,16 @@ def node_max_speed(system, q, dirs):
     return best
 
 
-def max_speed(system, Q, n_dirs=64, nodes=None):
+def max_speed(system, Q, n_dirs=64, nodes=None, cf=None):
     """max over the given node indices (flattened grid; all nodes if None) and over
-    n_dirs directions of the spectral radius of A_n."""
+    n_dirs directions of the spectral radius of A_n.  cf: the prescribed coefficient fields
+    on the same grid (a sequence of tensors), for systems that take them."""
     K = Q.shape[0]
     Qf = Q.reshape(K, -1)
     idx = range(Qf.shape[1]) if nodes is None else nodes
     dirs = directions(system.D, n_dirs)
-    return max(node_max_speed(system, Qf[:, j], dirs) for j in idx)
+    cff = None if cf is None else [c.reshape(-1) for c in cf]
+    return max(node_max_speed(system, Qf[:, j], dirs, None if cff is None else [c[j] for c in cff]) for j in idx)
 
 
 def check(system, Q, lam, cs2, n_dirs=64, nodes=None):

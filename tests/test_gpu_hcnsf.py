@@ -192,3 +192,20 @@ def test_hcnsf_reproduces_paper_table3_float_at_256():
         if f != "G_u":
             assert abs(got_li / li - 1) < 0.01
         assert abs(order - l2_eoc) < 0.15
+
+
+def test_hcnsf_subchar_bound_dominates_oracle_eigenvalues():
+    """The closed-form speed bound of lbx_subchar_check (alpha = 1, the largest dissipative
+    coupling) against the oracle's numeric spectral radius of the augmented flux Jacobian
+    with the prescribed porosity at each sampled node, over 48 directions."""
+    N = 24
+    case = syn.HcnsfPaperCase(n=N)
+    xs = syn.coords((N, N, N))
+    Q = case.table().augmented(xs, 0.4)
+    st = lbx.State(W.hcnsf_scheme(case, lbx.FP64), Q)
+    got = st.subchar_check()["max_speed"] / st.scheme.lam
+    osys = oracle.systems.HomogenizedNsf3D(case.gamma, case.mu, case.kappa, case.eta, case.g_tau * case.dt,
+                                           fields=case.prescribed)
+    cf = case.prescribed(xs, 0.4)
+    num = oracle.subchar.max_speed(osys, Q, n_dirs=48, nodes=list(range(0, N ** 3, 997)), cf=cf)
+    assert num * (1 - 1e-9) <= got <= 2.0 * num, (got, num)
