@@ -339,7 +339,9 @@ lbx_status lbx_set_populations(lbx_state* st, const double* f_in);
 
 /* Step counter and time t = step * dt. */
 lbx_status lbx_state_time(const lbx_state* st, int64_t* step, double* t);
-/* Device pointer to the buffer holding the current populations (storage type). */
+/* Device pointer to the buffer holding the current populations (storage type).  For an
+ * IN_PLACE state after an odd number of steps the buffer holds the step pair's
+ * intermediate layout (see lbx_streaming). */
 void* lbx_state_populations(const lbx_state* st);
 /* Wait for all work queued on the state's stream. */
 lbx_status lbx_synchronize(lbx_state* st);

@@ -19,6 +19,9 @@ Component orders (fixed by this library):
   Burgers             (u)                                                     K = 1
   Euler               (rho, m_x, m_y, E)                                      K = 4
   Maxwell TM          (E_z, H_x, H_y)                                         K = 3
+  12-component NSF    (rho, m_x, m_y, E, G_rho(2), G_mx(2), G_my(2), G_E(2))   K = 12
+  18-component MHD    (rho, m_x, m_y, E, B_x, B_y, G of the six, 2 each)      K = 18
+  3D homogenized NSF  (rho, m(3), E, G_u11, G_u22, G_T(3), G_u00, G_u01, G_u02, G_u12)  K = 14
 """
 from __future__ import annotations
 

@@ -773,3 +773,25 @@ def test_hcnsf_exact_trackers_are_the_symmetric_velocity_and_temperature_gradien
     for tt in (0.0, 0.4, 1.0, 2.5):
         al = case.prescribed(syn.coords((16, 16, 16)), tt)[0]
         assert float(al.min()) >= 0.0 and float(al.max()) <= 1.0
+
+
+def test_prescribed_field_time_levels_reach_flux_and_source():
+    """Sec. 3, HCNSF with prescribed fields (reading of their time level): step n evaluates the
+    flux's fields at t^n + theta_Phi dt and the drag source's at t^n + theta_S dt."""
+    calls = []
+
+    def fields(xx, t):
+        calls.append(float(t) if not torch.is_tensor(t) else float(t.reshape(-1)[0]))
+        one = torch.ones_like(xx[0])
+        return [0.5 * one, 0.1 * one, 0.0 * one, 0.0 * one]
+
+    sysm = S.HomogenizedNsf3D(1.4, 0.01, 0.01, 0.1, 0.3, fields=fields)
+    q = torch.tensor([1.0, 0.2, 0.1, 0.0, 3.0] + [0.0] * 9, dtype=F64)
+    Q = q.reshape(14, 1, 1, 1).expand(14, 2, 2, 2).contiguous()
+    dt = 0.01
+    sch = oracle.Scheme(sysm, oracle.LATTICES["D3Q7"], (2, 2, 2), 0.5, dt, torch.tensor([0.8] * 5 + [4.0] * 9, dtype=F64),
+                        source_theta=0.5, flux_theta=0.25)
+    f = sch.init(Q)
+    calls.clear()
+    sch.step(f, 3 * dt)
+    assert calls == pytest.approx([3.25 * dt, 3.5 * dt])      # flux (equilibrium), then source
