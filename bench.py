@@ -247,6 +247,8 @@ def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=Fals
     K, q = kq(workload)
     ncell = cells(workload, case)
     st = L.State(scheme(W, L, workload, case, precision, inplace), fields(workload, case).cuda(), stream=stream)
+    if inplace:
+        st.set_block(64)        # no tuner in place (no scratch buffer): the staged kernels' usual best
     launch = st.tune()
     if graph:
         st.use_graph(True)
@@ -257,7 +259,8 @@ def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=Fals
     out = {"lup_s": ncell / (ms * 1e-3), "ms_per_step": ms, "gbs": nbytes / (ms * 1e-3) / 1e9,
            "bytes_per_launch": nbytes, "finite": st.check_finite(), "graph": graph,
            "launch": launch_desc(L, launch) if not inplace else
-           {"kernel": "k_step_inplace (one buffer, kinds 1 and 2 alternating)", "block": 128},
+           {"kernel": "in place, kinds 1 and 2 alternating (k_step_bulk_inplace for staged systems with "
+                      "nx % 8 == 0, else k_step_inplace)", "block": 64},
            "population_buffers": 1 if inplace else 2}
     return out, st
 

@@ -163,8 +163,9 @@ typedef enum { LBX_PRESCRIBED_NONE = 0, LBX_PRESCRIBED_UNIFORM = 1, LBX_PRESCRIB
  *                layout is the pair's intermediate one: every call that reads or writes the
  *                populations (moments, populations, norms, sums, finite and sub-characteristic
  *                checks, save, load) fails with LBX_ERR_STATE until one more step is taken.
- *                Per-thread staging with 128-thread blocks for staged systems; no bulk
- *                copies, tuning, batches or adjoint. */
+ *                Staged systems use bulk row copies where the staging resolves to them
+ *                (lbx_state_set_staging, blocks of lbx_state_set_block), else per-thread
+ *                copies in 128-thread blocks; no tuning, batches or adjoint. */
 typedef enum { LBX_STREAM_TWO_BUFFERS = 0, LBX_STREAM_IN_PLACE = 1 } lbx_streaming;
 
 #define LBX_MMS_MAX_MODES 64

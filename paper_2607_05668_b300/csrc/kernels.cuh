@@ -401,8 +401,8 @@ struct StepMode {
   static constexpr size_t smem_per_thread = (size_t)SysT<typename St::C>::K * Lat::Q * sizeof(typename St::S);
   static constexpr size_t smem_bytes = value == MODE_SMEM ? smem_per_thread * COLS : 0;
   // blocks per SM the launch bounds ask the register allocator to allow: 4 for
-  // register-resident 4/8-byte storage, 3 when FP16 conversions need more registers, and
-  // for staged kernels what shared memory lets reside (228 KB per SM), at most 3
+  // register-resident kernels (128 registers; the FP16 ones spill at 5), and for staged
+  // kernels what shared memory lets reside (228 KB per SM), at most 384 threads
   static constexpr int smem_blocks = value == MODE_SMEM ? (int)(228 * 1024 / smem_bytes) : 0;
   static constexpr int min_blocks =
       value == MODE_REG ? 4
@@ -925,10 +925,16 @@ __device__ __forceinline__ void bulk_g2s(unsigned int dst, const void* src, unsi
 }
 constexpr unsigned long long BULK_WAIT_NS = 1000000000ull;   // 1 s
 
-template <class Lat, template <typename> class SysT, class St, int COLS>
-__global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_blocks)
-    k_step_bulk(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
-                const KParams<typename St::C> p) {
+// The bulk-staged step of one block.  KIND 0: two buffers (pull from A, write B); KIND 1, 2:
+// the in-place step kinds on one buffer (A == B; see k_step_inplace): kind 1 pulls the same
+// rows as KIND 0 and stores each post-collision population into the opposite slot it read
+// from, kind 2 copies the node row's swapped slots unshifted and stores in the standard
+// slots.  Every element a node uses is read and written by that node alone; the 16-byte
+// widening of a shifted row also reads a few elements of neighbouring blocks that this
+// block never uses.
+template <class Lat, template <typename> class SysT, class St, int COLS, int KIND>
+__device__ __forceinline__ void bulk_step_body(const typename St::S* A, typename St::S* B,
+                                               const KParams<typename St::C>& p) {
   using M = BulkMode<Lat, SysT, St, COLS>;
   using T = typename St::C;
   using S = typename St::S;
@@ -936,6 +942,7 @@ __global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_block
   constexpr int K = M::K, Q = Lat::Q, KP = M::KP, EP = M::EP, EO = M::EO;
   constexpr bool ODD = M::ODD;
   static_assert(Q <= 32, "one issuing lane per velocity");
+  static_assert(KIND == 0 || opp_valid<Lat>(), "velocities must come as rest, then (+c, -c) pairs");
   extern __shared__ __align__(16) unsigned char lbx_smem[];
   V* rowv = reinterpret_cast<V*>(lbx_smem + 16);                 // [KP q][ROWP]
   S* rowo = reinterpret_cast<S*>(rowv + (size_t)KP * Q * M::ROWP); // [q][ROWO]
@@ -943,19 +950,26 @@ __global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_block
   const int t = (int)threadIdx.x, x0 = (int)blockIdx.x * COLS, y = (int)blockIdx.y, z = (int)blockIdx.z;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const unsigned int plane = (unsigned int)p.ncell;
+  // offset of the element a thread uses in the shared row of velocity i
+  auto sh = [](int i, int E) { return KIND == 2 ? 0 : M::shift(i, E); };
 
   if (t == 0) mbar_init(bar, 1);
   __syncthreads();
   if (t < 32) {
     if (t < Q) {
+      // lane t copies the rows of velocity t: slot sv of the rows at (y - c_y, z - c_z),
+      // shifted by c_x (kind 2: the node row's opposite slot, unshifted)
       int cx = 0, cy = 0, cz = 0;
+      if constexpr (KIND != 2) {
 #pragma unroll
-      for (int j = 0; j < Q; ++j)
-        if (j == t) {
-          cx = Lat::c(j, 0);
-          cy = Lat::c(j, 1);
-          cz = Lat::c(j, 2);
-        }
+        for (int j = 0; j < Q; ++j)
+          if (j == t) {
+            cx = Lat::c(j, 0);
+            cy = Lat::c(j, 1);
+            cz = Lat::c(j, 2);
+          }
+      }
+      const int sv = KIND == 2 ? opp<Lat>(t) : t;
       const int ys = y - cy < 0 ? ny - 1 : (y - cy >= ny ? 0 : y - cy);
       const int zs = z - cz < 0 ? nz - 1 : (z - cz >= nz ? 0 : z - cz);
       const unsigned int cell0 = ((unsigned int)zs * (unsigned int)ny + (unsigned int)ys) * (unsigned int)nx;
@@ -970,20 +984,20 @@ __global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_block
 #pragma unroll
       for (int kp = 0; kp < KP; ++kp)
         bulk_g2s(smem_u32(rowv + (size_t)(kp * Q + t) * M::ROWP + (lop - xsp)),
-                 Av + (size_t)(kp * Q + t) * plane + cell0 + lop, bp, bar);
+                 Av + (size_t)(kp * Q + sv) * plane + cell0 + lop, bp, bar);
       if constexpr (ODD)
         bulk_g2s(smem_u32(rowo + (size_t)t * M::ROWO + (loo - xso)),
-                 A + (size_t)2 * KP * Q * plane + (size_t)t * plane + cell0 + loo, bo, bar);
+                 A + (size_t)2 * KP * Q * plane + (size_t)sv * plane + cell0 + loo, bo, bar);
     }
     __syncwarp();
     if (t == 0) mbar_arrive(bar);
   }
   const int x = x0 + t;
   if (x >= nx) return;
+  const PullIdx pi(x, y, z, nx, ny, nz);
 
   // periodic wrap at the row ends: the slot the clamped copy left empty
-  if (x == 0 || x == nx - 1) {
-    const PullIdx pi(x, y, z, nx, ny, nz);
+  if (KIND != 2 && (x == 0 || x == nx - 1)) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int cx = Lat::c(i, 0);
@@ -992,7 +1006,7 @@ __global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_block
 #pragma unroll
         for (int kp = 0; kp < KP; ++kp)
           rowv[(size_t)(kp * Q + i) * M::ROWP + t + M::shift(i, EP)] =
-              __ldg(reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, plane)));
+              *reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, plane));
         if constexpr (ODD) rowo[(size_t)i * M::ROWO + t + M::shift(i, EO)] = A[eidx<K, Q>(K - 1, i, src, plane)];
       }
     }
@@ -1004,10 +1018,31 @@ __global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_block
   }
   const unsigned int cell = ((unsigned int)z * (unsigned int)ny + (unsigned int)y) * (unsigned int)nx + x;
   const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
-  finish_node<Lat, SysT, St>(
-      B, p, x, y, z, cell, step, true,
-      [&](int kp, int i, T& a, T& b) { lds_pair(rowv + (size_t)(kp * Q + i) * M::ROWP + t + M::shift(i, EP), a, b); },
-      [&](int i) -> T { return lds_c(rowo + (size_t)(ODD ? i : 0) * M::ROWO + t + M::shift(i, EO)); });
+  auto get_pair = [&](int kp, int i, T& a, T& b) { lds_pair(rowv + (size_t)(kp * Q + i) * M::ROWP + t + sh(i, EP), a, b); };
+  auto get_odd = [&](int i) -> T { return lds_c(rowo + (size_t)(ODD ? i : 0) * M::ROWO + t + sh(i, EO)); };
+  if constexpr (KIND == 0) {
+    finish_node<Lat, SysT, St>(B, p, x, y, z, cell, step, true, get_pair, get_odd);
+  } else {
+    auto dst = [&](int k, int i) -> unsigned int {
+      return KIND == 1 ? eidx<K, Q>(k, opp<Lat>(i), pi.src<Lat>(opp<Lat>(i), nx, ny), plane)
+                       : eidx<K, Q>(k, i, cell, plane);
+    };
+    finish_node<Lat, SysT, St>(B, p, x, y, z, cell, step, true, get_pair, get_odd, nullptr, dst);
+  }
+}
+
+template <class Lat, template <typename> class SysT, class St, int COLS>
+__global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_blocks)
+    k_step_bulk(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
+                const KParams<typename St::C> p) {
+  bulk_step_body<Lat, SysT, St, COLS, 0>(A, B, p);
+}
+
+// In-place step of kind 1 or 2 with bulk row copies (one buffer F).
+template <class Lat, template <typename> class SysT, class St, int COLS, int KIND>
+__global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_blocks)
+    k_step_bulk_inplace(typename St::S* F, const KParams<typename St::C> p) {
+  bulk_step_body<Lat, SysT, St, COLS, KIND>(F, F, p);
 }
 
 // Register budget per thread follows the residency the populations' staging allows.
@@ -1117,22 +1152,13 @@ __global__ void __launch_bounds__(COLS, PipeMode<Lat, SysT, St, COLS>::min_block
 // A kind-1 step followed by a kind-2 step moves every population exactly as two pull steps
 // between two buffers, with the same arithmetic (finish_node), so the populations after an
 // even number of steps are bitwise those of the two-buffer kernels, in half the memory.
-template <class Lat>
-__host__ __device__ constexpr int opp(int i) {
-  return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
-}
-template <class Lat>
-__host__ __device__ constexpr bool opp_valid() {
-  for (int i = 0; i < Lat::Q; ++i)
-    for (int d = 0; d < 3; ++d)
-      if (Lat::c(opp<Lat>(i), d) != -Lat::c(i, d)) return false;
-  return true;
-}
 
-// plain (coherent) loads: the in-place kernels write the buffer they read
-__device__ __forceinline__ double2 ld_pair_rw(const double2* p) { return *p; }
-__device__ __forceinline__ float2 ld_pair_rw(const float2* p) { return *p; }
-__device__ __forceinline__ __half2 ld_pair_rw(const __half2* p) { return *p; }
+// Loads of the in-place kernels: the read-only (non-coherent) path is safe although the
+// kernel writes the buffer, because every element is read only by the node that owns it,
+// before that node writes it, and by no thread after.
+__device__ __forceinline__ double2 ld_pair_rw(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld_pair_rw(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ __half2 ld_pair_rw(const __half2* p) { return __ldg(p); }
 
 template <class Lat, template <typename> class SysT, class St, int MODE, int COLS, bool FOURIER, int KIND>
 __device__ __forceinline__ void step_node_inplace(typename St::S* F, const KParams<typename St::C>& p, int x,
@@ -1161,7 +1187,7 @@ __device__ __forceinline__ void step_node_inplace(typename St::S* F, const KPara
 #pragma unroll
       for (int kp = 0; kp < KP; ++kp)
         split(ld_pair_rw(reinterpret_cast<const V*>(F + src(2 * kp, i))), fv[2 * kp][i], fv[2 * kp + 1][i]);
-      if constexpr (ODD) fv[K - 1][i] = to_c(F[src(K - 1, i)]);
+      if constexpr (ODD) fv[K - 1][i] = to_c(__ldg(F + src(K - 1, i)));
     }
     finish_node<Lat, SysT, St, FOURIER>(
         F, p, x, y, z, cell, step, true,

@@ -57,6 +57,20 @@ struct LatD3Q19 {
   static constexpr double cs2 = 1.0 / 3.0;
 };
 
+// The velocity opposite to i (c_opp(i) = -c_i): every set lists rest first, then (+c, -c)
+// pairs.  opp_valid() checks that structure at compile time.
+template <class Lat>
+__host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+}
+template <class Lat>
+__host__ __device__ constexpr bool opp_valid() {
+  for (int i = 0; i < Lat::Q; ++i)
+    for (int d = 0; d < 3; ++d)
+      if (Lat::c(opp<Lat>(i), d) != -Lat::c(i, d)) return false;
+  return true;
+}
+
 // Weights for binary32 arithmetic: the moving weights rounded to multiples of 2^-26
 // (exact in binary32) and the rest weight 1 minus their sum, so that the weights add up
 // to exactly 1.  The nearest binary32 values of 1/3, 1/6, 1/9, ... add up to about

@@ -802,11 +802,34 @@ struct OpsImpl {
     k_step_inplace<Lat, SysT, St, MODE, 128, FOURIER, KIND><<<g, b, bytes, strm>>>((S*)F, p);
     return cudaGetLastError();
   }
+  template <int COLS, int KIND>
+  static cudaError_t launch_bulk_inplace(const lbx_state* st, void* F, const KParams<C>& p, cudaStream_t strm) {
+    const size_t bytes = BulkMode<Lat, SysT, St, COLS>::smem_bytes;
+    static cudaError_t prep = prepare((const void*)k_step_bulk_inplace<Lat, SysT, St, COLS, KIND>, bytes);
+    if (prep != cudaSuccess) return prep;
+    const dim3 b(COLS, 1, 1), g((st->sch.nx + COLS - 1) / COLS, st->sch.ny, st->sch.nz);
+    k_step_bulk_inplace<Lat, SysT, St, COLS, KIND><<<g, b, bytes, strm>>>((S*)F, p);
+    return cudaGetLastError();
+  }
+  template <int KIND>
+  static cudaError_t bulk_inplace(const lbx_state* st, void* F, const KParams<C>& p, cudaStream_t strm) {
+    switch (st->block) {
+      case 32: return launch_bulk_inplace<32, KIND>(st, F, p, strm);
+      case 64: return launch_bulk_inplace<64, KIND>(st, F, p, strm);
+      default: return launch_bulk_inplace<128, KIND>(st, F, p, strm);
+    }
+  }
+  // Staged systems use bulk row copies where the staging resolves to them (st->block wide),
+  // otherwise per-thread copies in 128-thread blocks; forced runs take the latter.
   static cudaError_t step_inplace(const lbx_state* st, void* F, int kind, int rel, cudaStream_t strm) {
     KParams<C> p = st->pc<C>();
     p.step_rel = rel;
     if (p.mms_modes != nullptr)
       return kind == 1 ? launch_inplace<true, 1>(st, F, p, strm) : launch_inplace<true, 2>(st, F, p, strm);
+    if constexpr (MODE == MODE_SMEM) {
+      if (resolved_staging(st) == LBX_STAGE_BULK)
+        return kind == 1 ? bulk_inplace<1>(st, F, p, strm) : bulk_inplace<2>(st, F, p, strm);
+    }
     return kind == 1 ? launch_inplace<false, 1>(st, F, p, strm) : launch_inplace<false, 2>(st, F, p, strm);
   }
   // staged kernels keep a fixed 128-column layout: larger blocks cannot launch
@@ -1198,8 +1221,8 @@ extern "C" lbx_status lbx_state_tune(lbx_state* st, int trials, int* staging, in
     st->staging = best_s;
     st->block = best_b;
   }
-  if (staging) *staging = (st->ops.reg || st->inplace) ? LBX_STAGE_AUTO : st->staging;
-  if (block) *block = (st->ops.reg || st->inplace) ? 128 : st->block;
+  if (staging) *staging = st->ops.reg ? LBX_STAGE_AUTO : st->staging;
+  if (block) *block = st->ops.reg ? 128 : st->block;
   if (ms_per_step) *ms_per_step = best;
   return LBX_OK;
 }

@@ -122,3 +122,25 @@ def test_inplace_graph_replay_and_checkpoint(tmp_path):
     a.step(2)
     c.step(2)
     assert torch.equal(a.moments(), c.moments())
+
+
+@pytest.mark.parametrize("prec", [lbx.FP32_SHIFT, lbx.FP16_SCALED, lbx.FP64])
+def test_inplace_bulk_and_thread_staging_equal_two_buffers(prec):
+    """MHD D3Q19 at 24^3 (nx % 8 == 0): in-place kinds with bulk row copies (blocks of 32, 64
+    and 128) and with per-thread copies equal the two-buffer pull bitwise."""
+    case = syn.MhdCase(n=24)
+    sys_ = lbx.System(lbx.MHD_J_TRACK, params=(case.gamma, case.eta), Q0=case.reference_state())
+    Q = syn.mhd_fields(case)
+
+    def make(streaming):
+        return lbx.Scheme(sys_, lbx.D3Q19, (24, 24, 24), lbx.ACOUSTIC, case.f, tau_R=case.tau_R, g_tau=case.g_tau,
+                          precision=prec, streaming=streaming)
+    ref = lbx.State(make(lbx.STREAM_TWO_BUFFERS), Q)
+    ref.step(6)
+    want = ref.get_populations()
+    for staging, block in ((lbx.STAGE_BULK, 32), (lbx.STAGE_BULK, 64), (lbx.STAGE_BULK, 128), (lbx.STAGE_THREAD, 128)):
+        st = lbx.State(make(lbx.STREAM_IN_PLACE), Q)
+        st.set_staging(staging)
+        st.set_block(block)
+        st.step(6)
+        assert torch.equal(st.get_populations(), want), (staging, block)
