@@ -260,7 +260,7 @@ def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=Fals
            "bytes_per_launch": nbytes, "finite": st.check_finite(), "graph": graph,
            "launch": launch_desc(L, launch) if not inplace else
            {"kernel": "in place, kinds 1 and 2 alternating (k_step_bulk_inplace for staged systems with "
-                      "nx % 8 == 0, else k_step_inplace)", "block": 64},
+                      "nx % 8 == 0, else k_step_inplace)", "block": launch["block"]},
            "population_buffers": 1 if inplace else 2}
     return out, st
 
