@@ -63,7 +63,7 @@ def tau_vector(system, dt, tau_cons=None, tau_R=None, g_tau=None):
 
 class Scheme:
     def __init__(self, system, lattice: Lattice, shape, dx, dt, tau, mms=None,
-                 shifted=False, Q0=None, source_theta=0.0, flux_theta=0.0):
+                 shifted=False, Q0=None, source_theta=0.0, flux_theta=0.0, origin=None):
         self.sys = system
         self.lat = lattice
         self.shape = tuple(shape)
@@ -78,8 +78,10 @@ class Scheme:
         self.source_theta = float(source_theta)
         self.flux_theta = float(flux_theta)
         self.Q0 = None if Q0 is None else torch.as_tensor(Q0, dtype=F64)
-        # node coordinates (x, y[, z]), x fastest, for prescribed coefficient fields
-        axes = [torch.arange(n, dtype=F64) * self.dx for n in self.shape]
+        # node coordinates (x, y[, z]), x fastest, for prescribed coefficient fields; `origin`
+        # (grid order, as shape) offsets the node indices of a slab of a larger domain
+        org = origin if origin is not None else (0,) * len(self.shape)
+        axes = [(torch.arange(n, dtype=F64) + o) * self.dx for n, o in zip(self.shape, org)]
         self.xx = tuple(m.contiguous() for m in reversed(torch.meshgrid(*axes, indexing="ij")))
         if shifted:
             q0 = self.Q0.reshape((system.K,) + (1,) * len(self.shape))
