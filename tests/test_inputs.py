@@ -87,3 +87,36 @@ def test_analytic_trackers_equal_forward_mode_derivatives(which):
         xs = syn.coords((8, 8, 8))
     t = torch.full_like(xs[0], 0.3)
     torch.testing.assert_close(tab.augmented(xs, t), exact_augmented(sysm, tab.exact, xs, t), rtol=0, atol=1e-13)
+
+
+def test_hcnsf_table_equals_the_papers_expanded_fields():
+    """Supplement, HCNSF MMS, compiler-expanded fields Q_0 .. Q_4 (rho0 = c_s = 1): the mode
+    table built from the physical form (U0 = Ma sqrt(gamma), p0 = rho0 c_s^2, linear response
+    gamma c_s^2 drho) reproduces the printed expansions, including the printed constants
+    0.591607978309962, 121/40, 161/200 and 0.0236643191323985 / 0.118321595661992."""
+    xs = syn.coords((6, 6, 6))
+    xs = tuple(x + 0.013 * (d + 1) for d, x in enumerate(xs))          # off the grid nodes
+    t = torch.full_like(xs[0], 0.73)
+    s = [torch.sin(TWO_PI * x) for x in xs]
+    c = [torch.cos(TWO_PI * x) for x in xs]
+    st, ct = torch.sin(t), torch.cos(t)
+    U = 0.591607978309962
+    Q = syn.HcnsfPaperCase(n=6).table().exact(*xs, t)
+    rho = s[0] * s[2] * ct * c[1] / 5 + 1
+    torch.testing.assert_close(Q[0], rho, rtol=0, atol=1e-15)
+    torch.testing.assert_close(Q[1], (st * s[1] * s[2] * c[0] / 5 + U) * rho, rtol=0, atol=1e-14)
+    torch.testing.assert_close(Q[2], (st * s[0] * s[2] * c[1] / 5 + U) * rho, rtol=0, atol=1e-14)
+    torch.testing.assert_close(Q[3], (st * s[0] * s[1] * c[2] / 5 + U) * rho, rtol=0, atol=1e-14)
+    a, b = 0.0236643191323985, 0.118321595661992
+    E = (st ** 2 * s[0] ** 3 * s[1] ** 2 * s[2] * ct * c[1] * c[2] ** 2 / 250
+         + st ** 2 * s[0] ** 3 * s[2] ** 3 * ct * c[1] ** 3 / 250
+         + st ** 2 * s[0] ** 2 * s[1] ** 2 * c[2] ** 2 / 50
+         + st ** 2 * s[0] ** 2 * s[2] ** 2 * c[1] ** 2 / 50
+         + st ** 2 * s[0] * s[1] ** 2 * s[2] ** 3 * ct * c[0] ** 2 * c[1] / 250
+         + st ** 2 * s[1] ** 2 * s[2] ** 2 * c[0] ** 2 / 50
+         + a * st * s[0] ** 2 * s[1] * s[2] * ct * c[1] * c[2]
+         + a * st * s[0] ** 2 * s[2] ** 2 * ct * c[1] ** 2
+         + a * st * s[0] * s[1] * s[2] ** 2 * ct * c[0] * c[1]
+         + b * st * s[0] * s[1] * c[2] + b * st * s[0] * s[2] * c[1] + b * st * s[1] * s[2] * c[0]
+         + st * s[1] * c[0] * c[2] / 2 + 161 * s[0] * s[2] * ct * c[1] / 200 + 121 / 40)
+    torch.testing.assert_close(Q[4], E, rtol=0, atol=1e-13)
