@@ -56,13 +56,13 @@ def table_system(table, params, Q0):
 
 def forced_scheme(table, system, lattice, extent, scaling, f, precision=L.FP64, tau_lb=0.0,
                   tau_R=0.0, g_tau=0.0, conserved_only=False, prescribed=L.PRESCRIBED_NONE,
-                  prescribed_params=()):
+                  prescribed_params=(), streaming=L.STREAM_TWO_BUFFERS):
     """A scheme carrying the FOURIER forcing of `table` (.lbx_modes(), .mean): every
     component, or the conserved ones with conserved_only."""
     return L.Scheme(system, lattice, extent, scaling, f, tau_lb=tau_lb, tau_R=tau_R, g_tau=g_tau,
                     precision=precision, mms=L.MMS_FOURIER, mms_modes=table.lbx_modes(),
                     mms_mean=list(table.mean), mms_conserved_only=conserved_only,
-                    prescribed=prescribed, prescribed_params=prescribed_params)
+                    prescribed=prescribed, prescribed_params=prescribed_params, streaming=streaming)
 
 
 # ------------------------------------------------------------- the paper's own cascades
@@ -113,7 +113,7 @@ def hcnsf_scheme(case, precision=L.FP32_SHIFT, forced=False, extent=None, stream
     if forced:
         return forced_scheme(case.table(), hcnsf_system(case), L.D3Q7, ext, L.ACOUSTIC, case.f,
                              precision=precision, tau_R=case.tau_R, g_tau=case.g_tau,
-                             prescribed=kind, prescribed_params=pf)
+                             prescribed=kind, prescribed_params=pf, streaming=streaming)
     return L.Scheme(hcnsf_system(case), L.D3Q7, ext, L.ACOUSTIC, case.f, tau_R=case.tau_R,
                     g_tau=case.g_tau, precision=precision, prescribed=kind, prescribed_params=pf,
                     streaming=streaming)
