@@ -402,11 +402,16 @@ struct StepMode {
   static constexpr size_t smem_bytes = value == MODE_SMEM ? smem_per_thread * COLS : 0;
   // blocks per SM the launch bounds ask the register allocator to allow: 4 for
   // register-resident kernels (128 registers; the FP16 ones spill at 5), and for staged
-  // kernels what shared memory lets reside (228 KB per SM), at most 384 threads
+  // kernels what shared memory lets reside (228 KB per SM), at most `cap` threads
   static constexpr int smem_blocks = value == MODE_SMEM ? (int)(228 * 1024 / smem_bytes) : 0;
-  static constexpr int min_blocks =
-      value == MODE_REG ? 4
-                        : (smem_blocks < 1 ? 1 : (smem_blocks * COLS > 384 ? 384 / COLS : smem_blocks));
+  static constexpr int blocks_for(int cap) {
+    return value == MODE_REG ? 4 : (smem_blocks < 1 ? 1 : (smem_blocks * COLS > cap ? cap / COLS : smem_blocks));
+  }
+  static constexpr int min_blocks = blocks_for(384);
+  // the unforced two-buffer step with FP16 storage: its half-size columns leave room for 640
+  // threads (96 registers, no spills), more warps to cover the memory latency; the forced
+  // and in-place kernels need their registers and keep 384
+  static constexpr int min_blocks_step = blocks_for(sizeof(typename St::S) == 2 ? 640 : 384);
 };
 
 template <typename S>
@@ -1050,7 +1055,8 @@ __global__ void __launch_bounds__(COLS, BulkMode<Lat, SysT, St, COLS>::min_block
 // compiles the manufactured forcing of a mode table in (a separate instantiation, so the
 // kernels of unforced runs carry none of its code).
 template <class Lat, template <typename> class SysT, class St, int MODE, int COLS, bool FOURIER = false>
-__global__ void __launch_bounds__(COLS, StepMode<Lat, SysT, St, COLS>::min_blocks)
+__global__ void __launch_bounds__(COLS, FOURIER ? StepMode<Lat, SysT, St, COLS>::min_blocks
+                                                : StepMode<Lat, SysT, St, COLS>::min_blocks_step)
     k_step(const typename St::S* __restrict__ A, typename St::S* __restrict__ B, const KParams<typename St::C> p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
