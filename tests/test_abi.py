@@ -133,3 +133,22 @@ def test_hcnsf_declaration_and_scheme_checks():
     with pytest.raises(lbx.LbxError, match="HCNSF_3D only"):
         lbx.Scheme(e, lbx.D2Q5, (8, 8), lbx.ACOUSTIC, 0.05, tau_R=1.0, prescribed=lbx.PRESCRIBED_UNIFORM,
                    prescribed_params=(0.5, 0.0, 0.0, 0.0))
+
+
+def test_header_is_plain_c99(tmp_path):
+    """include/lbx.h declares a C ABI: it compiles as C99 with pedantic warnings as errors."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_lbx.c"
+    src.write_text('#include "lbx.h"\n'
+                   "int main(void) {\n"
+                   "  lbx_scheme_desc d = {0};\n"
+                   "  d.streaming = LBX_STREAM_IN_PLACE; d.prescribed = LBX_PRESCRIBED_ADVECTED;\n"
+                   "  return d.mms + d.streaming + d.prescribed - 3;\n"
+                   "}\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
