@@ -814,3 +814,43 @@ def test_prescribed_field_time_levels_reach_flux_and_source():
     calls.clear()
     sch.step(f, 3 * dt)
     assert calls == pytest.approx([3.25 * dt, 3.5 * dt])      # flux (equilibrium), then source
+
+
+TWO_PI = 2.0 * math.pi
+
+
+def test_hcnsf_forcing_vanishes_for_a_uniform_flow_moving_with_the_solid():
+    """Sec. 3, HCNSF with Sec. 4's S_MMS: for a uniform state moving with the solid
+    (u_s = u everywhere), under a porosity that varies in space and time, every term
+    vanishes: no gradients, so no viscous or heat flux for alpha to scale, and no drag.
+    For a solid moving otherwise the forcing is exactly minus the drag (momentum) and minus
+    the drag's work (energy)."""
+    from oracle.mms import mms_source
+    u = (0.3, -0.2, 0.1)
+
+    def fields(xx, t):
+        t = t if torch.is_tensor(t) else torch.full_like(xx[0], float(t))
+        a = 0.5 + 0.3 * torch.sin(TWO_PI * (xx[0] - 0.2 * t)) * torch.cos(TWO_PI * xx[1]) * torch.sin(TWO_PI * xx[2])
+        return [a] + [torch.full_like(xx[0], v) for v in u]
+
+    sysm = S.HomogenizedNsf3D(1.4, 0.03, 0.05, 0.1, 0.2, fields=fields)
+
+    def exact(x, y, z, t):
+        one = torch.ones_like(x)
+        rho, p = 1.1 * one, 0.9 * one
+        return torch.stack([rho, rho * u[0], rho * u[1], rho * u[2], p / 0.4 + 0.5 * rho * sum(v * v for v in u)])
+
+    xs = syn.coords((5, 4, 6))
+    Sm = mms_source(sysm, exact, xs, 0.37)
+    assert Sm.shape[0] == 14 and float(Sm.abs().max()) < 1e-13
+    # a solid moving otherwise: the forcing is minus the drag, S_m = (1 - alpha)/eta rho (u_s - u)
+    us = (0.1, 0.25, -0.05)
+    moving = S.HomogenizedNsf3D(1.4, 0.03, 0.05, 0.1, 0.2,
+                                fields=lambda xx, t: [fields(xx, t)[0]] + [torch.full_like(xx[0], v) for v in us])
+    Sm = mms_source(moving, exact, xs, 0.37)
+    a = fields(xs, 0.37)[0]
+    drag = [(1 - a) / 0.1 * 1.1 * (us[b] - u[b]) for b in range(3)]
+    for b in range(3):
+        torch.testing.assert_close(Sm[1 + b], -drag[b], rtol=1e-12, atol=1e-13)
+    torch.testing.assert_close(Sm[4], -sum(drag[b] * u[b] for b in range(3)), rtol=1e-12, atol=1e-13)
+    assert float(Sm[0].abs().max()) < 1e-14 and float(Sm[5:].abs().max()) < 1e-13
