@@ -209,3 +209,25 @@ def test_hcnsf_subchar_bound_dominates_oracle_eigenvalues():
     cf = case.prescribed(xs, 0.4)
     num = oracle.subchar.max_speed(osys, Q, n_dirs=48, nodes=list(range(0, N ** 3, 997)), cf=cf)
     assert num * (1 - 1e-9) <= got <= 2.0 * num, (got, num)
+
+
+@pytest.mark.parametrize("kind", ["none", "uniform"])
+def test_hcnsf_constant_fields_match_oracle(kind):
+    """The pure-fluid (alpha = 1) and uniform (alpha = 0.35, u_s = (0.1, -0.2, 0.05)) prescribed
+    kinds on the paper's forced flow, FP64 against the oracle with the same constant fields."""
+    N = 16
+    case = syn.HcnsfPaperCase(n=N)
+    shape = (N, N, N)
+    vals = [1.0, 0.0, 0.0, 0.0] if kind == "none" else [0.35, 0.1, -0.2, 0.05]
+    pk = lbx.PRESCRIBED_NONE if kind == "none" else lbx.PRESCRIBED_UNIFORM
+    tab = case.table()
+    sch = W.forced_scheme(tab, W.hcnsf_system(case), lbx.D3Q7, shape, lbx.ACOUSTIC, case.f, tau_R=case.tau_R,
+                          g_tau=case.g_tau, prescribed=pk, prescribed_params=tuple(vals) if pk else ())
+    Q = tab.augmented(syn.coords(shape), 0.0)
+    st = lbx.State(sch, Q)
+    st.step(8)
+    fields = lambda xx, t: [torch.full_like(xx[0], v) for v in vals]
+    _, och = _oracle(case, shape, fields, True)
+    Qo = och.moments(och.run(och.init(Q), 8))
+    err = H.rel_linf_per_field(st.moments(), Qo)
+    assert err[:5].max() <= 1e-12 and err[5:].max() <= 1e-10, err.tolist()
