@@ -854,3 +854,26 @@ def test_hcnsf_forcing_vanishes_for_a_uniform_flow_moving_with_the_solid():
         torch.testing.assert_close(Sm[1 + b], -drag[b], rtol=1e-12, atol=1e-13)
     torch.testing.assert_close(Sm[4], -sum(drag[b] * u[b] for b in range(3)), rtol=1e-12, atol=1e-13)
     assert float(Sm[0].abs().max()) < 1e-14 and float(Sm[5:].abs().max()) < 1e-13
+
+
+def test_hcnsf_oracle_converges_on_the_papers_flow():
+    """Sec. 4 on the paper's HCNSF flow (forced, double recipe) to t = 0.1 on D3Q7: the
+    oracle's conserved fields approach the exact solution at close to second order between
+    N = 8 and 16 (1.76-1.83 measured; the paper's EOCs over N = 32..256 are 1.78-1.96)."""
+    from oracle.mms import make_mms
+    errs = []
+    for N in (8, 16):
+        case = syn.HcnsfPaperCase(n=N)
+        sysm = S.HomogenizedNsf3D(case.gamma, case.mu, case.kappa, case.eta, case.g_tau * case.dt,
+                                  fields=case.prescribed)
+        xs = syn.coords((N, N, N))
+        tab = case.table()
+        sch = oracle.Scheme(sysm, oracle.LATTICES["D3Q7"], (N, N, N), case.dx, case.dt,
+                            oracle.tau_vector(sysm, case.dt, tau_R=case.tau_R, g_tau=case.g_tau),
+                            mms=make_mms(sysm, tab.exact, xs, dt=case.dt, chunk=16), source_theta=case.theta)
+        n = round(0.1 / case.dt)
+        Q = sch.moments(sch.run(sch.init(tab.augmented(xs, 0.0)), n))
+        l2, _ = oracle.rel_norms(Q, tab.augmented(xs, n * case.dt))
+        errs.append(l2[:5])
+    orders = [math.log2(float(a) / float(b)) for a, b in zip(*errs)]
+    assert all(1.6 < o < 2.3 for o in orders), orders
