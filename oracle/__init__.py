@@ -3,8 +3,8 @@
 This package re-implements the paper's scheme step by step (stencils, exact-flux
 equilibrium Eq. feq, moments Eq. moments, BGK collide-and-stream Eq. lbe_update,
 reference/equilibrium shift Sec. 2.4.3, manufactured forcing Sec. 4, the
-sub-characteristic check Sec. 2.3.2) in float64 PyTorch CPU code written for reading,
-not speed.  It shares no code with the CUDA library and never imports it.
+sub-characteristic check Sec. 2.3.2, systems with prescribed coefficient fields such as the
+homogenized NSF of Sec. 3) in float64 PyTorch CPU code written for reading, not speed.  It shares no code with the CUDA library and never imports it.
 
 Only the tests, the smoke check and the timed CPU baseline of the benchmark may use it;
 the library never routes any computation through it.
