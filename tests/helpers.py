@@ -50,3 +50,22 @@ def fluct_rel_l2(a, b, Q0):
     e = (a - b).reshape(K, -1)
     r = (b - q0).reshape(K, -1)
     return torch.sqrt((e * e).sum(1)) / torch.sqrt((r * r).sum(1)).clamp_min(1e-300)
+
+
+def patch_moments(make_scheme, Q, centers, steps, r):
+    """The oracle's moments after `steps` steps at each of `centers` (grid-order index
+    tuples), each computed on a periodic patch of side 2 r + 1 cut from the full fields Q
+    [K, *grid] around the node.  With r > steps the centre's domain of dependence lies inside
+    the patch, so its value is the full domain's.  make_scheme(shape, origin) builds the
+    oracle scheme of a patch whose first node has grid index `origin`."""
+    out = []
+    for c in centers:
+        sub = Q
+        for d, cd in enumerate(c):
+            n = Q.shape[1 + d]
+            idx = torch.tensor([(cd - r + j) % n for j in range(2 * r + 1)])
+            sub = sub.index_select(1 + d, idx)
+        sch = make_scheme(tuple(sub.shape[1:]), tuple(cd - r for cd in c))
+        Qp = sch.moments(sch.run(sch.init(sub), steps))
+        out.append(Qp[(slice(None),) + (r,) * len(c)])
+    return torch.stack(out, dim=1)                 # [K, n_centres]
