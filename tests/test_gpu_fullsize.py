@@ -29,15 +29,22 @@ def _gpu_nodes(st, centers):
     return torch.stack([Qg[(slice(None),) + tuple(c)] for c in centers], dim=1)
 
 
-def _check(got, want, Q0, prec, comps):
+def _check(got, want, Q0, prec, comps, n_cons):
+    """FP64: max |diff| / max |value| per field; FP32: relative to the fluctuation about Q0.
+    Tracker populations carry V / tau_grad in their equilibria (tau_grad = g_tau dt is small
+    at these resolutions), which amplifies the rounding of the tracker fields by
+    (dt/dx) / (c_s^2 tau_grad) ~ 10^2: they get a 10^3 looser bound than the conserved ones."""
     got, want = got[comps], want[comps]
     if prec == lbx.FP64:
         err = (got - want).abs().amax(1) / want.abs().amax(1)
-        assert float(err.max()) <= 1e-12, err.tolist()
+        bound = 1e-12
     else:
         q0 = torch.tensor(Q0, dtype=F64)[comps].unsqueeze(1)
         err = (got - want).abs().amax(1) / (want - q0).abs().amax(1)
-        assert float(err.max()) <= 1e-4, err.tolist()
+        bound = 1e-4
+    assert float(err[:n_cons].max()) <= bound, err.tolist()
+    if len(comps) > n_cons:
+        assert float(err[n_cons:].max()) <= 1e3 * bound, err.tolist()
 
 
 @pytest.mark.parametrize("prec", [lbx.FP32_SHIFT, lbx.FP64])
@@ -53,7 +60,7 @@ def test_nsf_d2q9_1024_sampled_nodes(prec):
     ref = H.oracle_nsf(case)
     make = lambda shape, origin: oracle.Scheme(ref.sys, ref.lat, shape, case.dx, case.dt, ref.tau)
     _check(_gpu_nodes(st, centers), H.patch_moments(make, Q, centers, steps, steps + 1),
-           case.reference_state(), prec, list(range(10)))
+           case.reference_state(), prec, list(range(10)), 4)
 
 
 def test_mhd_d3q19_256_sampled_nodes():
@@ -68,7 +75,7 @@ def test_mhd_d3q19_256_sampled_nodes():
     ref = H.oracle_mhd(case)
     make = lambda shape, origin: oracle.Scheme(ref.sys, ref.lat, shape, case.dx, case.dt, ref.tau)
     _check(_gpu_nodes(st, centers), H.patch_moments(make, Q, centers, steps, steps + 1),
-           case.reference_state(), lbx.FP32_SHIFT, list(range(11)))
+           case.reference_state(), lbx.FP32_SHIFT, list(range(11)), 8)
 
 
 def test_hcnsf_d3q7_256_sampled_nodes():
@@ -80,10 +87,11 @@ def test_hcnsf_d3q7_256_sampled_nodes():
     st = lbx.State(W.hcnsf_scheme(case, lbx.FP32_SHIFT), Q.cuda())
     st.tune()
     st.step(steps)
-    centers = [(0, 0, 0), (n - 1, n // 3, 5), (n // 2, n - 1, n // 4), (3, 7, n - 1), (n // 2, n // 2, n // 2)]
+    # edges and corners, at coordinates where the flow's fluctuations are not small
+    centers = [(37, 101, n - 5), (n - 1, 3, 77), (0, 130, n - 1), (129, 64, 31), (n - 1, n - 1, 0), (37, 101, 211)]
     sysm = S.HomogenizedNsf3D(case.gamma, case.mu, case.kappa, case.eta, case.g_tau * case.dt, fields=case.prescribed)
     tau = oracle.tau_vector(sysm, case.dt, tau_R=case.tau_R, g_tau=case.g_tau)
     make = lambda shape, origin: oracle.Scheme(sysm, oracle.LATTICES["D3Q7"], shape, case.dx, case.dt, tau,
                                                source_theta=case.theta, origin=origin)
     _check(_gpu_nodes(st, centers), H.patch_moments(make, Q, centers, steps, steps + 1),
-           case.reference_state(), lbx.FP32_SHIFT, list(range(5)))
+           case.reference_state(), lbx.FP32_SHIFT, list(range(5)), 5)
