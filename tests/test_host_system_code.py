@@ -1,0 +1,133 @@
+"""The CUDA system code on the host (no GPU): systems.cuh's delta-form flux and source are
+__host__ __device__, so a small host-only build evaluates them on random states and the
+oracle's direct forms check them, Phi(Q0 + dQ) - Phi(Q0) and S(Q0 + dQ), for the 3D
+homogenized NSF (with prescribed alpha and u_s, flux and source at different values), the
+12-component NSF and the 18-component MHD."""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import systems as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2607_05668_b300", "csrc")
+F64 = torch.float64
+
+SRC = r'''
+#include "systems.cuh"
+using namespace lbx;
+template <class Sys, int NCF>
+static void run(const double* p, const double* Q0, const double* dQ, const double* cf, const double* cs,
+                double* dPhi, double* Sr) {
+  double P[Sys::K][Sys::D], Sv[Sys::K];
+  if constexpr (NCF > 0) {
+    double a[NCF], b[NCF];
+    for (int i = 0; i < NCF; ++i) { a[i] = cf[i]; b[i] = cs[i]; }
+    Sys::eval(p, Q0, dQ, P, Sv, a, b);
+  } else {
+    Sys::eval(p, Q0, dQ, P, Sv);
+  }
+  for (int k = 0; k < Sys::K; ++k) {
+    Sr[k] = Sv[k];
+    for (int d = 0; d < Sys::D; ++d) dPhi[k * Sys::D + d] = P[k][d];
+  }
+}
+extern "C" void eval_hcnsf(const double* p, const double* Q0, const double* dQ, const double* cf, const double* cs,
+                           double* dPhi, double* Sr) { run<SysHCNSF<double>, 4>(p, Q0, dQ, cf, cs, dPhi, Sr); }
+extern "C" void eval_nsf12(const double* p, const double* Q0, const double* dQ, double* dPhi, double* Sr) {
+  run<SysNSF12<double>, 0>(p, Q0, dQ, nullptr, nullptr, dPhi, Sr);
+}
+extern "C" void eval_mhd18(const double* p, const double* Q0, const double* dQ, double* dPhi, double* Sr) {
+  run<SysMHD18<double>, 0>(p, Q0, dQ, nullptr, nullptr, dPhi, Sr);
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def host_lib(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or (os.path.exists("/usr/local/cuda/bin/nvcc") and "/usr/local/cuda/bin/nvcc")
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    d = tmp_path_factory.mktemp("hostsys")
+    src, lib = d / "host_systems.cu", d / "libhostsys.so"
+    src.write_text(SRC)
+    r = subprocess.run([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-O1", "-shared", "-Xcompiler", "-fPIC",
+                        "-I", CSRC, str(src), "-o", str(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return C.CDLL(str(lib))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def test_hcnsf_host_eval_matches_oracle(host_lib):
+    gam, mu, kap, eta, tg = 1.4, 0.03, 0.05, 0.1, 0.3
+    g = np.random.default_rng(5)
+    Q0 = np.array([1.1, 0.4, -0.2, 0.3, 3.2] + [0.0] * 9)
+    ke0 = 0.5 * (Q0[1:4] ** 2).sum() / Q0[0]
+    p0 = (gam - 1) * (Q0[4] - ke0)
+    prm = np.zeros(24)
+    prm[:11] = [gam - 1, mu, kap, 1 / eta, 1 / tg, *(Q0[1:4] / Q0[0]), Q0[4] + p0, p0 / Q0[0], gam]
+    osys = S.HomogenizedNsf3D(gam, mu, kap, eta, tg, fields=None)
+    for trial in range(20):
+        dQ = g.uniform(-0.1, 0.1, 14)
+        cf = np.array([g.uniform(0, 1), *g.uniform(-0.3, 0.3, 3)])
+        cs = np.array([g.uniform(0, 1), *g.uniform(-0.3, 0.3, 3)])
+        dPhi, Sr = np.zeros(42), np.zeros(14)
+        host_lib.eval_hcnsf(_ptr(prm), _ptr(Q0), _ptr(dQ), _ptr(cf), _ptr(cs), _ptr(dPhi), _ptr(Sr))
+        Q = torch.tensor(Q0 + dQ, dtype=F64)
+        cft = [torch.tensor(v, dtype=F64) for v in cf]
+        cst = [torch.tensor(v, dtype=F64) for v in cs]
+        want = (osys.flux(Q, cft) - osys.flux(torch.tensor(Q0, dtype=F64), cft)).numpy().reshape(-1)
+        np.testing.assert_allclose(dPhi, want, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(Sr, osys.source(Q, cst).numpy(), rtol=1e-12, atol=1e-12)
+
+
+def _cascade_prm(family, Q0, P, tg):
+    """The background-dependent parameters of the cascade families (uniform background:
+    zero gradients), laid out as systems.cuh documents them."""
+    prm = np.zeros(24)
+    rho, m = Q0[0], Q0[1:3]
+    u = m / rho
+    if family == "nsf12":
+        g, R, mu, K = P
+        p0 = (g - 1) * (Q0[3] - 0.5 * (m * u).sum())
+        prm[:19] = [g - 1, R, mu, K, 1 / tg, u[0], u[1], Q0[3] + p0, p0 / (rho * R)] + [0.0] * 9 + [g]
+    else:
+        g, mu, K, eta = P
+        B = Q0[4:6]
+        b2 = (B * B).sum()
+        p0 = (g - 1) * (Q0[3] - 0.5 * (m * u).sum() - 0.5 * b2)
+        prm[:20] = [g - 1, mu, K, eta, 1 / tg, u[0], u[1], Q0[3] + p0 + 0.5 * b2, (u * B).sum(), p0 / rho] + [0.0] * 9 + [g]
+    return prm
+
+
+@pytest.mark.parametrize("family", ["nsf12", "mhd18"])
+def test_cascade_host_eval_matches_oracle(host_lib, family):
+    g = np.random.default_rng(7)
+    tg = 0.37
+    if family == "nsf12":
+        P = (1.4, 0.8, 0.03, 0.05)
+        Q0 = np.array([1.05, 0.3, -0.2, 2.6] + [0.0] * 8)
+        osys = S.NsfConservedGradients(*P, tau_grad=tg)
+        fn, K = host_lib.eval_nsf12, 12
+    else:
+        P = (1.4, 0.03, 0.05, 0.07)
+        Q0 = np.array([1.05, 0.3, -0.2, 3.4, 0.4, -0.3] + [0.0] * 12)
+        osys = S.MhdPowell2D(*P, tau_grad=tg)
+        fn, K = host_lib.eval_mhd18, 18
+    prm = _cascade_prm(family, Q0, P, tg)
+    for trial in range(20):
+        dQ = g.uniform(-0.1, 0.1, K)
+        dPhi, Sr = np.zeros(2 * K), np.zeros(K)
+        fn(_ptr(prm), _ptr(Q0), _ptr(dQ), _ptr(dPhi), _ptr(Sr))
+        Q = torch.tensor(Q0 + dQ, dtype=F64)
+        want = (osys.flux(Q) - osys.flux(torch.tensor(Q0, dtype=F64))).numpy().reshape(-1)
+        np.testing.assert_allclose(dPhi, want, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(Sr, osys.source(Q).numpy(), rtol=1e-12, atol=1e-12)
