@@ -2,7 +2,8 @@
 __host__ __device__, so a small host-only build evaluates them on random states and the
 oracle's direct forms check them, Phi(Q0 + dQ) - Phi(Q0) and S(Q0 + dQ), for the 3D
 homogenized NSF (with prescribed alpha and u_s, flux and source at different values), the
-12-component NSF and the 18-component MHD."""
+12-component NSF and the 18-component MHD, and the configurations' families (ADR cascade,
+NSF with primitive trackers, 3D MHD with a current tracker, Burgers, Euler, Maxwell TM)."""
 import ctypes as C
 import os
 import shutil
@@ -45,6 +46,16 @@ extern "C" void eval_nsf12(const double* p, const double* Q0, const double* dQ, 
 extern "C" void eval_mhd18(const double* p, const double* Q0, const double* dQ, double* dPhi, double* Sr) {
   run<SysMHD18<double>, 0>(p, Q0, dQ, nullptr, nullptr, dPhi, Sr);
 }
+#define PLAIN(name, Sys) \
+  extern "C" void eval_##name(const double* p, const double* Q0, const double* dQ, double* dPhi, double* Sr) { \
+    run<Sys<double>, 0>(p, Q0, dQ, nullptr, nullptr, dPhi, Sr); \
+  }
+PLAIN(adr, SysADR)
+PLAIN(nsf, SysNSF)
+PLAIN(mhd, SysMHD)
+PLAIN(burgers, SysBurgers)
+PLAIN(euler, SysEuler)
+PLAIN(maxwell, SysMaxwell)
 '''
 
 
@@ -126,6 +137,59 @@ def test_cascade_host_eval_matches_oracle(host_lib, family):
     for trial in range(20):
         dQ = g.uniform(-0.1, 0.1, K)
         dPhi, Sr = np.zeros(2 * K), np.zeros(K)
+        fn(_ptr(prm), _ptr(Q0), _ptr(dQ), _ptr(dPhi), _ptr(Sr))
+        Q = torch.tensor(Q0 + dQ, dtype=F64)
+        want = (osys.flux(Q) - osys.flux(torch.tensor(Q0, dtype=F64))).numpy().reshape(-1)
+        np.testing.assert_allclose(dPhi, want, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(Sr, osys.source(Q).numpy(), rtol=1e-12, atol=1e-12)
+
+
+def _plain_case(name, g):
+    """(oracle system, Q0, parameter array as systems.cuh lays it out, K, D) for a uniform
+    background with zero trackers."""
+    prm = np.zeros(24)
+    tg = 0.29
+    if name == "adr":
+        a, nu, R = (0.4, -0.25), 0.05, 0.7
+        prm[:5] = [a[0], a[1], nu, R, 1 / tg]
+        return S.AdrCascade(a, nu, tg, R=R), np.array([0.6, 0.0, 0.0]), prm, 3, 2
+    if name == "nsf":
+        gam, R, mu, K = 1.4, 0.8, 0.03, 0.05
+        Q0 = np.array([1.05, 0.3, -0.2, 2.6] + [0.0] * 6)
+        u = Q0[1:3] / Q0[0]
+        p0 = (gam - 1) * (Q0[3] - 0.5 * (Q0[1:3] * u).sum())
+        prm[:14] = [gam - 1, R, mu, K, 1 / tg, u[0], u[1], Q0[3] + p0, p0 / Q0[0], 0, 0, 0, gam, 1 / R]  # 8: R T0
+        return S.NsfPrimitive(gam, R, mu, K, tg), Q0, prm, 10, 2
+    if name == "mhd":
+        gam, eta = 1.4, 0.02
+        Q0 = np.array([1.05, 0.3, -0.2, 0.1, 0.4, -0.3, 0.2, 3.4, 0.0, 0.0, 0.0])
+        u, B = Q0[1:4] / Q0[0], Q0[4:7]
+        b2 = (B * B).sum()
+        p0 = (gam - 1) * (Q0[7] - 0.5 * (Q0[1:4] * u).sum() - 0.5 * b2)
+        prm[:9] = [gam - 1, eta, 1 / tg, u[0], u[1], u[2], Q0[7] + p0 + 0.5 * b2, (u * B).sum(), gam]
+        return S.MhdCurrent(gam, eta, tg), Q0, prm, 11, 3
+    if name == "burgers":
+        return S.Burgers(), np.array([0.3]), prm, 1, 2
+    if name == "euler":
+        gam = 1.4
+        Q0 = np.array([1.05, 0.3, -0.2, 2.6])
+        u = Q0[1:3] / Q0[0]
+        p0 = (gam - 1) * (Q0[3] - 0.5 * (Q0[1:3] * u).sum())
+        prm[:5] = [gam - 1, u[0], u[1], Q0[3] + p0, gam]
+        return S.Euler(gam), Q0, prm, 4, 2
+    c = 1.3
+    prm[0] = c
+    return S.MaxwellTM(c), np.array([0.2, -0.1, 0.3]), prm, 3, 2
+
+
+@pytest.mark.parametrize("name", ["adr", "nsf", "mhd", "burgers", "euler", "maxwell"])
+def test_configuration_families_host_eval_matches_oracle(host_lib, name):
+    g = np.random.default_rng(11)
+    osys, Q0, prm, K, D = _plain_case(name, g)
+    fn = getattr(host_lib, f"eval_{name}")
+    for trial in range(20):
+        dQ = g.uniform(-0.1, 0.1, K)
+        dPhi, Sr = np.zeros(D * K), np.zeros(K)
         fn(_ptr(prm), _ptr(Q0), _ptr(dQ), _ptr(dPhi), _ptr(Sr))
         Q = torch.tensor(Q0 + dQ, dtype=F64)
         want = (osys.flux(Q) - osys.flux(torch.tensor(Q0, dtype=F64))).numpy().reshape(-1)
