@@ -50,6 +50,21 @@ extern "C" void eval_mhd18(const double* p, const double* Q0, const double* dQ, 
   extern "C" void eval_##name(const double* p, const double* Q0, const double* dQ, double* dPhi, double* Sr) { \
     run<Sys<double>, 0>(p, Q0, dQ, nullptr, nullptr, dPhi, Sr); \
   }
+// augment: the exact augmented state from primitives V[NPRIM] and gradients G[NPRIM][3]
+template <class Sys>
+static void aug(const double* p, const double* V, const double* G, double* Q) {
+  double v[Sys::NPRIM], g[Sys::NPRIM][3], q[Sys::K];
+  for (int i = 0; i < Sys::NPRIM; ++i) {
+    v[i] = V[i];
+    for (int b = 0; b < 3; ++b) g[i][b] = G[3 * i + b];
+  }
+  Sys::augment(p, v, g, q);
+  for (int k = 0; k < Sys::K; ++k) Q[k] = q[k];
+}
+extern "C" void aug_hcnsf(const double* p, const double* V, const double* G, double* Q) { aug<SysHCNSF<double>>(p, V, G, Q); }
+extern "C" void aug_nsf12(const double* p, const double* V, const double* G, double* Q) { aug<SysNSF12<double>>(p, V, G, Q); }
+extern "C" void aug_mhd18(const double* p, const double* V, const double* G, double* Q) { aug<SysMHD18<double>>(p, V, G, Q); }
+extern "C" void aug_nsf(const double* p, const double* V, const double* G, double* Q) { aug<SysNSF<double>>(p, V, G, Q); }
 PLAIN(adr, SysADR)
 PLAIN(nsf, SysNSF)
 PLAIN(mhd, SysMHD)
@@ -195,3 +210,34 @@ def test_configuration_families_host_eval_matches_oracle(host_lib, name):
         want = (osys.flux(Q) - osys.flux(torch.tensor(Q0, dtype=F64))).numpy().reshape(-1)
         np.testing.assert_allclose(dPhi, want, rtol=1e-12, atol=1e-12)
         np.testing.assert_allclose(Sr, osys.source(Q).numpy(), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("family", ["hcnsf", "nsf12", "mhd18", "nsf"])
+def test_host_augment_matches_the_mode_tables(host_lib, family):
+    """Sys::augment (the exact augmented state the manufactured forcing differentiates)
+    against synthetic.ModeTable.augmented at scattered points of the paper's flows."""
+    import synthetic as syn
+    if family == "hcnsf":
+        case = syn.HcnsfPaperCase(n=8)
+        tab, dim, prm = case.table(), 3, np.array([case.gamma - 1.0] + [0.0] * 23)
+    elif family == "mhd18":
+        case = syn.MhdPaper2DCase(n=8)
+        tab, dim, prm = case.table(), 2, np.array([case.gamma - 1.0] + [0.0] * 23)
+    else:
+        case = syn.NsfPaperCase(n=8)
+        tab, dim = case.table(family), 2
+        prm = np.array([case.gamma - 1.0, case.R] + [0.0] * 22)
+    g = np.random.default_rng(3)
+    pts = [tuple(torch.tensor([float(v)], dtype=F64) for v in g.uniform(0, 1, dim)) for _ in range(6)]
+    fn = getattr(host_lib, f"aug_{family}")
+    for xs in pts:
+        t = torch.tensor([0.61], dtype=F64)
+        V = np.array([float(v[0]) for v in tab.primitives(xs, t)])
+        G = np.zeros((len(V), 3))
+        for q in range(len(V)):
+            for b in range(dim):
+                G[q, b] = float(tab.gradient(xs, t, q, b)[0])
+        want = tab.augmented(xs, t)[:, 0].numpy()
+        got = np.zeros(len(want))
+        fn(_ptr(prm), _ptr(V), _ptr(G.reshape(-1).copy()), _ptr(got))
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
