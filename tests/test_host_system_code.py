@@ -65,6 +65,22 @@ extern "C" void aug_hcnsf(const double* p, const double* V, const double* G, dou
 extern "C" void aug_nsf12(const double* p, const double* V, const double* G, double* Q) { aug<SysNSF12<double>>(p, V, G, Q); }
 extern "C" void aug_mhd18(const double* p, const double* V, const double* G, double* Q) { aug<SysMHD18<double>>(p, V, G, Q); }
 extern "C" void aug_nsf(const double* p, const double* V, const double* G, double* Q) { aug<SysNSF<double>>(p, V, G, Q); }
+#include "lattices.cuh"
+// binary32 weights of each lattice (lattices.cuh, weight<Lat, float>) and their float sum
+template <class Lat>
+static int weights_f32(float* w, float* sum) {
+  float acc = 0.0f;
+  for (int i = 0; i < Lat::Q; ++i) {
+    w[i] = weight<Lat, float>(i);
+    acc += w[i];
+  }
+  *sum = acc;
+  return Lat::Q;
+}
+extern "C" int weights_f32_d2q5(float* w, float* s) { return weights_f32<LatD2Q5>(w, s); }
+extern "C" int weights_f32_d2q9(float* w, float* s) { return weights_f32<LatD2Q9>(w, s); }
+extern "C" int weights_f32_d3q7(float* w, float* s) { return weights_f32<LatD3Q7>(w, s); }
+extern "C" int weights_f32_d3q19(float* w, float* s) { return weights_f32<LatD3Q19>(w, s); }
 PLAIN(adr, SysADR)
 PLAIN(nsf, SysNSF)
 PLAIN(mhd, SysMHD)
@@ -241,3 +257,23 @@ def test_host_augment_matches_the_mode_tables(host_lib, family):
         got = np.zeros(len(want))
         fn(_ptr(prm), _ptr(V), _ptr(G.reshape(-1).copy()), _ptr(got))
         np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("lat", ["d2q5", "d2q9", "d3q7", "d3q19"])
+def test_binary32_weights_sum_to_exactly_one(host_lib, lat):
+    """The FP32 kernels' weights (moving weights on multiples of 2^-26, rest = 1 - their sum)
+    add up to exactly 1 as real numbers, so sum_i w_i X = X holds without a systematic bias
+    (only the per-operation rounding remains); each moving weight lies within 2^-27 of the
+    exact one and the rest weight within (q - 1) 2^-27.  Exact weights in the library's own
+    velocity order (lbx_lattice_velocities, a host call)."""
+    from fractions import Fraction as Fr
+    from paper_2607_05668_b300 import lbx
+    w = np.zeros(32, dtype=np.float32)
+    sm = np.zeros(1, dtype=np.float32)
+    q = getattr(host_lib, f"weights_f32_{lat}")(w.ctypes.data_as(C.POINTER(C.c_float)), sm.ctypes.data_as(C.POINTER(C.c_float)))
+    w = w[:q]
+    assert sum(Fr(float(x)) for x in w) == 1
+    _, wd = lbx.lattice_velocities(getattr(lbx, lat.upper()))
+    exact = [Fr(float(v)).limit_denominator(64) for v in wd]
+    assert all(abs(Fr(float(x)) - e) <= Fr(1, 2 ** 27) for x, e in zip(w[1:], exact[1:]))
+    assert abs(Fr(float(w[0])) - exact[0]) <= Fr(q - 1, 2 ** 27)          # the rest weight absorbs them
