@@ -81,6 +81,19 @@ extern "C" int weights_f32_d2q5(float* w, float* s) { return weights_f32<LatD2Q5
 extern "C" int weights_f32_d2q9(float* w, float* s) { return weights_f32<LatD2Q9>(w, s); }
 extern "C" int weights_f32_d3q7(float* w, float* s) { return weights_f32<LatD3Q7>(w, s); }
 extern "C" int weights_f32_d3q19(float* w, float* s) { return weights_f32<LatD3Q19>(w, s); }
+#define SPEED(name, Sys) \
+  extern "C" double speed_##name(const double* p, const double* Q0, const double* dQ) { \
+    return Sys<double>::max_speed(p, Q0, dQ); \
+  }
+SPEED(adr, SysADR)
+SPEED(nsf, SysNSF)
+SPEED(mhd, SysMHD)
+SPEED(burgers, SysBurgers)
+SPEED(euler, SysEuler)
+SPEED(maxwell, SysMaxwell)
+SPEED(nsf12, SysNSF12)
+SPEED(mhd18, SysMHD18)
+SPEED(hcnsf, SysHCNSF)
 PLAIN(adr, SysADR)
 PLAIN(nsf, SysNSF)
 PLAIN(mhd, SysMHD)
@@ -277,3 +290,45 @@ def test_binary32_weights_sum_to_exactly_one(host_lib, lat):
     exact = [Fr(float(v)).limit_denominator(64) for v in wd]
     assert all(abs(Fr(float(x)) - e) <= Fr(1, 2 ** 27) for x, e in zip(w[1:], exact[1:]))
     assert abs(Fr(float(w[0])) - exact[0]) <= Fr(q - 1, 2 ** 27)          # the rest weight absorbs them
+
+
+def _hcnsf_case():
+    gam, mu, kap, eta, tg = 1.4, 0.03, 0.05, 0.1, 0.3
+    Q0 = np.array([1.1, 0.4, -0.2, 0.3, 3.2] + [0.0] * 9)
+    p0 = (gam - 1) * (Q0[4] - 0.5 * (Q0[1:4] ** 2).sum() / Q0[0])
+    prm = np.zeros(24)
+    prm[:11] = [gam - 1, mu, kap, 1 / eta, 1 / tg, *(Q0[1:4] / Q0[0]), Q0[4] + p0, p0 / Q0[0], gam]
+    return S.HomogenizedNsf3D(gam, mu, kap, eta, tg, fields=None), Q0, prm, 14, 3
+
+
+@pytest.mark.parametrize("name", ["adr", "nsf", "mhd", "burgers", "euler", "maxwell", "nsf12", "mhd18", "hcnsf"])
+def test_host_speed_bounds_dominate_the_oracle_eigenvalues(host_lib, name):
+    """Sec. 2.3.2: each family's closed-form max_speed bounds the spectral radius of the
+    directional flux Jacobian (the oracle's numeric eigenvalues over 48 directions) at random
+    states, and is no more than twice it (HCNSF: the bound takes alpha = 1, the oracle a
+    random alpha <= 1)."""
+    from oracle import subchar
+    g = np.random.default_rng(21)
+    if name in ("nsf12", "mhd18"):
+        tg = 0.37
+        if name == "nsf12":
+            P, Q0 = (1.4, 0.8, 0.03, 0.05), np.array([1.05, 0.3, -0.2, 2.6] + [0.0] * 8)
+            osys = S.NsfConservedGradients(*P, tau_grad=tg)
+        else:
+            P, Q0 = (1.4, 0.03, 0.05, 0.07), np.array([1.05, 0.3, -0.2, 3.4, 0.4, -0.3] + [0.0] * 12)
+            osys = S.MhdPowell2D(*P, tau_grad=tg)
+        prm, K = _cascade_prm(name, Q0, P, tg), len(Q0)
+    elif name == "hcnsf":
+        osys, Q0, prm, K, _ = _hcnsf_case()
+    else:
+        osys, Q0, prm, K, _ = _plain_case(name, g)
+    fn = getattr(host_lib, f"speed_{name}")
+    fn.restype = C.c_double
+    dirs = subchar.directions(osys.D, 48)
+    for trial in range(8):
+        dQ = g.uniform(-0.1, 0.1, K)
+        bound = fn(_ptr(prm), _ptr(Q0), _ptr(dQ))
+        q = torch.tensor(Q0 + dQ, dtype=F64)
+        cf = None if name != "hcnsf" else [torch.tensor(v, dtype=F64) for v in (g.uniform(0, 1), 0.1, 0.0, -0.1)]
+        num = subchar.node_max_speed(osys, q, dirs, cf)
+        assert num * (1 - 1e-9) <= bound <= 2.0 * num + 1e-12, (bound, num)
