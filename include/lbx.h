@@ -162,7 +162,8 @@ typedef enum { LBX_PRESCRIBED_NONE = 0, LBX_PRESCRIBED_UNIFORM = 1, LBX_PRESCRIB
  *                populations are bitwise those of TWO_BUFFERS.  After an odd number the
  *                layout is the pair's intermediate one: every call that reads or writes the
  *                populations (moments, populations, norms, sums, finite and sub-characteristic
- *                checks, save, load) fails with LBX_ERR_STATE until one more step is taken.
+ *                checks, save) fails with LBX_ERR_STATE until one more step is taken; lbx_load
+ *                restores a standard layout.
  *                Staged systems use bulk row copies where the staging resolves to them
  *                (lbx_state_set_staging, blocks of lbx_state_set_block), else per-thread
  *                copies in 128-thread blocks; no tuning, batches or adjoint. */
@@ -265,10 +266,11 @@ size_t lbx_state_buffer_bytes(const lbx_scheme* sch);
  * the first time this (n, buffer parity) occurs and replayed afterwards. */
 lbx_status lbx_step(lbx_state* st, int64_t n);
 /* Threads per block (32, 64 or 128; default 128) of the step kernels that stage a node's
- * populations in shared memory (K q s > 360 bytes: MHD on D3Q19, FP64 NSF); the other
- * kernels always use 128.  Only speed changes, never results. */
+ * populations in shared memory (K q s > 360 bytes or K > 12: MHD on D3Q19, FP64 NSF, the
+ * 18-component MHD, the homogenized NSF), in-place bulk steps included; the other kernels
+ * always use 128.  Only speed changes, never results. */
 lbx_status lbx_state_set_block(lbx_state* st, int block);
-/* How the staged step kernels (K q s > 360 bytes) bring a node's pulled populations into
+/* How the staged step kernels (K q s > 360 bytes or K > 12) bring a node's pulled populations into
  * shared memory; only speed changes, except LBX_STAGE_LANES2, whose moment sums add in
  * another order (results change by rounding only).
  *   LBX_STAGE_AUTO     bulk row copies when they apply, else per-thread copies (default)
