@@ -65,6 +65,11 @@ extern "C" void aug_hcnsf(const double* p, const double* V, const double* G, dou
 extern "C" void aug_nsf12(const double* p, const double* V, const double* G, double* Q) { aug<SysNSF12<double>>(p, V, G, Q); }
 extern "C" void aug_mhd18(const double* p, const double* V, const double* G, double* Q) { aug<SysMHD18<double>>(p, V, G, Q); }
 extern "C" void aug_nsf(const double* p, const double* V, const double* G, double* Q) { aug<SysNSF<double>>(p, V, G, Q); }
+extern "C" void aug_mhd(const double* p, const double* V, const double* G, double* Q) { aug<SysMHD<double>>(p, V, G, Q); }
+extern "C" void aug_euler(const double* p, const double* V, const double* G, double* Q) { aug<SysEuler<double>>(p, V, G, Q); }
+extern "C" void aug_adr(const double* p, const double* V, const double* G, double* Q) { aug<SysADR<double>>(p, V, G, Q); }
+extern "C" void aug_burgers(const double* p, const double* V, const double* G, double* Q) { aug<SysBurgers<double>>(p, V, G, Q); }
+extern "C" void aug_maxwell(const double* p, const double* V, const double* G, double* Q) { aug<SysMaxwell<double>>(p, V, G, Q); }
 #include "lattices.cuh"
 // binary32 weights of each lattice (lattices.cuh, weight<Lat, float>) and their float sum
 template <class Lat>
@@ -241,7 +246,7 @@ def test_configuration_families_host_eval_matches_oracle(host_lib, name):
         np.testing.assert_allclose(Sr, osys.source(Q).numpy(), rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("family", ["hcnsf", "nsf12", "mhd18", "nsf"])
+@pytest.mark.parametrize("family", ["hcnsf", "nsf12", "mhd18", "nsf", "mhd", "euler", "adr", "burgers", "maxwell"])
 def test_host_augment_matches_the_mode_tables(host_lib, family):
     """Sys::augment (the exact augmented state the manufactured forcing differentiates)
     against synthetic.ModeTable.augmented at scattered points of the paper's flows."""
@@ -252,6 +257,17 @@ def test_host_augment_matches_the_mode_tables(host_lib, family):
     elif family == "mhd18":
         case = syn.MhdPaper2DCase(n=8)
         tab, dim, prm = case.table(), 2, np.array([case.gamma - 1.0] + [0.0] * 23)
+    elif family == "mhd":
+        case = syn.MhdPaperCase(n=8)
+        tab, dim, prm = case.table(), 3, np.array([case.gamma - 1.0] + [0.0] * 23)
+    elif family == "euler":
+        tab, dim, prm = syn.euler_table(), 2, np.array([0.4] + [0.0] * 23)
+    elif family == "adr":
+        tab, dim, prm = syn.AdrPaperCase(n=8).table(), 2, np.zeros(24)
+    elif family == "burgers":
+        tab, dim, prm = syn.burgers_table(), 2, np.zeros(24)
+    elif family == "maxwell":
+        tab, dim, prm = syn.maxwell_table(), 2, np.zeros(24)
     else:
         case = syn.NsfPaperCase(n=8)
         tab, dim = case.table(family), 2
