@@ -500,7 +500,8 @@ def _oracle_scheme(workload, case, shape):
         lat = "D2Q5"
     tau = oracle.tau_vector(sysm, case.dt, tau_R=getattr(case, "tau_R", None),
                             tau_cons=getattr(case, "tau_u", None), g_tau=case.g_tau)
-    return oracle.Scheme(sysm, oracle.LATTICES[lat], shape, case.dx, case.dt, tau)
+    return oracle.Scheme(sysm, oracle.LATTICES[lat], shape, case.dx, case.dt, tau,
+                         source_theta=getattr(case, "theta", 0.0), flux_theta=getattr(case, "theta_flux", 0.0))
 
 
 def _oracle_sample(workload, case, rows):
