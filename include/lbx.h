@@ -297,6 +297,17 @@ typedef enum {
     LBX_STAGE_PIPE = 4
 } lbx_staging;
 lbx_status lbx_state_set_staging(lbx_state* st, int staging);
+/* Limit of the bounded wait of the bulk-staged step kernels (LBX_STAGE_BULK, and the
+ * in-place bulk steps) for their row copies, in nanoseconds of the GPU's global timer;
+ * the default is 1e9 (1 s).  When it runs out, a block raises the state's device error
+ * word, waits once more (at most 1 s) for the copies it issued to land, and leaves the
+ * populations of its nodes unwritten for that step; lbx_synchronize and
+ * lbx_check_finite then return LBX_ERR_TIMEOUT and clear the word.  ns = 0 makes every
+ * bulk-staged block give up before its first try while its copies complete normally,
+ * which exercises that path without any fault; the populations of such a step are not
+ * valid (restore them, e.g. with lbx_set_populations or lbx_load, before stepping on).
+ * Other kernels never wait.  Drops the state's recorded graphs when the limit changes. */
+lbx_status lbx_state_set_wait_limit(lbx_state* st, uint64_t ns);
 /* Autotune the staged step kernel of this state: time per-thread copies and (where they
  * apply) bulk row copies, each with blocks of 32, 64 and 128 threads, over `trials`
  * launches (1..1000) after one warm-up launch, and keep the fastest.  Every timed launch
@@ -408,6 +419,15 @@ void lbx_batch_destroy(lbx_batch* b);
 lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, int64_t n_steps, int ckpt_every,
                        const double* rho_target, void* stream, double* J, double* dJ_dQ0,
                        double* dJ_dtau);
+
+/* Device time (CUDA events on the adjoint's stream, milliseconds) of the phases of the
+ * last lbx_adjoint call that succeeded on the calling thread: ms[0] the forward sweep,
+ * ms[1] the recomputation of the checkpointed segments, ms[2] the reverse (adjoint)
+ * steps, ms[3] everything else between the first and the last timed point (misfit,
+ * adjoint seed, segment restores and their host synchronisations, initial VJP, dJ/dtau
+ * reduction).  Allocation, the host-to-device copies of the inputs and the copies of the
+ * results back to the host are outside all four.  -1 before any call. */
+lbx_status lbx_adjoint_timings(double* ms /* [4] host */);
 
 /* ---- conserved sums without any device allocation --------------------------------------
  * The paper has no counterpart to this call; it exists for callers that must not

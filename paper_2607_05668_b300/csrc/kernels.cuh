@@ -57,6 +57,7 @@ struct KParams {
   const long long* step_ptr;   // step index at the start of this launch sequence
   int step_rel;                // offset of this launch in the sequence
   unsigned int* err;           // device error word: bit 0 = a bounded wait timed out
+  unsigned long long wait_ns;  // limit of a bounded wait for bulk copies (global-timer ns)
   T dx;                        // node spacing (coordinates of the manufactured fields)
   const MmsMode* mms_modes;    // FOURIER forcing table; null = off
   int mms_n;
@@ -901,8 +902,9 @@ __device__ __forceinline__ void mbar_arrive(unsigned int bar) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
 }
 // Suspend until phase `parity` of the barrier completes: tries of at most about a
-// microsecond each, for no longer than `limit_ns` of the global timer and no more than
-// 2^22 tries; false on timeout.
+// microsecond each while less than `limit_ns` of the global timer has passed, and no
+// more than 2^22 tries; false on timeout.  The time is checked before every try, so a
+// zero limit gives up at once whatever the copies' progress.
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -911,6 +913,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ bool mbar_wait(unsigned int bar, unsigned int parity, unsigned long long limit_ns) {
   const unsigned long long t0 = global_ns();
   for (int it = 0; it < (1 << 22); ++it) {
+    if (global_ns() - t0 >= limit_ns) break;
     unsigned int done;
     asm volatile(
         "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
@@ -919,7 +922,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned int bar, unsigned int parity,
         : "r"(bar), "r"(parity), "r"(1000u)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > limit_ns) break;
   }
   return false;
 }
@@ -928,6 +930,9 @@ __device__ __forceinline__ void bulk_g2s(unsigned int dst, const void* src, unsi
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// Default limit of the bounded wait for bulk copies (KParams::wait_ns), and the fixed limit
+// of the second wait after a timeout, which lets the copies in flight land before the
+// block leaves.
 constexpr unsigned long long BULK_WAIT_NS = 1000000000ull;   // 1 s
 
 // The bulk-staged step of one block.  KIND 0: two buffers (pull from A, write B); KIND 1, 2:
@@ -1016,7 +1021,7 @@ __device__ __forceinline__ void bulk_step_body(const typename St::S* A, typename
       }
     }
   }
-  if (!mbar_wait(bar, 0, BULK_WAIT_NS)) {
+  if (!mbar_wait(bar, 0, p.wait_ns)) {
     if (p.err) atomicOr(p.err, 1u);
     mbar_wait(bar, 0, BULK_WAIT_NS);         // let copies in flight land before leaving
     return;

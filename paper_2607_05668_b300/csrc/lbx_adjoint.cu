@@ -102,7 +102,43 @@ __global__ void k_sum_f64(const double* __restrict__ v, long long n, double* __r
   if (threadIdx.x == 0) *out = sm[0];
 }
 
+// Device time of the phases of the last lbx_adjoint call on this thread (ms): forward
+// sweep, recomputation of the segments, reverse steps, and the rest (misfit, seed, initial
+// VJP, dJ/dtau reduction); allocation and host copies of the inputs are outside all four.
+thread_local double g_phase_ms[4] = {-1.0, -1.0, -1.0, -1.0};
+
+// CUDA events around the phases; a failed event call only loses the timing.
+struct PhaseTimer {
+  std::vector<cudaEvent_t> ev;
+  cudaStream_t s;
+  explicit PhaseTimer(cudaStream_t st) : s(st) {}
+  int mark() {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    if (cudaEventRecord(e, s) != cudaSuccess) {
+      cudaEventDestroy(e);
+      return -1;
+    }
+    ev.push_back(e);
+    return (int)ev.size() - 1;
+  }
+  double ms(int a, int b) const {
+    if (a < 0 || b < 0) return 0.0;
+    float v = 0.f;
+    return cudaEventElapsedTime(&v, ev[a], ev[b]) == cudaSuccess ? (double)v : 0.0;
+  }
+  ~PhaseTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace
+
+extern "C" lbx_status lbx_adjoint_timings(double* ms) {
+  if (!ms) return fail(LBX_ERR_ARG, "lbx_adjoint_timings: null argument");
+  for (int i = 0; i < 4; ++i) ms[i] = g_phase_ms[i];
+  return LBX_OK;
+}
 
 extern "C" lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, int64_t n_steps, int ckpt_every,
                                   const double* rho_target, void* stream, double* J, double* dJ_dQ0,
@@ -159,6 +195,11 @@ extern "C" lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, i
   STEP(cudaMemcpyAsync(d_Q, Q_init, sizeof(double) * K * ncell, cudaMemcpyHostToDevice, s));
   STEP(cudaMalloc((void**)&d_grad, sizeof(double) * K * ncell));
   STEP(cudaMalloc((void**)&d_sum, sizeof(double)));
+  for (int i = 0; i < 4; ++i) g_phase_ms[i] = -1.0;
+  STEP(cudaStreamSynchronize(s));      // inputs on the device: the timed phases start here
+  PhaseTimer tm(s);
+  std::vector<int> seg_marks;          // per segment: start, recomputed, reversed
+  const int m_fwd0 = tm.mark();
   // forward sweep, keeping the state at the start of every segment
   for (long long c = 0; c < nck; ++c) {
     STEP(cudaMemcpyAsync(ckpt + bytes * c, st->cur(), bytes, cudaMemcpyDeviceToDevice, s));
@@ -168,6 +209,7 @@ extern "C" lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, i
       return rc;
     }
   }
+  const int m_fwd1 = tm.mark();
   // misfit J = 1/2 sum (rho - rho*)^2 (deterministic float64 reduction)
   {
     double out[KMAX * 4];
@@ -178,6 +220,7 @@ extern "C" lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, i
     if (J) *J = 0.5 * out[0];
   }
   STEP(adj.seed(st->cur(), d_tgt, La, st));
+
   // reverse sweep: recompute each segment from its checkpoint, then step the adjoint back
   void* Lnext = La;
   void* Lout = Lb;
@@ -187,19 +230,34 @@ extern "C" lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, i
     long long base = c * k;
     STEP(cudaMemcpyAsync(st->d_step, &base, sizeof(base), cudaMemcpyHostToDevice, s));
     STEP(cudaStreamSynchronize(s));   // `base` lives on this stack frame
+    seg_marks.push_back(tm.mark());
     for (long long m = 0; m + 1 < len; ++m) STEP(st->ops.step(st, seg + bytes * m, seg + bytes * (m + 1), (int)m, s));
+    seg_marks.push_back(tm.mark());
     for (long long m = len - 1; m >= 0; --m) {
       STEP(adj.step(seg + bytes * m, Lnext, Lout, st, tau_acc));
       std::swap(Lnext, Lout);
     }
+    seg_marks.push_back(tm.mark());
   }
   STEP(adj.init(Lnext, d_Q, st, d_grad));
-  if (dJ_dQ0) STEP(cudaMemcpyAsync(dJ_dQ0, d_grad, sizeof(double) * K * ncell, cudaMemcpyDeviceToHost, s));
   k_sum_f64<<<1, 256, 0, s>>>(tau_acc, ncell, d_sum);
   STEP(cudaGetLastError());
+  const int m_end = tm.mark();
+  if (dJ_dQ0) STEP(cudaMemcpyAsync(dJ_dQ0, d_grad, sizeof(double) * K * ncell, cudaMemcpyDeviceToHost, s));
   double tsum = 0.0;
   STEP(cudaMemcpyAsync(&tsum, d_sum, sizeof(double), cudaMemcpyDeviceToHost, s));
   STEP(cudaStreamSynchronize(s));
+  {
+    double rec = 0.0, rev = 0.0;
+    for (size_t i = 0; i + 2 < seg_marks.size(); i += 3) {
+      rec += tm.ms(seg_marks[i], seg_marks[i + 1]);
+      rev += tm.ms(seg_marks[i + 1], seg_marks[i + 2]);
+    }
+    g_phase_ms[0] = tm.ms(m_fwd0, m_fwd1);
+    g_phase_ms[1] = rec;
+    g_phase_ms[2] = rev;
+    g_phase_ms[3] = tm.ms(m_fwd0, m_end) - g_phase_ms[0] - rec - rev;
+  }
   const double tau = sch->tau[0];
   if (dJ_dtau) *dJ_dtau = tsum / (tau * tau);
   cleanup();

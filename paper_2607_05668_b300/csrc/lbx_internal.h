@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <map>
 #include <utility>
 
@@ -90,6 +91,7 @@ struct lbx_state {
   int block = 128;              // threads per block of staged (shared-memory) step kernels
   int staging = 0;              // lbx_staging of staged step kernels (0 = automatic)
   unsigned int* d_err = nullptr; // device error word of the step kernels
+  unsigned long long wait_ns = lbx::BULK_WAIT_NS;  // limit of the bulk-copy waits
   std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
 
   void* cur() const { return cur_a ? fa : fb; }
@@ -104,6 +106,16 @@ template <>
 inline const lbx::KParams<float>& lbx_state::pc<float>() const { return pf; }
 
 namespace lbx {
+// Bulk row copies need rows of whole 16-byte runs and 16-byte aligned population buffers.
+inline bool bulk_eligible(const lbx_state* st) {
+  return st->sch.nx % 8 == 0 && ((uintptr_t)st->fa % 16) == 0 && ((uintptr_t)st->fb % 16) == 0;
+}
+// The staging a staged step kernel uses: LBX_STAGE_AUTO resolves to bulk row copies when
+// they apply and to per-thread copies otherwise.
+inline int resolved_staging(const lbx_state* st) {
+  if (st->staging != LBX_STAGE_AUTO) return st->staging;
+  return bulk_eligible(st) ? LBX_STAGE_BULK : LBX_STAGE_THREAD;
+}
 void refresh_params(lbx_state* st);
 lbx_status run_reduce(lbx_state* st, const double* Qref, int mode, double* host_out);
 lbx_status ensure_step_counter(lbx_state* st);

@@ -1,0 +1,6 @@
+// Step, init, moment and reduction kernels of the paper's 18-component MHD on D2Q5, in every storage mode.
+#include "ops_impl.cuh"
+
+namespace lbx {
+bool find_ops_mhd18_d2q5(int precision, Ops* o) { return pick_store<LatD2Q5, SysMHD18>(precision, o); }
+}  // namespace lbx

@@ -86,6 +86,7 @@ _sig("lbx_step", C.c_int, [_P, C.c_int64])
 _sig("lbx_state_use_graph", C.c_int, [_P, C.c_int])
 _sig("lbx_state_set_block", C.c_int, [_P, C.c_int])
 _sig("lbx_state_set_staging", C.c_int, [_P, C.c_int])
+_sig("lbx_state_set_wait_limit", C.c_int, [_P, C.c_uint64])
 _sig("lbx_state_tune", C.c_int, [_P, C.c_int, _I, _I, _D])
 _sig("lbx_moments", C.c_int, [_P, _P, C.c_int])
 _sig("lbx_conserved_sums", C.c_int, [_P, _D])
@@ -103,6 +104,7 @@ _sig("lbx_state_destroy", None, [_P])
 _sig("lbx_probe_peaks", C.c_int, [C.c_size_t, _P, _D, _D, _D])
 _sig("lbx_conserved_sums_static", C.c_int, [_P, _P, _P, C.c_int, _P])
 _sig("lbx_adjoint", C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, _D, _P, _D])
+_sig("lbx_adjoint_timings", C.c_int, [_D])
 STATIC_REDUCE_MAX_BLOCKS = 512
 
 
@@ -269,6 +271,10 @@ class State:
         STAGE_BULK or STAGE_PIPE (see lbx_state_set_staging)."""
         check(_lib.lbx_state_set_staging(self._h, int(staging)))
 
+    def set_wait_limit(self, ns):
+        """lbx_state_set_wait_limit: limit (ns) of the bulk-staged kernels' bounded wait."""
+        check(_lib.lbx_state_set_wait_limit(self._h, int(ns)))
+
     def tune(self, trials=5):
         """lbx_state_tune: pick the fastest staging and block without changing the state;
         returns {"staging", "block", "ms_per_step"}."""
@@ -291,6 +297,15 @@ class State:
         out = np.empty(shape, dtype=np.float64)
         check(_lib.lbx_moments(self._h, out.ctypes.data, 0))
         return torch.from_numpy(out)
+
+    def moments_into(self, out):
+        """lbx_moments into a caller-owned CUDA float64 tensor [K, *grid] (asynchronous on
+        the state's stream)."""
+        shape = (self.K,) + self.scheme.grid
+        if not (out.is_cuda and out.dtype == torch.float64 and tuple(out.shape) == shape and out.is_contiguous()):
+            raise ValueError(f"moments_into needs a contiguous CUDA float64 tensor of shape {shape}")
+        check(_lib.lbx_moments(self._h, out.data_ptr(), 1))
+        return out
 
     def conserved_sums(self):
         s = _dbl(self.K)
@@ -424,6 +439,10 @@ class Batch:
                         int(cur["use_graph"] if use_graph is None else use_graph))
         check(_lib.lbx_batch_set_config(self._h, C.byref(c)))
 
+    def set_wait_limit(self, ns):
+        """lbx_state_set_wait_limit: limit (ns) of the bulk-staged kernels' bounded wait."""
+        check(_lib.lbx_state_set_wait_limit(self._h, int(ns)))
+
     def tune(self, trials=5):
         buf = C.create_string_buffer(1 << 15)
         check(_lib.lbx_batch_tune(self._h, int(trials), buf, len(buf)))
@@ -448,3 +467,11 @@ def adjoint(scheme: Scheme, Q_init, n_steps, ckpt_every, rho_target, stream=None
     check(_lib.lbx_adjoint(scheme._h, Qh.ctypes.data, int(n_steps), int(ckpt_every), th.ctypes.data,
                            _stream_handle(stream), C.byref(J), g.ctypes.data, C.byref(gt)))
     return J.value, torch.from_numpy(g), gt.value
+
+
+def adjoint_timings():
+    """lbx_adjoint_timings: device ms of the last adjoint's forward sweep, recomputation,
+    reverse steps and the rest, as a dict."""
+    ms = _dbl(4)
+    check(_lib.lbx_adjoint_timings(ms))
+    return {"forward_ms": ms[0], "recompute_ms": ms[1], "reverse_ms": ms[2], "other_ms": ms[3]}

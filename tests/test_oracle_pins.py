@@ -336,6 +336,37 @@ def test_relaxation_diffusion_decay_rate():
     assert abs(rate - pred) / pred < 5e-3                     # O(k^2) relative correction
 
 
+@pytest.mark.parametrize("sname,lname", CASES)
+def test_populations_relax_at_the_stated_lattice_rates(sname, lname):
+    """Supplement, recipes paragraph: tracker populations collide at the fixed lattice rate
+    1/(g_tau + 1), with tau_grad = g_tau dt in their flux and source; conserved populations
+    at 1/tau_LB, tau_LB = 1/2 + tau_R dt (Sec. 2.3.1).  On a spatially uniform state the
+    streaming moves nothing, and a perturbation delta of one component's populations whose
+    moment is zero leaves Q, f^eq(Q) and S(Q) unchanged, so one step of Eq. lbe_update maps
+    it to exactly (1 - 1/tau_k) delta.  The rates below are the paper's numbers, written
+    out; the oracle's step (and its relaxation-time vector) are run as a black box."""
+    g_tau, tau_R, f = 6.0, 50.0, 1.9
+    lat = oracle.LATTICES[lname]
+    N = 4
+    dx, dt = oracle.lattice_steps(N, f, "diffusive")
+    sysm = _system(sname)
+    sch = oracle.Scheme(sysm, lat, (N,) * lat.D, dx, dt, oracle.tau_vector(sysm, dt, tau_R=tau_R, g_tau=g_tau))
+    Q = _positive_state(sysm, 1, 11).reshape((sysm.K,) + (1,) * lat.D).expand((sysm.K,) + (N,) * lat.D).clone()
+    f0 = sch.init(Q)
+    base = sch.step(f0, 0.0)
+    q = len(lat.c)
+    rate_cons = 1.0 - 1.0 / (0.5 + tau_R * dt)
+    rate_track = 1.0 - 1.0 / (g_tau + 1.0)
+    for k in range(sysm.K):
+        delta = torch.zeros_like(f0)
+        eps = 1e-6 * (1.0 + float(f0[k].abs().max()))
+        delta[k, 1] = eps                           # moment-free: + on velocity 1, - on velocity 2
+        delta[k, 2] = -eps
+        got = sch.step(f0 + delta, 0.0) - base
+        rate = rate_cons if k < sysm.n_cons else rate_track
+        torch.testing.assert_close(got, rate * delta, rtol=0, atol=1e-9 * eps * q)
+
+
 def test_shifted_equals_unshifted_fp64():
     """Sec. 2.4.3: evolving f* = f - f^eq(Q0, F0) is an identity transformation."""
     case, a = _nsf_scheme(16)
