@@ -224,9 +224,12 @@ def fields(workload, case):
     return {"nsf": syn.nsf_fields, "mhd": syn.mhd_fields, "adr": syn.adr_fields}[workload](case)
 
 
-def scheme(W, L, workload, case, prec, inplace=False):
+def scheme(W, L, workload, case, prec, inplace=False, **slab):
     p = PREC[prec]
     sm = L.STREAM_IN_PLACE if inplace else L.STREAM_TWO_BUFFERS
+    if slab:
+        fn = {"nsf": W.nsf_scheme, "mhd": W.mhd_scheme, "hcnsf": W.hcnsf_scheme}[workload]
+        return fn(case, p, **slab)
     if workload in PAPER_D2Q5:
         params, Q0 = case.system_args()
         sysm = W.table_system(case.table(), params, Q0)
@@ -444,21 +447,55 @@ def run_variants(L, W, args, stream, peak, probe_fp64=None):
     return v
 
 # --------------------------------------------------------------------- our arm
+def slab_kwargs(workload, case, rank, ws):
+    """Slab arguments of rank `rank` when every rank holds one case-sized slab of a grid
+    stacked along the last axis (weak scaling): global planes n ws, origin n rank.  The
+    seeded fields are periodic with period 1 in every coordinate, so each slab's initial
+    fields are the case's own."""
+    if workload not in ("nsf", "mhd", "hcnsf"):
+        raise SystemExit(f"--decomp slab: workload {workload} has no slab wiring")
+    dim3 = workload in DIM3
+    ext = (case.n, case.n, case.n) if dim3 else (case.n, case.n)
+    return {"extent": ext, "slab_origin": rank * case.n, "slab_planes_global": ws * case.n}
+
+
 def run_ours(args):
     ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_2607_05668_b300 import lbx as L, workloads as W
+    from paper_2607_05668_b300 import lbx as L, workloads as W, slab as SL
 
+    decomp = args.decomp or ("slab" if ws > 1 else "whole")
     case = make_case(args.workload, args.n)
     Q = fields(args.workload, case)
     ncell = cells(args.workload, case)
     K, q = kq(args.workload)
-    sch = scheme(W, L, args.workload, case, args.precision)
     stream = torch.cuda.Stream()
-    st = L.State(sch, Q.cuda(), stream=stream)
+    ring = None
+    if decomp == "slab":
+        ring = SL.RingExchange(rank=0, world=1) if ws == 1 else SL.RingExchange()
+        kw = slab_kwargs(args.workload, case, rank, ws)
+        sch = scheme(W, L, args.workload, case, args.precision, **kw)
+        if args.precision == "fp16":        # the slabs share the grid's storage scales
+            probe_st = L.State(sch, Q.cuda(), stream=stream)
+            kw["fp16_scales"] = list(ring.max(probe_st.scales()))
+            probe_st.close()
+            sch = scheme(W, L, args.workload, case, args.precision, **kw)
+    else:
+        sch = scheme(W, L, args.workload, case, args.precision)
+    with torch.cuda.stream(stream):
+        slab = SL.Slab(sch, Q.cuda(), stream=stream) if decomp == "slab" else None
+    st = slab.state if slab else L.State(sch, Q.cuda(), stream=stream)
+
+    def run_steps(n, state=None, sl=None):
+        if sl is not None:
+            with torch.cuda.stream(stream):   # NCCL orders its messages with this stream
+                SL.step_ring(sl, ring, n)
+        else:
+            state.step(n)
+
     if args.staging is not None:            # a fixed launch shape (profiling one staging)
         st.set_staging({"thread": L.STAGE_THREAD, "bulk": L.STAGE_BULK, "lanes2": L.STAGE_LANES2,
                         "pipe": L.STAGE_PIPE}[args.staging])
@@ -466,7 +503,7 @@ def run_ours(args):
         launch = {"kernel": f"staging {args.staging} (fixed)", "block": args.block}
     else:
         launch = launch_desc(L, st.tune())  # staged kernels: fastest launch shape, state unchanged
-    st.step(args.warmup)
+    run_steps(args.warmup, st, slab)
     st.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -479,7 +516,7 @@ def run_ours(args):
     barrier()
     with ClockSampler(local) as clk:
         e0.record(stream)
-        st.step(args.steps)
+        run_steps(args.steps, st, slab)
         e1.record(stream)
         e1.synchronize()
     barrier()
@@ -501,6 +538,8 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_kernel": profile_kernel(f"{args.workload}_{args.precision}"),
             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch}
+    if decomp == "slab":
+        roof["note"] = "time per step includes the face exchange (pack, transport, unpack)"
     if args.precision == "fp64":
         roof["note"] = "FP64 arithmetic on B300 is far below the HBM ridge; see fp64_alu"
 
@@ -509,26 +548,31 @@ def run_ours(args):
     # `steps` steps, the moments back to pinned host memory.  The population buffers and the
     # device copy of the fields are allocated once, outside the timed region (caller-owned
     # buffers, as a program that solves repeatedly keeps them).
-    st.close()
+    if slab:
+        slab.close()
+    else:
+        st.close()
     Qh = Q.contiguous().pin_memory()
     out_h = torch.empty_like(Qh).pin_memory()
     Qdev = torch.empty_like(Qh, device="cuda")
     Qout = torch.empty_like(Qdev)
     bufs = [torch.empty(sch.buffer_bytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    faces = [torch.empty(max(sch.halo_bytes, 16), dtype=torch.uint8, device="cuda") for _ in range(4)]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         ev[0].record(stream)
         Qdev.copy_(Qh, non_blocking=True)
         ev[1].record(stream)
-    st2 = L.State(sch, Qdev, stream=stream, buffers=bufs)       # synchronous (checks)
+    sl2 = SL.Slab(sch, Qdev, stream=stream, buffers=bufs, faces=faces) if decomp == "slab" else None
+    st2 = sl2.state if sl2 else L.State(sch, Qdev, stream=stream, buffers=bufs)   # synchronous (checks)
     t1 = time.perf_counter()
     if launch.get("tuned_ms_per_step") is not None:
         st2.set_staging(L.STAGE_BULK if launch["kernel"].startswith("k_step_bulk") else L.STAGE_THREAD)
         st2.set_block(launch["block"])
     ev[2].record(stream)
-    st2.step(args.steps)
+    run_steps(args.steps, st2, sl2)
     ev[3].record(stream)
     st2.moments_into(Qout)
     with torch.cuda.stream(stream):
@@ -536,6 +580,11 @@ def run_ours(args):
     stream.synchronize()
     t2 = time.perf_counter()
     e2e_s = t2 - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
     st2.close()
     del bufs
     e2e = {"value": ws * ncell * args.steps / e2e_s, "unit": "LUP/s",
@@ -549,17 +598,25 @@ def run_ours(args):
                         "moments_and_d2h": (t2 - t1) * 1e3 - ev[2].elapsed_time(ev[3]),
                         "total": e2e_s * 1e3}}
 
+    config = config_of(args.workload, case, args.precision, K, q, ws)
+    if decomp == "slab":
+        g = list(config["grid"])
+        g[-1] = case.n * ws
+        config["parallelism"] = (f"slab x{ws}: one {'z' if args.workload in DIM3 else 'y'}-slab of "
+                                 f"{'x'.join(map(str, config['grid']))} per GPU of a {'x'.join(map(str, g))} "
+                                 "grid, one face exchange per step (lbx_halo_pack, NCCL send/recv, "
+                                 "lbx_halo_unpack)")
     result = {
         "metric": "Lattice updates/s", "value": value, "unit": "LUP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAME[args.precision], "data": "synthetic",
-        "config": config_of(args.workload, case, args.precision, K, q, ws),
-        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "finite": finite, "launch": launch,
-        "clocks": clk.summary(),
+        "config": config,
+        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps * (3 if decomp == "slab" else 1),
+        "finite": finite, "launch": launch, "clocks": clk.summary(),
     }
-    if args.precision == "fp64" or args.probe or not args.no_variants:
+    if rank == 0 and (args.precision == "fp64" or args.probe or not args.no_variants):
         result["probe"] = L.probe_peaks(2 << 30, stream=stream)
-    if not args.no_variants and args.workload == "nsf" and args.precision == "fp32":
+    if rank == 0 and not args.no_variants and args.workload == "nsf" and args.precision == "fp32":
         result["variants"] = run_variants(L, W, args, stream, peak, result["probe"]["fp64_gflops"])
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args, case)
@@ -567,6 +624,7 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
     if ws > 1:
         import torch.distributed as dist
+        dist.barrier()
         dist.destroy_process_group()
 
 
@@ -683,6 +741,9 @@ def main():
     ap.add_argument("--staging", choices=["thread", "bulk", "lanes2", "pipe"], default=None,
                     help="staged kernels: fix the staging instead of tuning (with --block)")
     ap.add_argument("--block", type=int, default=128, choices=[32, 64, 128], help="block size with --staging")
+    ap.add_argument("--decomp", choices=["whole", "slab", "replicas"], default=None,
+                    help="multi-GPU layout: slab (default for N > 1) = one slab per GPU of one grid with a face "
+                         "exchange per step; replicas = independent grids; whole (N = 1 default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

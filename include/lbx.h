@@ -211,6 +211,21 @@ typedef struct {
     int prescribed;        /* lbx_prescribed (HCNSF_3D only; NONE for every other family) */
     double prescribed_params[10]; /* pf of the prescribed fields                         */
     int streaming;         /* lbx_streaming                                             */
+    /* Slab of a larger periodic grid cut along its last axis (y in 2D, z in 3D), for a
+     * domain decomposition with one slab per process or GPU (see lbx_halo_pack).
+     * slab_planes_global: planes of the whole grid along that axis; 0 (the default) means
+     * this scheme is the whole grid.  slab_origin: global index of the slab's first plane
+     * (0 <= slab_origin and slab_origin + local planes <= slab_planes_global).  The extents
+     * are the slab's own; dx = 1/nx is the whole grid's (a slab spans the whole x extent,
+     * and the whole y extent in 3D), and node coordinates (manufactured forcing, prescribed
+     * fields) use the global plane index.  TWO_BUFFERS streaming only. */
+    int64_t slab_origin;
+    int64_t slab_planes_global;
+    /* FP16_SCALED only: when every one of the K values is > 0, the storage scales s_k
+     * lbx_init uses instead of deriving them from the initial populations (slabs of one
+     * grid must share their scales; powers of two keep the scaling exact).  All zero (the
+     * default): derived at init as described for LBX_FP16_SCALED. */
+    double fp16_scales[24];
 } lbx_scheme_desc;
 
 typedef struct lbx_system lbx_system;
@@ -366,6 +381,48 @@ lbx_status lbx_save(lbx_state* st, const char* path);
 lbx_status lbx_load(lbx_state* st, const char* path);
 
 void lbx_state_destroy(lbx_state* st);
+
+/* ---- slabs of one grid: the face exchange (domain decomposition) ----------------------
+ * A slab (lbx_scheme_desc.slab_planes_global > 0) steps with the periodic wrap of its own
+ * planes along the slab axis a (y in 2D, z in 3D).  In the pull layout that wrap makes the
+ * nodes of plane 0 read their c_a = +1 populations from the slots of the last plane P - 1,
+ * and the nodes of plane P - 1 read their c_a = -1 populations from the slots of plane 0;
+ * nothing else reads those slots.  After a step they hold the populations that leave the
+ * slab through its upper and its lower face, and Eq. lbe_update across the faces needs
+ * them exchanged with the neighbouring slabs: after EVERY lbx_step(st, 1) of a slab, and
+ * before its next step or any call that reads its populations, the caller runs
+ *     lbx_halo_pack(st, to_upper, to_lower);      exchange;
+ *     lbx_halo_unpack(st, from_lower, from_upper);
+ * where from_lower is the lower neighbour's to_upper and from_upper the upper neighbour's
+ * to_lower (periodic: the first slab's lower neighbour is the last slab).  lbx_init and
+ * lbx_set_populations leave the slots consistent (they hold the nodes' own pre-collision
+ * values), so no exchange is needed before the first step; lbx_load restores the slots as
+ * they were saved.  One velocity
+ * plane of one face per velocity crossing it: 3 of 9 on D2Q9, 1 of 5 on D2Q5, 1 of 7 on
+ * D3Q7, 5 of 19 on D3Q19, for all K components.  Reductions (sums, norms, checks) are per
+ * slab: add the sums (lbx_conserved_sums, lbx_error_stats) over the slabs in float64.
+ * With a single slab (the whole grid) the exchange is from_lower = to_upper and
+ * from_upper = to_lower.  These calls also accept a whole-grid two-buffer state. */
+/* Bytes of each face buffer: (velocities crossing a face) x K x (nodes of a plane) x the
+ * storage size; 0 for a NULL scheme. */
+size_t lbx_halo_bytes(const lbx_scheme* sch);
+/* Copy the two faces' outgoing slots of the current populations into device buffers of
+ * lbx_halo_bytes() bytes, 16-byte aligned: to_upper (plane P - 1, c_a = +1) and to_lower
+ * (plane 0, c_a = -1).  Asynchronous on the state's stream (one kernel launch). */
+lbx_status lbx_halo_pack(lbx_state* st, void* to_upper, void* to_lower);
+/* Copy the neighbours' face buffers into the slots the next step pulls across the faces:
+ * from_lower into plane P - 1's c_a = +1 slots, from_upper into plane 0's c_a = -1 slots.
+ * Asynchronous on the state's stream (one kernel launch).  The face buffers' contents are
+ * in the state's storage representation (shifted and scaled), so slabs that exchange must
+ * share the scheme's storage, background state and (FP16) scales. */
+lbx_status lbx_halo_unpack(lbx_state* st, const void* from_lower, const void* from_upper);
+/* The storage scales s_k of the state (1 unless FP16_SCALED), float64 [K] host array. */
+lbx_status lbx_state_scales(const lbx_state* st, double* scales);
+/* Raw error statistics per component against Q_ref [K][cells] (host or device): stats[k][0]
+ * = sum_x e^2, [k][1] = sum_x Q_ref^2, [k][2] = max_x |e|, [k][3] = max_x |Q_ref|, e = Q_k -
+ * Q_ref,k, float64 [K][4] host array.  The relative norms of lbx_error_norms follow from
+ * them; slabs add [0], [1] and take the maximum of [2], [3] over the grid. */
+lbx_status lbx_error_stats(lbx_state* st, const double* Q_ref, int ref_on_device, double* stats);
 
 /* ---- batched states: many independent grids, one persistent launch per step ---------
  * n 2D schemes of the same family, lattice, storage (FP64 or FP32_SHIFT) and forcing,

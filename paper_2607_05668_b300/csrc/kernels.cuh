@@ -42,6 +42,7 @@ struct MmsMode {
 template <typename T>
 struct KParams {
   int nx, ny, nz, pad_;
+  int oy, oz;                  // slab origin: global index of local row 0 (2D) or plane 0 (3D)
   long long ncell;             // nodes per population plane
   T Q0[KMAX];                  // background state (shift reference)
   T F0l[KMAX][3];              // (dt/dx)/c_s^2 * Phi(Q0), used by the unshifted mode
@@ -232,7 +233,7 @@ __device__ __forceinline__ void eval_node(const KParams<T>& p, int x, int y, int
                                           T (&Phi)[SysT<T>::K][SysT<T>::D], T (&Src)[SysT<T>::K]) {
   using Sys = SysT<T>;
   if constexpr (NcfOf<Sys>::value > 0) {
-    const T xc[3] = {T(x) * p.dx, T(y) * p.dx, T(z) * p.dx};
+    const T xc[3] = {T(x) * p.dx, T(y + p.oy) * p.dx, T(z + p.oz) * p.dx};
     T cf[NcfOf<Sys>::value];
     if (p.pf_src_dt != p.pf_flux_dt && p.pf_kind == 2) {
       // two time levels of a moving solid: the spatial factors are shared
@@ -286,7 +287,7 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
   using SysD = SysT<D1>;
   constexpr int K = SysD::K, NC = SysD::NC, NP = SysD::NPRIM, D = Lat::D;
   const T t = (T(step) + T(0.5)) * p.dt;
-  const T xc[3] = {T(x) * p.dx, T(y) * p.dx, T(z) * p.dx};
+  const T xc[3] = {T(x) * p.dx, T(y + p.oy) * p.dx, T(z + p.oz) * p.dx};
   T V[NP], Vt[NP], G[NP][3], Gt[NP][3], H[NP][3][3];
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
@@ -1265,6 +1266,72 @@ __global__ void k_step_batch(const typename St::S* __restrict__ A, typename St::
       const int y = c / p.nx;
       step_node<Lat, SysT, St, MODE, 128, FOURIER>(A + off, B + off, p, c - y * p.nx, y, 0, step);
     }
+  }
+}
+
+// ------------------------------------------------------------ slab faces (halo exchange)
+// A slab of a larger periodic grid, cut along its last axis a (y in 2D, z in 3D) into P
+// local planes, steps with the local periodic wrap along a.  In the pull layout the wrap
+// makes the nodes of plane 0 read their c_a = +1 populations from the slots of plane P - 1,
+// and the nodes of plane P - 1 read their c_a = -1 populations from the slots of plane 0;
+// no other node reads those slots.  After a step they hold this slab's outgoing populations
+// (the post-collision values leaving through the upper and the lower face), and the global
+// streaming (Eq. lbe_update across the faces) needs them replaced by the lower neighbour's
+// plane P - 1, c_a = +1 values and the upper neighbour's plane 0, c_a = -1 values.
+// k_face copies the slots of one face between the population buffer and a contiguous face
+// buffer.  Face buffer layout, for each of the NF velocities with c_a = s (lattice order):
+// the component pairs [KP][plane cells] of V, then the odd component [plane cells] of S.
+template <class Lat>
+struct FaceVel {
+  static constexpr int A = Lat::D - 1;                           // the slab axis
+  static constexpr int count(int s) {
+    int n = 0;
+    for (int i = 0; i < Lat::Q; ++i) n += Lat::c(i, A) == s ? 1 : 0;
+    return n;
+  }
+  static constexpr int NF = count(1);
+  static_assert(NF == count(-1), "the velocity set is symmetric along the slab axis");
+  // the j-th velocity (lattice order) with c_a = s
+  __host__ __device__ static constexpr int nth(int j, int s) {
+    for (int i = 0; i < Lat::Q; ++i)
+      if (Lat::c(i, A) == s && j-- == 0) return i;
+    return 0;
+  }
+};
+
+// One thread per (plane cell, face velocity j); blockIdx.z selects the face: 0 = the upper
+// face (plane P - 1, c_a = +1), 1 = the lower face (plane 0, c_a = -1).  PACK copies the
+// population buffer's slots into the face buffers, otherwise the face buffers into the slots.
+template <class Lat, template <typename> class SysT, class St, bool PACK>
+__global__ void k_face(typename St::S* __restrict__ A, typename St::S* __restrict__ up,
+                       typename St::S* __restrict__ dn, const KParams<typename St::C> p) {
+  using S = typename St::S;
+  using V = typename PairOf<S>::V;
+  constexpr int K = SysT<typename St::C>::K, Q = Lat::Q, KP = K / 2, NF = FaceVel<Lat>::NF;
+  const unsigned int pc = Lat::D == 3 ? (unsigned int)p.nx * (unsigned int)p.ny : (unsigned int)p.nx;
+  const unsigned int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= pc) return;
+  const int j = (int)blockIdx.y, face = (int)blockIdx.z;
+  const int sgn = face == 0 ? 1 : -1;
+  int i = 0;
+#pragma unroll
+  for (int jj = 0; jj < NF; ++jj)
+    if (jj == j) i = FaceVel<Lat>::nth(jj, sgn);
+  const unsigned int planes = Lat::D == 3 ? (unsigned int)p.nz : (unsigned int)p.ny;
+  const unsigned int cell = (face == 0 ? planes - 1u : 0u) * pc + c;
+  const unsigned int plane = (unsigned int)p.ncell;
+  S* buf = face == 0 ? up : dn;
+  V* bv = reinterpret_cast<V*>(buf);
+#pragma unroll
+  for (int kp = 0; kp < KP; ++kp) {
+    V* g = reinterpret_cast<V*>(A + eidx<K, Q>(2 * kp, i, cell, plane));
+    V* h = bv + ((size_t)j * KP + kp) * pc + c;
+    if (PACK) *h = *g; else *g = *h;
+  }
+  if constexpr ((K & 1) != 0) {
+    S* g = A + eidx<K, Q>(K - 1, i, cell, plane);
+    S* h = buf + (size_t)NF * KP * pc * 2 + (size_t)j * pc + c;
+    if (PACK) *h = *g; else *g = *h;
   }
 }
 

@@ -148,6 +148,8 @@ extern "C" lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, i
   if (ckpt_every < 1) return fail(LBX_ERR_ARG, "lbx_adjoint: ckpt_every must be >= 1");
   if (sch->d.streaming != LBX_STREAM_TWO_BUFFERS)
     return fail(LBX_ERR_UNSUPPORTED, "lbx_adjoint: two-buffer streaming needed");
+  if (sch->d.slab_planes_global != 0)
+    return fail(LBX_ERR_UNSUPPORTED, "lbx_adjoint: whole grids only (no slab face exchange in the reverse sweep)");
   AdjOps adj;
   if (!find_adj(sch->sys.family, sch->d.lattice, sch->d.precision, &adj))
     return fail(LBX_ERR_UNSUPPORTED, "lbx_adjoint: FP64 or FP32_SHIFT storage of a compiled family needed");

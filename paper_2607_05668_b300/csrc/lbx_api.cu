@@ -250,6 +250,30 @@ extern "C" lbx_status lbx_scheme_derive(const lbx_system* sys, const lbx_scheme_
   }
   if (d->streaming != LBX_STREAM_TWO_BUFFERS && d->streaming != LBX_STREAM_IN_PLACE)
     return fail(LBX_ERR_ARG, "lbx_scheme_derive: unknown streaming %d", d->streaming);
+  if (d->slab_planes_global != 0) {
+    const int64_t P = sys->D == 3 ? nz : ny;
+    if (d->slab_planes_global < P || d->slab_origin < 0 || d->slab_origin + P > d->slab_planes_global ||
+        d->slab_planes_global > (1 << 24))
+      return fail(LBX_ERR_ARG, "lbx_scheme_derive: slab of %lld planes at %lld does not fit %lld global planes",
+                  (long long)P, (long long)d->slab_origin, (long long)d->slab_planes_global);
+    if (d->streaming != LBX_STREAM_TWO_BUFFERS)
+      return fail(LBX_ERR_UNSUPPORTED, "lbx_scheme_derive: slabs need two-buffer streaming");
+  } else if (d->slab_origin != 0) {
+    return fail(LBX_ERR_ARG, "lbx_scheme_derive: slab_origin without slab_planes_global");
+  }
+  {
+    int given = 0;
+    for (int k = 0; k < family_K(sys->family); ++k) {
+      const double v = d->fp16_scales[k];
+      if (!std::isfinite(v) || v < 0.0) return fail(LBX_ERR_ARG, "lbx_scheme_derive: fp16_scales[%d] invalid", k);
+      given += v > 0.0;
+    }
+    if (given != 0 && given != family_K(sys->family))
+      return fail(LBX_ERR_ARG, "lbx_scheme_derive: give fp16_scales for all %d components or none",
+                  family_K(sys->family));
+    if (given != 0 && d->precision != LBX_FP16_SCALED)
+      return fail(LBX_ERR_ARG, "lbx_scheme_derive: fp16_scales need FP16_SCALED storage");
+  }
   const bool has_trackers = sys->K > sys->NC;
   if (has_trackers && !(d->g_tau > 0.0)) return fail(LBX_ERR_ARG, "lbx_scheme_derive: g_tau must be > 0");
   auto* s = new lbx_scheme();
@@ -567,6 +591,8 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
   p.nx = s.nx;
   p.ny = s.ny;
   p.nz = s.nz;
+  p.oy = s.sys.D == 2 ? (int)s.d.slab_origin : 0;
+  p.oz = s.sys.D == 3 ? (int)s.d.slab_origin : 0;
   p.ncell = s.ncell;
   double F0[KMAX][3], prm[NPRM];
   background_flux(&s, F0);
@@ -761,9 +787,12 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
       t[i] = std::sin(2.0 * M_PI * i / nx);
       t[nx + i] = std::cos(2.0 * M_PI * i / nx);
     }
+    // rows of a slab take their global index over the whole grid's rows
+    const double gy = sch->d.slab_planes_global > 0 ? (double)sch->d.slab_planes_global : (double)ny;
+    const double oy = (double)sch->d.slab_origin;
     for (int j = 0; j < ny; ++j) {
-      t[2 * nx + j] = std::sin(2.0 * M_PI * j / ny);
-      t[2 * nx + ny + j] = std::cos(2.0 * M_PI * j / ny);
+      t[2 * nx + j] = std::sin(2.0 * M_PI * (j + oy) / gy);
+      t[2 * nx + ny + j] = std::cos(2.0 * M_PI * (j + oy) / gy);
     }
     for (size_t i = 0; i < t.size(); ++i) tf[i] = (float)t[i];
     CKI(cudaMalloc(&st->d_mms_tab64, sizeof(double) * t.size()));
@@ -798,7 +827,10 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
     CKI(cudaMalloc(&dQ, qbytes));
     CKI(cudaMemcpyAsync(dQ, Q, qbytes, cudaMemcpyHostToDevice, st->stream));
   }
-  if (sch->d.precision == LBX_FP16_SCALED) {
+  if (sch->d.precision == LBX_FP16_SCALED && sch->d.fp16_scales[0] > 0.0) {
+    for (int k = 0; k < K; ++k) st->scale[k] = sch->d.fp16_scales[k];    // given (shared by slabs)
+    refresh_params(st);
+  } else if (sch->d.precision == LBX_FP16_SCALED) {
     unsigned long long* dmax = nullptr;
     CKI(cudaMalloc(&dmax, sizeof(unsigned long long) * K));
     cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long) * K, st->stream);
@@ -1092,6 +1124,61 @@ extern "C" lbx_status lbx_error_norms(lbx_state* st, const double* Q_ref, int re
     if (relL2) relL2[k] = out[4 * k + 1] > 0 ? std::sqrt(out[4 * k] / out[4 * k + 1]) : std::sqrt(out[4 * k]);
     if (relLinf) relLinf[k] = out[4 * k + 3] > 0 ? out[4 * k + 2] / out[4 * k + 3] : out[4 * k + 2];
   }
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_error_stats(lbx_state* st, const double* Q_ref, int ref_on_device, double* stats) {
+  if (!st || !Q_ref || !stats) return fail(LBX_ERR_ARG, "lbx_error_stats: null argument");
+  const int K = st->sch.sys.K;
+  const size_t bytes = sizeof(double) * K * (size_t)st->sch.ncell;
+  const double* d = Q_ref;
+  double* tmp = nullptr;
+  if (!ref_on_device) {
+    CK(cudaMalloc(&tmp, bytes));
+    if (cudaError_t e = cudaMemcpyAsync(tmp, Q_ref, bytes, cudaMemcpyHostToDevice, st->stream)) {
+      cudaFree(tmp);
+      return fail(LBX_ERR_CUDA, "lbx_error_stats: %s", cudaGetErrorString(e));
+    }
+    d = tmp;
+  }
+  double out[KMAX * 4];
+  lbx_status s = run_reduce(st, d, 1, out);
+  if (tmp) cudaFree(tmp);
+  if (s) return s;
+  for (int i = 0; i < 4 * K; ++i) stats[i] = out[i];
+  return LBX_OK;
+}
+
+// ------------------------------------------------------------------ slab faces
+extern "C" size_t lbx_halo_bytes(const lbx_scheme* s) {
+  if (!s) return 0;
+  Ops o{};
+  if (!find_ops(s->sys.family, s->d.lattice, s->d.precision, &o)) return 0;
+  const size_t pc = s->sys.D == 3 ? (size_t)s->nx * s->ny : (size_t)s->nx;
+  return (size_t)o.face_nf * s->sys.K * pc * storage_size(s->d.precision);
+}
+
+static lbx_status face_call(lbx_state* st, void* a, void* b, int pack, const char* who) {
+  if (!st || !a || !b) return fail(LBX_ERR_ARG, "%s: null argument", who);
+  if (st->inplace) return fail(LBX_ERR_UNSUPPORTED, "%s: two-buffer states only", who);
+  if (((uintptr_t)a % 16) != 0 || ((uintptr_t)b % 16) != 0)
+    return fail(LBX_ERR_ARG, "%s: face buffers must be 16-byte aligned", who);
+  if (cudaError_t e = st->ops.face(st, st->cur(), a, b, pack))
+    return fail(LBX_ERR_CUDA, "%s: %s", who, cudaGetErrorString(e));
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_halo_pack(lbx_state* st, void* to_upper, void* to_lower) {
+  return face_call(st, to_upper, to_lower, 1, "lbx_halo_pack");
+}
+
+extern "C" lbx_status lbx_halo_unpack(lbx_state* st, const void* from_lower, const void* from_upper) {
+  return face_call(st, const_cast<void*>(from_lower), const_cast<void*>(from_upper), 0, "lbx_halo_unpack");
+}
+
+extern "C" lbx_status lbx_state_scales(const lbx_state* st, double* scales) {
+  if (!st || !scales) return fail(LBX_ERR_ARG, "lbx_state_scales: null argument");
+  for (int k = 0; k < st->sch.sys.K; ++k) scales[k] = st->scale[k];
   return LBX_OK;
 }
 

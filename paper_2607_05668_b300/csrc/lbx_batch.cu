@@ -165,6 +165,8 @@ extern "C" lbx_status lbx_batch_create(const lbx_scheme* const* schemes, int n, 
     if (s.sys.D != 2) return fail(LBX_ERR_UNSUPPORTED, "lbx_batch_create: batches are 2D");
     if (s.d.streaming != LBX_STREAM_TWO_BUFFERS)
       return fail(LBX_ERR_UNSUPPORTED, "lbx_batch_create: batches use two-buffer streaming");
+    if (s.d.slab_planes_global != 0)
+      return fail(LBX_ERR_UNSUPPORTED, "lbx_batch_create: instances are whole grids, not slabs");
   }
   if (s0.d.precision == LBX_FP16_SCALED)
     return fail(LBX_ERR_UNSUPPORTED, "lbx_batch_create: FP16_SCALED storage is not batched");

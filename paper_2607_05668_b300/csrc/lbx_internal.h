@@ -54,6 +54,9 @@ struct Ops {
   size_t elem_bytes;   // storage bytes per population value
   // in-place step of the given kind (1 or 2) on the single buffer F (see k_step_inplace)
   cudaError_t (*step_inplace)(const lbx_state*, void* F, int kind, int rel, cudaStream_t);
+  // slab faces: copy the face slots of A into (pack = 1) or from (0) the two face buffers
+  cudaError_t (*face)(const lbx_state*, void* A, void* up, void* dn, int pack);
+  int face_nf;         // velocities crossing one face (c_a = +1 along the slab axis)
 };
 
 lbx_status fail(lbx_status s, const char* fmt, ...);

@@ -217,6 +217,17 @@ struct OpsImpl {
     }
     return kind == 1 ? launch_inplace<false, 1>(st, F, p, strm) : launch_inplace<false, 2>(st, F, p, strm);
   }
+  // Slab faces (k_face): one thread per plane cell, face velocity and face.
+  static cudaError_t face(const lbx_state* st, void* A, void* up, void* dn, int pack) {
+    const lbx_scheme& s = st->sch;
+    const unsigned int pc = Lat::D == 3 ? (unsigned int)(s.nx * s.ny) : (unsigned int)s.nx;
+    const dim3 b(128, 1, 1), g((pc + 127) / 128, FaceVel<Lat>::NF, 2);
+    if (pack)
+      k_face<Lat, SysT, St, true><<<g, b, 0, st->stream>>>((S*)A, (S*)up, (S*)dn, st->pc<C>());
+    else
+      k_face<Lat, SysT, St, false><<<g, b, 0, st->stream>>>((S*)A, (S*)up, (S*)dn, st->pc<C>());
+    return cudaGetLastError();
+  }
   // staged kernels keep a fixed 128-column layout: larger blocks cannot launch
   static size_t smem_bytes(int threads) { return (MODE == MODE_SMEM && threads > 128) ? (size_t)1 << 30 : smem(threads); }
 };
@@ -227,7 +238,8 @@ inline Ops make_ops() {
   return Ops{I::step,       I::init,     I::gather,
              I::scatter,    I::reduce,   I::step_fn,
              I::REG,        I::batch_step, I::batch_fn, I::smem_bytes,
-             sizeof(BatchInst<typename St::C>), sizeof(typename St::S), I::step_inplace};
+             sizeof(BatchInst<typename St::C>), sizeof(typename St::S), I::step_inplace,
+             I::face, FaceVel<Lat>::NF};
 }
 
 template <class Lat, template <typename> class SysT>

@@ -55,7 +55,9 @@ class SchemeDesc(C.Structure):
                 ("mms_amp", C.c_double), ("allow_subchar_violation", C.c_int),
                 ("mms_modes", C.POINTER(MmsMode)), ("mms_n_modes", C.c_int), ("mms_mean", C.c_double * 8),
                 ("mms_conserved_only", C.c_int), ("prescribed", C.c_int),
-                ("prescribed_params", C.c_double * 10), ("streaming", C.c_int)]
+                ("prescribed_params", C.c_double * 10), ("streaming", C.c_int),
+                ("slab_origin", C.c_int64), ("slab_planes_global", C.c_int64),
+                ("fp16_scales", C.c_double * 24)]
 
 
 _P = C.c_void_p
@@ -103,6 +105,11 @@ _sig("lbx_load", C.c_int, [_P, C.c_char_p])
 _sig("lbx_state_destroy", None, [_P])
 _sig("lbx_probe_peaks", C.c_int, [C.c_size_t, _P, _D, _D, _D])
 _sig("lbx_conserved_sums_static", C.c_int, [_P, _P, _P, C.c_int, _P])
+_sig("lbx_halo_bytes", C.c_size_t, [_P])
+_sig("lbx_halo_pack", C.c_int, [_P, _P, _P])
+_sig("lbx_halo_unpack", C.c_int, [_P, _P, _P])
+_sig("lbx_state_scales", C.c_int, [_P, _D])
+_sig("lbx_error_stats", C.c_int, [_P, _P, C.c_int, _D])
 _sig("lbx_adjoint", C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, _D, _P, _D])
 _sig("lbx_adjoint_timings", C.c_int, [_D])
 STATIC_REDUCE_MAX_BLOCKS = 512
@@ -185,11 +192,15 @@ class Scheme:
     def __init__(self, system: System, lattice, extent, scaling, f, tau_lb=0.0, tau_R=0.0,
                  g_tau=0.0, precision=FP64, mms=MMS_NONE, mms_amp=0.0,
                  allow_subchar_violation=False, mms_modes=None, mms_mean=None, mms_conserved_only=False,
-                 prescribed=PRESCRIBED_NONE, prescribed_params=(), streaming=STREAM_TWO_BUFFERS):
+                 prescribed=PRESCRIBED_NONE, prescribed_params=(), streaming=STREAM_TWO_BUFFERS,
+                 slab_origin=0, slab_planes_global=0, fp16_scales=None):
         """mms_modes: sequence of (p, (kx, ky[, kz]), amp, phase, sigma, omega, psi) for
         MMS_FOURIER; mms_mean: the primitives' means; prescribed, prescribed_params: the
         HCNSF coefficient fields (lbx_prescribed); streaming: STREAM_TWO_BUFFERS or
-        STREAM_IN_PLACE (one population buffer, lbx_streaming)."""
+        STREAM_IN_PLACE (one population buffer, lbx_streaming); slab_origin,
+        slab_planes_global: this scheme is the slab of a larger grid starting at that
+        global plane of the last axis (extent = the slab's own); fp16_scales: the K storage
+        scales of FP16_SCALED instead of the ones derived at init."""
         d = SchemeDesc()
         d.lattice = lattice
         ext = list(extent) + [1] * (3 - len(extent))
@@ -217,6 +228,9 @@ class Scheme:
         for i, v in enumerate(prescribed_params):
             d.prescribed_params[i] = float(v)
         d.streaming = int(streaming)
+        d.slab_origin, d.slab_planes_global = int(slab_origin), int(slab_planes_global)
+        for i, v in enumerate(fp16_scales or []):
+            d.fp16_scales[i] = float(v)
         h = _P()
         check(_lib.lbx_scheme_derive(system._h, C.byref(d), C.byref(h)))
         self._h = h
@@ -232,6 +246,8 @@ class Scheme:
         self.tau = list(tau[:])
         self.grid = tuple(reversed(self.extent))          # (nz,) ny, nx
         self.buffer_bytes = _lib.lbx_state_buffer_bytes(h)
+        self.halo_bytes = _lib.lbx_halo_bytes(h)
+        self.slab_origin, self.slab_planes_global = int(slab_origin), int(slab_planes_global)
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -306,6 +322,30 @@ class State:
             raise ValueError(f"moments_into needs a contiguous CUDA float64 tensor of shape {shape}")
         check(_lib.lbx_moments(self._h, out.data_ptr(), 1))
         return out
+
+    def halo_pack(self, to_upper, to_lower):
+        """lbx_halo_pack into two CUDA uint8 tensors of scheme.halo_bytes bytes."""
+        check(_lib.lbx_halo_pack(self._h, to_upper.data_ptr(), to_lower.data_ptr()))
+
+    def halo_unpack(self, from_lower, from_upper):
+        """lbx_halo_unpack from the neighbours' face buffers (CUDA tensors)."""
+        check(_lib.lbx_halo_unpack(self._h, from_lower.data_ptr(), from_upper.data_ptr()))
+
+    def scales(self):
+        s = _dbl(self.K)
+        check(_lib.lbx_state_scales(self._h, s))
+        return np.array(s[:])
+
+    def error_stats(self, Q_ref):
+        """lbx_error_stats: [K, 4] float64 (sum e^2, sum ref^2, max|e|, max|ref|)."""
+        out = _dbl(4 * self.K)
+        if isinstance(Q_ref, torch.Tensor) and Q_ref.is_cuda:
+            R = Q_ref.detach().to(torch.float64).contiguous()
+            check(_lib.lbx_error_stats(self._h, R.data_ptr(), 1, out))
+        else:
+            R = _host_f64(Q_ref)
+            check(_lib.lbx_error_stats(self._h, R.ctypes.data, 0, out))
+        return np.array(out[:]).reshape(self.K, 4)
 
     def conserved_sums(self):
         s = _dbl(self.K)

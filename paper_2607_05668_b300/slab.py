@@ -1,0 +1,157 @@
+"""One periodic grid cut into slabs along its last axis (y in 2D, z in 3D): the domain
+decomposition of the collide-and-stream step across processes or GPUs.
+
+Each slab is an lbx state whose scheme carries `slab_origin` / `slab_planes_global`; it
+steps with the periodic wrap of its own planes, and after every step the populations that
+left through its two faces are exchanged with the neighbouring slabs (lbx_halo_pack, a
+transport, lbx_halo_unpack), which makes the streaming of Eq. lbe_update cross the faces.
+This module holds the exchange schedule and the bookkeeping only: the population copies
+into and out of the face buffers run in liblbx.so's kernels, and the transport is
+torch.distributed point-to-point messages (NCCL between GPUs, gloo for host tensors) or,
+for several slabs in one process, device-to-device copies.  Reductions are per slab and
+are combined here in float64 (sums add, maxima take the maximum).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import lbx as L
+
+
+def slab_bounds(planes, nslabs, s):
+    """(origin, count) of slab s when `planes` planes are cut into `nslabs` slabs whose
+    sizes differ by at most one (the first planes % nslabs slabs take one more)."""
+    base, extra = divmod(planes, nslabs)
+    origin = s * base + min(s, extra)
+    return origin, base + (1 if s < extra else 0)
+
+
+def slab_of(Q, origin, count):
+    """The slab's fields: Q [K, (nz,) ny, nx] cut along its first grid axis (the slab axis)."""
+    return Q.narrow(1, origin, count).contiguous()
+
+
+class RingExchange:
+    """The face exchange of `world` slabs in a periodic ring over torch.distributed: slab r's
+    upper neighbour is r + 1 and its lower neighbour r - 1 (mod world).  Every rank posts
+    the same four messages in the same order (send up, receive from below, send down,
+    receive from above), so the sends and receives between two ranks pair up in order even
+    when both neighbours are the same rank (world = 2).  A ring of one slab is the periodic
+    grid itself: its own outgoing faces are its incoming ones."""
+
+    def __init__(self, rank=None, world=None, group=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.group = group
+        self.rank = dist.get_rank(group) if rank is None else rank
+        self.world = dist.get_world_size(group) if world is None else world
+        self.up = (self.rank + 1) % self.world
+        self.down = (self.rank - 1) % self.world
+
+    def _peer(self, r):
+        return r if self.group is None else self.dist.get_global_rank(self.group, r)
+
+    def exchange(self, to_upper, to_lower, from_lower, from_upper):
+        if self.world == 1:
+            from_lower.copy_(to_upper)
+            from_upper.copy_(to_lower)
+            return
+        d = self.dist
+        ops = [d.P2POp(d.isend, to_upper, self._peer(self.up), self.group),
+               d.P2POp(d.irecv, from_lower, self._peer(self.down), self.group),
+               d.P2POp(d.isend, to_lower, self._peer(self.down), self.group),
+               d.P2POp(d.irecv, from_upper, self._peer(self.up), self.group)]
+        for req in d.batch_isend_irecv(ops):
+            req.wait()
+
+    def sum(self, values):
+        """float64 sum over the ring of a per-slab array (host), e.g. conserved sums."""
+        t = torch.as_tensor(np.asarray(values, dtype=np.float64))
+        if self.world > 1:
+            dev = "cuda" if self.dist.get_backend(self.group) == "nccl" else "cpu"
+            t = t.to(dev)
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group)
+        return t.cpu().numpy()
+
+    def max(self, values):
+        t = torch.as_tensor(np.asarray(values, dtype=np.float64))
+        if self.world > 1:
+            dev = "cuda" if self.dist.get_backend(self.group) == "nccl" else "cpu"
+            t = t.to(dev)
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX, group=self.group)
+        return t.cpu().numpy()
+
+
+class Slab:
+    """One slab: an lbx.State and its four face buffers (device, 16-byte aligned)."""
+
+    def __init__(self, scheme: L.Scheme, Q, stream=None, buffers=None, faces=None):
+        """buffers: caller-owned population buffers (lbx_init f_buf_a, f_buf_b); faces:
+        four caller-owned face buffers (to_upper, to_lower, from_lower, from_upper) of at
+        least scheme.halo_bytes bytes; None: allocated here."""
+        self.scheme = scheme
+        self.state = L.State(scheme, Q, stream=stream, buffers=buffers)
+        nb = scheme.halo_bytes
+        if faces is None:
+            faces = [torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(4)]
+        self.to_upper, self.to_lower, self.from_lower, self.from_upper = faces
+
+    def pack(self):
+        self.state.halo_pack(self.to_upper, self.to_lower)
+
+    def unpack(self):
+        self.state.halo_unpack(self.from_lower, self.from_upper)
+
+    def close(self):
+        self.state.close()
+
+
+def step_ring(slab: Slab, ring: RingExchange, n=1):
+    """n steps of one slab of a multi-process run: each step, then its face exchange.  The
+    slab's state must run on torch's current stream (the stream the messages order with)."""
+    for _ in range(int(n)):
+        slab.state.step(1)
+        slab.pack()
+        ring.exchange(slab.to_upper, slab.to_lower, slab.from_lower, slab.from_upper)
+        slab.unpack()
+
+
+def step_local(slabs, n=1):
+    """n steps of several slabs of one grid held by this process (one stream, listed from
+    the lowest plane up): every slab steps, packs its faces, receives its neighbours' faces
+    by device copies, and unpacks them."""
+    m = len(slabs)
+    for _ in range(int(n)):
+        for s in slabs:
+            s.state.step(1)
+            s.pack()
+        for i, s in enumerate(slabs):
+            s.from_lower.copy_(slabs[(i - 1) % m].to_upper)
+            s.from_upper.copy_(slabs[(i + 1) % m].to_lower)
+        for s in slabs:
+            s.unpack()
+
+
+def combine_error_stats(stats):
+    """relative L2 and L-infinity per component (Sec. 4, as lbx_error_norms) from the
+    [K, 4] statistics of every slab (lbx_error_stats) combined over the grid."""
+    st = np.asarray(stats, dtype=np.float64)
+    l2 = np.sqrt(st[:, 0] / np.where(st[:, 1] > 0, st[:, 1], 1.0))
+    li = st[:, 2] / np.where(st[:, 3] > 0, st[:, 3], 1.0)
+    return l2, li
+
+
+def ring_error_norms(slab: Slab, Q_ref_local, ring: RingExchange):
+    """Relative norms of the whole grid from one slab of a multi-process run."""
+    st = slab.state.error_stats(Q_ref_local)
+    s = ring.sum(st[:, :2])
+    m = ring.max(st[:, 2:])
+    return combine_error_stats(np.concatenate([s, m], axis=1))
+
+
+def shared_fp16_scales(scales_per_slab):
+    """The FP16 storage scales slabs of one grid share: the largest of each component's
+    derived scales (s_k = 2^ceil(log2(4 max|f*_k|)) grows with the maximum, so the largest
+    slab scale is the scale of the whole grid)."""
+    return np.max(np.asarray(scales_per_slab, dtype=np.float64), axis=0)

@@ -27,20 +27,25 @@ def nsf_system(case):
                     Q0=case.reference_state())
 
 
-def nsf_scheme(case, precision=L.FP64, lattice=L.D2Q9, tau_lb=0.0, streaming=L.STREAM_TWO_BUFFERS):
-    """Diffusive refinement dt = f dx^2, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
-    return L.Scheme(nsf_system(case), lattice, (case.n, case.n), L.DIFFUSIVE, case.f,
-                    tau_lb=tau_lb, tau_R=case.tau_R, g_tau=case.g_tau, precision=precision, streaming=streaming)
+def nsf_scheme(case, precision=L.FP64, lattice=L.D2Q9, tau_lb=0.0, streaming=L.STREAM_TWO_BUFFERS, extent=None,
+               **slab):
+    """Diffusive refinement dt = f dx^2, tau_LB = 1/2 + tau_R dt, trackers g_tau.  extent and
+    slab (slab_origin, slab_planes_global, fp16_scales): a slab of the grid."""
+    return L.Scheme(nsf_system(case), lattice, extent or (case.n, case.n), L.DIFFUSIVE, case.f,
+                    tau_lb=tau_lb, tau_R=case.tau_R, g_tau=case.g_tau, precision=precision, streaming=streaming,
+                    **slab)
 
 
 def mhd_system(case):
     return L.System(L.MHD_J_TRACK, params=(case.gamma, case.eta), Q0=case.reference_state())
 
 
-def mhd_scheme(case, precision=L.FP32_SHIFT, lattice=L.D3Q19, streaming=L.STREAM_TWO_BUFFERS):
-    """Acoustic refinement dt = f dx, tau_LB = 1/2 + tau_R dt, trackers g_tau."""
-    return L.Scheme(mhd_system(case), lattice, (case.n, case.n, case.n), L.ACOUSTIC, case.f,
-                    tau_R=case.tau_R, g_tau=case.g_tau, precision=precision, streaming=streaming)
+def mhd_scheme(case, precision=L.FP32_SHIFT, lattice=L.D3Q19, streaming=L.STREAM_TWO_BUFFERS, extent=None,
+               **slab):
+    """Acoustic refinement dt = f dx, tau_LB = 1/2 + tau_R dt, trackers g_tau.  extent and
+    slab (slab_origin, slab_planes_global, fp16_scales): a slab of the grid."""
+    return L.Scheme(mhd_system(case), lattice, extent or (case.n, case.n, case.n), L.ACOUSTIC, case.f,
+                    tau_R=case.tau_R, g_tau=case.g_tau, precision=precision, streaming=streaming, **slab)
 
 
 # ------------------------------------------------------------- forced (manufactured) runs
@@ -56,13 +61,13 @@ def table_system(table, params, Q0):
 
 def forced_scheme(table, system, lattice, extent, scaling, f, precision=L.FP64, tau_lb=0.0,
                   tau_R=0.0, g_tau=0.0, conserved_only=False, prescribed=L.PRESCRIBED_NONE,
-                  prescribed_params=(), streaming=L.STREAM_TWO_BUFFERS):
+                  prescribed_params=(), streaming=L.STREAM_TWO_BUFFERS, **slab):
     """A scheme carrying the FOURIER forcing of `table` (.lbx_modes(), .mean): every
     component, or the conserved ones with conserved_only."""
     return L.Scheme(system, lattice, extent, scaling, f, tau_lb=tau_lb, tau_R=tau_R, g_tau=g_tau,
                     precision=precision, mms=L.MMS_FOURIER, mms_modes=table.lbx_modes(),
                     mms_mean=list(table.mean), mms_conserved_only=conserved_only,
-                    prescribed=prescribed, prescribed_params=prescribed_params, streaming=streaming)
+                    prescribed=prescribed, prescribed_params=prescribed_params, streaming=streaming, **slab)
 
 
 # ------------------------------------------------------------- the paper's own cascades
@@ -105,15 +110,17 @@ def hcnsf_prescribed(case):
                                    + (getattr(case, "theta", 0.0), getattr(case, "theta_flux", 0.0)))
 
 
-def hcnsf_scheme(case, precision=L.FP32_SHIFT, forced=False, extent=None, streaming=L.STREAM_TWO_BUFFERS):
+def hcnsf_scheme(case, precision=L.FP32_SHIFT, forced=False, extent=None, streaming=L.STREAM_TWO_BUFFERS,
+                 **slab):
     """The paper's HCNSF recipe on D3Q7: acoustic dt = f dx, tau_LB = 1/2 + tau_R dt, trackers
-    g_tau, prescribed fields of the moving solid; forced: the case's manufactured flow."""
+    g_tau, prescribed fields of the moving solid; forced: the case's manufactured flow.  slab
+    (slab_origin, slab_planes_global, fp16_scales): a z-slab of the grid (extent its own)."""
     kind, pf = hcnsf_prescribed(case)
     ext = extent or (case.n, case.n, case.n)
     if forced:
         return forced_scheme(case.table(), hcnsf_system(case), L.D3Q7, ext, L.ACOUSTIC, case.f,
                              precision=precision, tau_R=case.tau_R, g_tau=case.g_tau,
-                             prescribed=kind, prescribed_params=pf, streaming=streaming)
+                             prescribed=kind, prescribed_params=pf, streaming=streaming, **slab)
     return L.Scheme(hcnsf_system(case), L.D3Q7, ext, L.ACOUSTIC, case.f, tau_R=case.tau_R,
                     g_tau=case.g_tau, precision=precision, prescribed=kind, prescribed_params=pf,
-                    streaming=streaming)
+                    streaming=streaming, **slab)

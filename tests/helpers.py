@@ -69,3 +69,48 @@ def patch_moments(make_scheme, Q, centers, steps, r):
         Qp = sch.moments(sch.run(sch.init(sub), steps))
         out.append(Qp[(slice(None),) + (r,) * len(c)])
     return torch.stack(out, dim=1)                 # [K, n_centres]
+
+
+def _primitives(kind, Q, gamma, R=1.0):
+    """Tracker parents from conserved fields [K, n]: name -> [components, n]."""
+    rho = Q[0]
+    if kind == "nsf":
+        p = (gamma - 1.0) * (Q[3] - 0.5 * (Q[1] ** 2 + Q[2] ** 2) / rho)
+        return {"u": (Q[1] / rho)[None], "v": (Q[2] / rho)[None], "T": (p / (rho * R))[None]}
+    if kind == "mhd":
+        return {"B": Q[4:7]}
+    if kind == "hcnsf":
+        m2 = Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2
+        p = (gamma - 1.0) * (Q[4] - 0.5 * m2 / rho)
+        return {"u": Q[1:4] / rho, "T": (p / rho)[None]}
+    raise ValueError(kind)
+
+
+# tracker component -> parent field, per family (component orders of include/lbx.h)
+TRACKER_PARENT = {
+    "nsf": {4: "u", 5: "u", 6: "v", 7: "v", 8: "T", 9: "T"},
+    "mhd": {8: "B", 9: "B", 10: "B"},
+    "hcnsf": {5: "u", 6: "u", 7: "T", 8: "T", 9: "T", 10: "u", 11: "u", 12: "u", 13: "u"},
+}
+
+
+def parity_scales(kind, Q, Q0, n_cons, dx, g_tau, cs2, gamma, shifted, R=1.0):
+    """Per-component scale a parity error is measured against: the largest magnitude the
+    component's stored populations carry, which sets the rounding unit of its moment.
+    A conserved field's populations are of the size of the field (or, shifted, of its
+    fluctuation about Q0).  A tracker of V has equilibrium populations
+    w_i (G + c_i . (dt/dx) Phi_G / c_s^2) with Phi_G containing -I V / tau_grad, so their size
+    is (dt/dx) |V| / (c_s^2 tau_grad) = |V| / (c_s^2 g_tau dx) (shifted: |V - V0|), far larger
+    than G itself at fine grids; its moment's rounding error scales with that, not with G."""
+    K = Q.shape[0]
+    Qf = Q.reshape(K, -1)
+    q0 = torch.as_tensor(Q0, dtype=F64).reshape(K, 1)
+    scale = ((Qf - q0) if shifted else Qf).abs().amax(1)
+    if K > n_cons:
+        prim = _primitives(kind, Qf, gamma, R)
+        prim0 = _primitives(kind, q0, gamma, R)
+        amp = 1.0 / (cs2 * g_tau * dx)
+        for k, par in TRACKER_PARENT[kind].items():
+            v = prim[par] - prim0[par] if shifted else prim[par]
+            scale[k] = torch.maximum(scale[k], amp * v.abs().max())
+    return scale

@@ -1,0 +1,122 @@
+"""Parity at the configurations' own horizons (the benchmark configurations' step counts).
+
+1. Compressible NSF with primitive trackers on D2Q9 at 256^2 (the configuration's smallest
+   grid), 2000 steps: the FP64, shifted FP32 and scaled FP16 kernels against one CPU FP64
+   oracle run.
+2. 3D resistive MHD with the current tracker on D3Q19 at 32^3 (the configuration's oracle
+   size), 500 steps: shifted FP32 and scaled FP16 against the oracle.
+3. The FP32 adjoint of NSF at 256^2 over 2000 steps with checkpoints every 64 against the
+   FP64 GPU adjoint at the same size (itself matched to the oracle's reverse mode at 32^2 in
+   test_gpu_adjoint.py).
+
+Errors are per field, as max-norm and L2, each divided by the field's population scale
+(tests/helpers.parity_scales): the size of the field (FP64) or of its fluctuation about
+the background Q0 (shifted storage) for conserved fields, and for a tracker of V also
+|V| / (c_s^2 g_tau dx) (shifted: |V - V0| / ...), the size of the V / tau_grad term its
+equilibrium populations carry.  Bounds:
+  FP64   max-norm <= 1e-12: rounding of q populations of that scale per step (q eps ~ 2e-15),
+         damped by the relaxation, stays far below it at these horizons;
+  FP32   max-norm <= 1e-4 and L2 <= 2e-5: the unit roundoff 6e-8 of the stored populations,
+         q of them per moment, accumulated with the same damping (~1e-5 measured at 1024^2);
+  FP16   L2 <= 3e-2 and max-norm <= 1e-1: the stored binary16 values carry 2^-11 of the
+         per-component scale s_k, i.e. up to ~2e-3 of the fluctuation per value; the FP16
+         bound is provisional (the paper has no FP16 results).
+The per-field errors are printed for the record.
+"""
+import json
+
+import pytest
+import torch
+
+import oracle
+import synthetic as syn
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+lbx = pytest.importorskip("paper_2607_05668_b300.lbx")
+from paper_2607_05668_b300 import workloads as W  # noqa: E402
+
+F64 = torch.float64
+BOUNDS = {lbx.FP64: (1e-12, 1e-12), lbx.FP32_SHIFT: (1e-4, 2e-5), lbx.FP16_SCALED: (1e-1, 3e-2)}
+NAMES = {lbx.FP64: "fp64", lbx.FP32_SHIFT: "fp32", lbx.FP16_SCALED: "fp16"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def _errors(got, want, scale):
+    K = got.shape[0]
+    d = (got - want).reshape(K, -1)
+    linf = d.abs().amax(1) / scale
+    l2 = d.pow(2).mean(1).sqrt() / scale
+    return linf, l2
+
+
+def _check(tag, got, want, scale, prec):
+    linf, l2 = _errors(got, want, scale)
+    print(json.dumps({"case": tag, "precision": NAMES[prec], "max": [float(f"{v:.3e}") for v in linf],
+                      "l2": [float(f"{v:.3e}") for v in l2]}))
+    bmax, bl2 = BOUNDS[prec]
+    assert float(linf.max()) <= bmax, linf.tolist()
+    assert float(l2.max()) <= bl2, l2.tolist()
+
+
+@pytest.fixture(scope="module")
+def nsf_256_oracle():
+    case = syn.NsfCase(n=256)
+    Q = syn.nsf_fields(case)
+    och = H.oracle_nsf(case)
+    return case, Q, och.moments(och.run(och.init(Q), 2000))
+
+
+@pytest.mark.parametrize("prec", [lbx.FP64, lbx.FP32_SHIFT, lbx.FP16_SCALED])
+def test_nsf_d2q9_256_over_2000_steps(nsf_256_oracle, prec):
+    case, Q, Qo = nsf_256_oracle
+    st = lbx.State(W.nsf_scheme(case, prec), Q.cuda())
+    st.step(2000)
+    shifted = prec != lbx.FP64
+    scale = H.parity_scales("nsf", Qo, case.reference_state(), 4, case.dx, case.g_tau, 1.0 / 3.0, case.gamma,
+                            shifted)
+    _check("nsf_d2q9_256_2000", st.moments(), Qo, scale, prec)
+
+
+@pytest.fixture(scope="module")
+def mhd_32_oracle():
+    case = syn.MhdCase(n=32)
+    Q = syn.mhd_fields(case)
+    och = H.oracle_mhd(case)
+    return case, Q, och.moments(och.run(och.init(Q), 500))
+
+
+@pytest.mark.parametrize("prec", [lbx.FP64, lbx.FP32_SHIFT, lbx.FP16_SCALED])
+def test_mhd_d3q19_32_over_500_steps(mhd_32_oracle, prec):
+    case, Q, Qo = mhd_32_oracle
+    st = lbx.State(W.mhd_scheme(case, prec), Q.cuda())
+    st.tune()
+    st.step(500)
+    shifted = prec != lbx.FP64
+    scale = H.parity_scales("mhd", Qo, case.reference_state(), 8, case.dx, case.g_tau, 1.0 / 3.0, case.gamma,
+                            shifted)
+    _check("mhd_d3q19_32_500", st.moments(), Qo, scale, prec)
+
+
+def test_fp32_adjoint_at_256_over_2000_steps_against_the_fp64_adjoint():
+    """Config 5 at its own size: the FP32-shift gradient against the FP64 one (same
+    checkpointing).  The gradient of the final misfit carries the FP32 rounding of 2000 forward
+    and 2000 reverse steps; bounds: relative L2 of dJ/dQ0 over each conserved field <= 1e-3,
+    dJ/dtau and J within 1e-4 relative."""
+    n, steps, ck = 256, 2000, 64
+    case = syn.NsfCase(n=n)
+    Q, tgt = syn.nsf_fields(case), syn.density_target(n)
+    J64, g64, t64 = lbx.adjoint(W.nsf_scheme(case, lbx.FP64), Q, steps, ck, tgt)
+    J32, g32, t32 = lbx.adjoint(W.nsf_scheme(case, lbx.FP32_SHIFT), Q, steps, ck, tgt)
+    rel = [float((g32[k] - g64[k]).norm() / g64[k].norm()) for k in range(4)]
+    print(json.dumps({"case": "adjoint_nsf_256_2000_fp32_vs_fp64", "J": [J32, J64], "dJ_dtau": [t32, t64],
+                      "rel_l2_dJ_dQ0_conserved": [float(f"{v:.3e}") for v in rel]}))
+    assert abs(J32 - J64) <= 1e-4 * abs(J64)
+    assert abs(t32 - t64) <= 1e-4 * abs(t64)
+    assert max(rel) <= 1e-3, rel
