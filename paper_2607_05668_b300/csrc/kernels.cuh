@@ -47,6 +47,8 @@ struct KParams {
   T Q0[KMAX];                  // background state (shift reference)
   T F0l[KMAX][3];              // (dt/dx)/c_s^2 * Phi(Q0), used by the unshifted mode
   T omega[KMAX];               // 1 / tau_LB per component
+  T omc[KMAX];                 // 1 - 1 / tau_LB (the float64 update)
+  T ow[KMAX][3];               // omega_k w_i by weight class |c_i|^2 = 0, 1, 2 (float64 update)
   T tau[KMAX];                 // tau_LB per component
   T scale[KMAX];               // float16 storage scale s_k (1 otherwise)
   T inv_scale[KMAX];
@@ -390,6 +392,13 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
 //              every population once.
 constexpr int MODE_REG = 0, MODE_SMEM = 1;
 
+// Blocks of 128 threads per SM that the launch bounds of the unforced register-resident
+// FP16 step ask for (the others ask for 4, i.e. 128 registers).
+#ifndef LBX_REG_BLOCKS_F16
+#define LBX_REG_BLOCKS_F16 5
+#endif
+constexpr int REG_BLOCKS_F16 = LBX_REG_BLOCKS_F16;
+
 // COLS: threads per block of a staged launch (the column stride of its layout).
 template <class Lat, template <typename> class SysT, class St, int COLS = 128>
 struct StepMode {
@@ -407,12 +416,15 @@ struct StepMode {
   // kernels what shared memory lets reside (228 KB per SM), at most `cap` threads
   static constexpr int smem_blocks = value == MODE_SMEM ? (int)(228 * 1024 / smem_bytes) : 0;
   static constexpr int blocks_for(int cap) {
-    return value == MODE_REG ? 4 : (smem_blocks < 1 ? 1 : (smem_blocks * COLS > cap ? cap / COLS : smem_blocks));
+    return value == MODE_REG ? (cap >= 640 ? REG_BLOCKS_F16 : 4)
+                             : (smem_blocks < 1 ? 1 : (smem_blocks * COLS > cap ? cap / COLS : smem_blocks));
   }
   static constexpr int min_blocks = blocks_for(384);
-  // the unforced two-buffer step with FP16 storage: its half-size columns leave room for 640
-  // threads (96 registers, no spills), more warps to cover the memory latency; the forced
-  // and in-place kernels need their registers and keep 384
+  // the unforced two-buffer step with FP16 storage: staged, its half-size columns leave room
+  // for 640 threads (96 registers, no spills); register-resident, the stored pairs take half
+  // the registers of converted values, which leaves room for REG_BLOCKS_F16 blocks of 128.
+  // More warps cover more memory latency; the forced and in-place kernels need their
+  // registers and keep 384 (staged) or 4 blocks (register-resident)
   static constexpr int min_blocks_step = blocks_for(sizeof(typename St::S) == 2 ? 640 : 384);
 };
 
@@ -488,6 +500,32 @@ __device__ __forceinline__ void lds_pair(const __half2* p, float& a, float& b) {
   b = __high2float(h);
 }
 
+// Moment accumulation straight from stored values: a component pair (or the odd component)
+// added to float32/float64 moments.  For binary16 storage, add.rn.f32.f16 converts the stored
+// value exactly and rounds the sum once, which is bitwise the conversion followed by an add,
+// in one instruction instead of two.
+__device__ __forceinline__ void acc_h2(__half2 h, float& a, float& b) {
+  const unsigned int v = *reinterpret_cast<unsigned int*>(&h);
+  asm("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tadd.rn.f32.f16 %0, lo, %0;\n\t"
+      "add.rn.f32.f16 %1, hi, %1;\n\t}"
+      : "+f"(a), "+f"(b)
+      : "r"(v));
+}
+__device__ __forceinline__ void acc_h1(__half h, float& a) {
+  asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(a) : "h"(__half_as_ushort(h)));
+}
+// staged pair / odd value from shared memory into the moments
+__device__ __forceinline__ void acc_lds_pair(const __half2* p, float& a, float& b) {
+  unsigned int v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"((unsigned int)__cvta_generic_to_shared(p)));
+  acc_h2(*reinterpret_cast<__half2*>(&v), a, b);
+}
+__device__ __forceinline__ void acc_lds_odd(const __half* p, float& a) {
+  unsigned short v;
+  asm volatile("ld.shared.b16 %0, [%1];" : "=h"(v) : "r"((unsigned int)__cvta_generic_to_shared(p)));
+  acc_h1(__ushort_as_half(v), a);
+}
+
 __device__ __forceinline__ float to_c(__half h) { return __half2float(h); }
 __device__ __forceinline__ float to_c(float v) { return v; }
 __device__ __forceinline__ double to_c(double v) { return v; }
@@ -504,18 +542,26 @@ __device__ __forceinline__ double to_c(double v) { return v; }
 // and the weight class shares w_i (X_k + tau_k dt S_k), so each population costs one
 // add (moment) and three fused operations.  FP16 storage works in stored units (values
 // divided by s_k): X, phi and dt S are divided by s_k once per component.
+// Float64 runs on the far narrower FP64 pipe, where the operation count sets the speed:
+// there f_out = (1 - w) f + [w w_i (X_k + tau_k dt S_k) + (w w_i) c_i . phi_k] with
+// 1 - w and w w_i per weight class from host tables, two fused operations per population.
+// The rounded coefficient 1 - w on the O(f) term moves sum_i f_out by one float64 rounding
+// (~1e-16 relative) per step, far below what the float64 path is checked to.
 // Moments, flux and source, equilibrium, BGK and store for one node whose populations
 // are available through get_pair(kp, i, a, b) / get_odd(i) (registers or a staged column).
 // Destination of the post-collision populations: DstSelf stores population (k, i) of the
 // node at (k, i, cell); another functor maps (k, i) to an element index (in-place steps).
 struct DstSelf {};
 
+// acc_pair(kp, i, X0, X1) / acc_odd(i, X), when given, add the populations into the moments
+// without get_pair's conversion (binary16 storage: one mixed-precision add per value).
 template <class Lat, template <typename> class SysT, class St, bool FOURIER = false, class GetPair, class GetOdd,
-          class Dst = DstSelf>
+          class Dst = DstSelf, class AccPair = std::nullptr_t, class AccOdd = std::nullptr_t>
 __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, const KParams<typename St::C>& p,
                                             int x, int y, int z, unsigned int cell, long long step, bool active,
                                             GetPair get_pair, GetOdd get_odd,
-                                            const typename St::C* tfac = nullptr, Dst dst = Dst()) {
+                                            const typename St::C* tfac = nullptr, Dst dst = Dst(),
+                                            AccPair acc_pair = nullptr, AccOdd acc_odd = nullptr) {
   using T = typename St::C;
   using V = typename PairOf<typename St::S>::V;
   using Sys = SysT<T>;
@@ -531,14 +577,23 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
   for (int kp = 0; kp < KP; ++kp)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      T a, b;
-      get_pair(kp, i, a, b);
-      X[2 * kp] += a;
-      X[2 * kp + 1] += b;
+      if constexpr (std::is_same<AccPair, std::nullptr_t>::value) {
+        T a, b;
+        get_pair(kp, i, a, b);
+        X[2 * kp] += a;
+        X[2 * kp + 1] += b;
+      } else {
+        acc_pair(kp, i, X[2 * kp], X[2 * kp + 1]);
+      }
     }
   if constexpr (ODD) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) X[K - 1] += get_odd(i);
+    for (int i = 0; i < Q; ++i) {
+      if constexpr (std::is_same<AccOdd, std::nullptr_t>::value)
+        X[K - 1] += get_odd(i);
+      else
+        acc_odd(i, X[K - 1]);
+    }
   }
 
   // a3: primitives, flux and source at the node (physical units)
@@ -574,9 +629,18 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
       if (cd == -1) P -= phd;
     }
     const T Xs = X[k] + p.tau[k] * (p.dt * Src[k] * inv_s);
-    const T wi = weight<Lat, T>(i);
-    const T Fi = fma(T(sg) * wi, P, wi * Xs);
-    return fma(p.omega[k], Fi - f, f);
+    if constexpr (sizeof(T) == 8) {
+      // float64 (the arithmetic-bound kind): (1 - w) f + w F_i with w w_i from the table of
+      // the weight class, two fused operations per population; the products w w_i X's are
+      // shared by the class and the projection P by the opposite pair.
+      const int cls = Lat::c(i, 0) * Lat::c(i, 0) + Lat::c(i, 1) * Lat::c(i, 1) + Lat::c(i, 2) * Lat::c(i, 2);
+      const T owi = p.ow[k][cls];
+      return fma(p.omc[k], f, fma(T(sg) * owi, P, owi * Xs));
+    } else {
+      const T wi = weight<Lat, T>(i);
+      const T Fi = fma(T(sg) * wi, P, wi * Xs);
+      return fma(p.omega[k], Fi - f, f);
+    }
   };
 #pragma unroll
   for (int kp = 0; kp < KP; ++kp)
@@ -629,7 +693,23 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
   // element offsets fit in 32 bits (the host guarantees K q cells < 2^32)
   const unsigned int plane = (unsigned int)p.ncell;
   const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
-  if constexpr (MODE == MODE_REG) {
+  if constexpr (MODE == MODE_REG && sizeof(S) == 2) {
+    // a1: binary16 storage keeps the stored pairs in registers (half the registers of
+    // converted values) and converts them where they are used
+    V hv[KP > 0 ? KP : 1][Q];
+    S ho[ODD ? Q : 1] = {};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const unsigned int src = pi.src<Lat>(i, p.nx, p.ny);
+#pragma unroll
+      for (int kp = 0; kp < KP; ++kp) hv[kp][i] = ldg_pair(reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, plane)));
+      if constexpr (ODD) ho[i] = __ldg(A + eidx<K, Q>(K - 1, i, src, plane));
+    }
+    finish_node<Lat, SysT, St, FOURIER>(
+        B, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { split(hv[kp][i], a, b); },
+        [&](int i) -> T { return to_c(ho[ODD ? i : 0]); }, tfac, DstSelf(),
+        [&](int kp, int i, T& a, T& b) { acc_h2(hv[kp][i], a, b); }, [&](int i, T& a) { acc_h1(ho[ODD ? i : 0], a); });
+  } else if constexpr (MODE == MODE_REG) {
     // a1: pull every population of the node into registers, two components per access
     T fv[K][Q];
 #pragma unroll
@@ -655,9 +735,15 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
     S* colo = reinterpret_cast<S*>(reinterpret_cast<V*>(lbx_smem) + KP * Q * COLS) + threadIdx.x;
     stage_node<Lat, SysT, St, COLS>(A, colv, colo, pi, p);
     stage_wait();
-    finish_node<Lat, SysT, St, FOURIER>(
-        B, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); },
-        [&](int i) -> T { return lds_c(colo + i * COLS); }, tfac);
+    auto get_pair = [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); };
+    auto get_odd = [&](int i) -> T { return lds_c(colo + i * COLS); };
+    if constexpr (sizeof(S) == 2)
+      finish_node<Lat, SysT, St, FOURIER>(
+          B, p, x, y, z, cell, step, true, get_pair, get_odd, tfac, DstSelf(),
+          [&](int kp, int i, T& a, T& b) { acc_lds_pair(colv + (kp * Q + i) * COLS, a, b); },
+          [&](int i, T& a) { acc_lds_odd(colo + i * COLS, a); });
+    else
+      finish_node<Lat, SysT, St, FOURIER>(B, p, x, y, z, cell, step, true, get_pair, get_odd, tfac);
   }
 }
 
@@ -1029,16 +1115,25 @@ __device__ __forceinline__ void bulk_step_body(const typename St::S* A, typename
   }
   const unsigned int cell = ((unsigned int)z * (unsigned int)ny + (unsigned int)y) * (unsigned int)nx + x;
   const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
-  auto get_pair = [&](int kp, int i, T& a, T& b) { lds_pair(rowv + (size_t)(kp * Q + i) * M::ROWP + t + sh(i, EP), a, b); };
-  auto get_odd = [&](int i) -> T { return lds_c(rowo + (size_t)(ODD ? i : 0) * M::ROWO + t + sh(i, EO)); };
+  auto pair_at = [&](int kp, int i) { return rowv + (size_t)(kp * Q + i) * M::ROWP + t + sh(i, EP); };
+  auto odd_at = [&](int i) { return rowo + (size_t)(ODD ? i : 0) * M::ROWO + t + sh(i, EO); };
+  auto get_pair = [&](int kp, int i, T& a, T& b) { lds_pair(pair_at(kp, i), a, b); };
+  auto get_odd = [&](int i) -> T { return lds_c(odd_at(i)); };
+  auto finish = [&](auto dst) {
+    if constexpr (sizeof(S) == 2)
+      finish_node<Lat, SysT, St>(B, p, x, y, z, cell, step, true, get_pair, get_odd, nullptr, dst,
+                                 [&](int kp, int i, T& a, T& b) { acc_lds_pair(pair_at(kp, i), a, b); },
+                                 [&](int i, T& a) { acc_lds_odd(odd_at(i), a); });
+    else
+      finish_node<Lat, SysT, St>(B, p, x, y, z, cell, step, true, get_pair, get_odd, nullptr, dst);
+  };
   if constexpr (KIND == 0) {
-    finish_node<Lat, SysT, St>(B, p, x, y, z, cell, step, true, get_pair, get_odd);
+    finish(DstSelf());
   } else {
-    auto dst = [&](int k, int i) -> unsigned int {
+    finish([&](int k, int i) -> unsigned int {
       return KIND == 1 ? eidx<K, Q>(k, opp<Lat>(i), pi.src<Lat>(opp<Lat>(i), nx, ny), plane)
                        : eidx<K, Q>(k, i, cell, plane);
-    };
-    finish_node<Lat, SysT, St>(B, p, x, y, z, cell, step, true, get_pair, get_odd, nullptr, dst);
+    });
   }
 }
 
@@ -1192,7 +1287,20 @@ __device__ __forceinline__ void step_node_inplace(typename St::S* F, const KPara
     return KIND == 1 ? eidx<K, Q>(k, opp<Lat>(i), pi.src<Lat>(opp<Lat>(i), p.nx, p.ny), plane)
                      : eidx<K, Q>(k, i, cell, plane);
   };
-  if constexpr (MODE == MODE_REG) {
+  if constexpr (MODE == MODE_REG && sizeof(S) == 2) {
+    V hv[KP > 0 ? KP : 1][Q];
+    S ho[ODD ? Q : 1] = {};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+#pragma unroll
+      for (int kp = 0; kp < KP; ++kp) hv[kp][i] = ld_pair_rw(reinterpret_cast<const V*>(F + src(2 * kp, i)));
+      if constexpr (ODD) ho[i] = __ldg(F + src(K - 1, i));
+    }
+    finish_node<Lat, SysT, St, FOURIER>(
+        F, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { split(hv[kp][i], a, b); },
+        [&](int i) -> T { return to_c(ho[ODD ? i : 0]); }, tfac, dst,
+        [&](int kp, int i, T& a, T& b) { acc_h2(hv[kp][i], a, b); }, [&](int i, T& a) { acc_h1(ho[ODD ? i : 0], a); });
+  } else if constexpr (MODE == MODE_REG) {
     T fv[K][Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -1219,9 +1327,15 @@ __device__ __forceinline__ void step_node_inplace(typename St::S* F, const KPara
       if constexpr (ODD) stage(colo + i * COLS, F + src(K - 1, i));
     }
     stage_wait();
-    finish_node<Lat, SysT, St, FOURIER>(
-        F, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); },
-        [&](int i) -> T { return lds_c(colo + i * COLS); }, tfac, dst);
+    auto get_pair = [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); };
+    auto get_odd = [&](int i) -> T { return lds_c(colo + i * COLS); };
+    if constexpr (sizeof(S) == 2)
+      finish_node<Lat, SysT, St, FOURIER>(
+          F, p, x, y, z, cell, step, true, get_pair, get_odd, tfac, dst,
+          [&](int kp, int i, T& a, T& b) { acc_lds_pair(colv + (kp * Q + i) * COLS, a, b); },
+          [&](int i, T& a) { acc_lds_odd(colo + i * COLS, a); });
+    else
+      finish_node<Lat, SysT, St, FOURIER>(F, p, x, y, z, cell, step, true, get_pair, get_odd, tfac, dst);
   }
 }
 

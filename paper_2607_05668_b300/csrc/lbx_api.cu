@@ -598,10 +598,18 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
   background_flux(&s, F0);
   pack_prm(&s, prm);
   const double lc = s.lam / s.cs2;
+  double wcls[3] = {0.0, 0.0, 0.0};         // lattice weight of each class |c|^2 = 0, 1, 2
+  for (int i = 0; i < s.q; ++i) {
+    int c[3];
+    lattice_c(s.d.lattice, i, c);
+    wcls[c[0] * c[0] + c[1] * c[1] + c[2] * c[2]] = lattice_w(s.d.lattice, i);
+  }
   for (int k = 0; k < s.sys.K; ++k) {
     p.Q0[k] = (T)s.sys.Q0[k];
     for (int d = 0; d < 3; ++d) p.F0l[k][d] = (T)(lc * F0[k][d]);
     p.omega[k] = (T)(1.0 / s.tau[k]);
+    p.omc[k] = (T)(1.0 - 1.0 / s.tau[k]);
+    for (int c = 0; c < 3; ++c) p.ow[k][c] = (T)(wcls[c] / s.tau[k]);
     p.tau[k] = (T)s.tau[k];
     p.scale[k] = (T)scale[k];
     p.inv_scale[k] = (T)(1.0 / scale[k]);
