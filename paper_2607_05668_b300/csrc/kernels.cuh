@@ -392,13 +392,6 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
 //              every population once.
 constexpr int MODE_REG = 0, MODE_SMEM = 1;
 
-// Blocks of 128 threads per SM that the launch bounds of the unforced register-resident
-// FP16 step ask for (the others ask for 4, i.e. 128 registers).
-#ifndef LBX_REG_BLOCKS_F16
-#define LBX_REG_BLOCKS_F16 5
-#endif
-constexpr int REG_BLOCKS_F16 = LBX_REG_BLOCKS_F16;
-
 // COLS: threads per block of a staged launch (the column stride of its layout).
 template <class Lat, template <typename> class SysT, class St, int COLS = 128>
 struct StepMode {
@@ -416,15 +409,13 @@ struct StepMode {
   // kernels what shared memory lets reside (228 KB per SM), at most `cap` threads
   static constexpr int smem_blocks = value == MODE_SMEM ? (int)(228 * 1024 / smem_bytes) : 0;
   static constexpr int blocks_for(int cap) {
-    return value == MODE_REG ? (cap >= 640 ? REG_BLOCKS_F16 : 4)
-                             : (smem_blocks < 1 ? 1 : (smem_blocks * COLS > cap ? cap / COLS : smem_blocks));
+    return value == MODE_REG ? 4 : (smem_blocks < 1 ? 1 : (smem_blocks * COLS > cap ? cap / COLS : smem_blocks));
   }
   static constexpr int min_blocks = blocks_for(384);
-  // the unforced two-buffer step with FP16 storage: staged, its half-size columns leave room
-  // for 640 threads (96 registers, no spills); register-resident, the stored pairs take half
-  // the registers of converted values, which leaves room for REG_BLOCKS_F16 blocks of 128.
-  // More warps cover more memory latency; the forced and in-place kernels need their
-  // registers and keep 384 (staged) or 4 blocks (register-resident)
+  // the unforced two-buffer step with FP16 storage: its half-size columns leave room for 640
+  // threads (96 registers, no spills), more warps to cover the memory latency; the forced
+  // and in-place kernels need their registers and keep 384.  (Register-resident FP16 kernels
+  // measured the same at 4, 5 and 6 blocks of 128 per SM: they keep 4.)
   static constexpr int min_blocks_step = blocks_for(sizeof(typename St::S) == 2 ? 640 : 384);
 };
 
@@ -526,6 +517,32 @@ __device__ __forceinline__ void acc_lds_odd(const __half* p, float& a) {
   acc_h1(__ushort_as_half(v), a);
 }
 
+// Paired float32 arithmetic (fma/add/sub .rn.f32x2): two independent IEEE operations in one
+// instruction, each lane rounded exactly as the scalar operation, so results are bitwise
+// those of two scalar instructions.
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) { return *reinterpret_cast<unsigned long long*>(&v); }
+__device__ __forceinline__ float2 bits_f2(unsigned long long b) { return *reinterpret_cast<float2*>(&b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+  return bits_f2(d);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+
 __device__ __forceinline__ float to_c(__half h) { return __half2float(h); }
 __device__ __forceinline__ float to_c(float v) { return v; }
 __device__ __forceinline__ double to_c(double v) { return v; }
@@ -574,18 +591,31 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
 #pragma unroll
   for (int k = 0; k < K; ++k) X[k] = T(0);
 #pragma unroll
-  for (int kp = 0; kp < KP; ++kp)
+  for (int kp = 0; kp < KP; ++kp) {
+    if constexpr (sizeof(T) == 4 && std::is_same<AccPair, std::nullptr_t>::value) {
+      float2 x2 = make_float2(0.f, 0.f);      // the pair's two sums in one paired add per velocity
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if constexpr (std::is_same<AccPair, std::nullptr_t>::value) {
+      for (int i = 0; i < Q; ++i) {
         T a, b;
         get_pair(kp, i, a, b);
-        X[2 * kp] += a;
-        X[2 * kp + 1] += b;
-      } else {
-        acc_pair(kp, i, X[2 * kp], X[2 * kp + 1]);
+        x2 = add2(x2, make_float2(a, b));
+      }
+      X[2 * kp] = x2.x;
+      X[2 * kp + 1] = x2.y;
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if constexpr (std::is_same<AccPair, std::nullptr_t>::value) {
+          T a, b;
+          get_pair(kp, i, a, b);
+          X[2 * kp] += a;
+          X[2 * kp + 1] += b;
+        } else {
+          acc_pair(kp, i, X[2 * kp], X[2 * kp + 1]);
+        }
       }
     }
+  }
   if constexpr (ODD) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -642,15 +672,68 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
       return fma(p.omega[k], Fi - f, f);
     }
   };
+  if constexpr (sizeof(T) == 4) {
+    // float32 arithmetic: the two components of a pair share the paired FP32 pipe (the
+    // same operations as out_of, lane by lane, so bitwise its results); the projection of
+    // a velocity is formed once for it and its opposite, w_i X's once per weight class
 #pragma unroll
-  for (int kp = 0; kp < KP; ++kp)
+    for (int kp = 0; kp < KP; ++kp) {
+      const int ka = 2 * kp, kb = 2 * kp + 1;
+      const T isa = St::SCALE ? p.inv_scale[ka] : T(1), isb = St::SCALE ? p.inv_scale[kb] : T(1);
+      float2 ph2[D];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      T a, b;
-      get_pair(kp, i, a, b);
-      const T oa = out_of(2 * kp, i, a), ob = out_of(2 * kp + 1, i, b);
-      if (active) st_pair(reinterpret_cast<V*>(B + out_idx(2 * kp, i)), oa, ob);
+      for (int d = 0; d < D; ++d)
+        ph2[d] = make_float2((p.lc * Phi[ka][d] + (St::SHIFT ? T(0) : p.F0l[ka][d])) * isa,
+                             (p.lc * Phi[kb][d] + (St::SHIFT ? T(0) : p.F0l[kb][d])) * isb);
+      const float2 xs2 = make_float2(X[ka] + p.tau[ka] * (p.dt * Src[ka] * isa), X[kb] + p.tau[kb] * (p.dt * Src[kb] * isb));
+      const float2 om2 = make_float2(p.omega[ka], p.omega[kb]);
+      float2 wx2[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        int i0 = -1;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          if (i0 < 0 && Lat::c(i, 0) * Lat::c(i, 0) + Lat::c(i, 1) * Lat::c(i, 1) + Lat::c(i, 2) * Lat::c(i, 2) == c) i0 = i;
+        const T wc = i0 < 0 ? T(0) : weight<Lat, T>(i0);
+        wx2[c] = i0 < 0 ? make_float2(0.f, 0.f) : mul2(make_float2(wc, wc), xs2);
+      }
+      float2 P2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int sg = Lat::c(i, 0) != 0 ? Lat::c(i, 0) : (Lat::c(i, 1) != 0 ? Lat::c(i, 1) : Lat::c(i, 2));
+        if (i == 0 || i != opp<Lat>(i) + 1) {   // rest, or the first of an opposite pair
+          bool first = true;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            const int cd = Lat::c(i, d) * sg;
+            if (cd == 0) continue;
+            if (first) P2 = cd == 1 ? ph2[d] : sub2(make_float2(0.f, 0.f), ph2[d]);
+            else P2 = cd == 1 ? add2(P2, ph2[d]) : sub2(P2, ph2[d]);
+            first = false;
+          }
+          if (first) P2 = make_float2(0.f, 0.f);
+        }
+        const int cls = Lat::c(i, 0) * Lat::c(i, 0) + Lat::c(i, 1) * Lat::c(i, 1) + Lat::c(i, 2) * Lat::c(i, 2);
+        const T swi = T(sg) * weight<Lat, T>(i);
+        T a, b;
+        get_pair(kp, i, a, b);
+        const float2 f2 = make_float2(a, b);
+        const float2 F2 = fma2(make_float2(swi, swi), P2, wx2[cls]);
+        const float2 o2 = fma2(om2, sub2(F2, f2), f2);
+        if (active) st_pair(reinterpret_cast<V*>(B + out_idx(ka, i)), o2.x, o2.y);
+      }
     }
+  } else {
+#pragma unroll
+    for (int kp = 0; kp < KP; ++kp)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        T a, b;
+        get_pair(kp, i, a, b);
+        const T oa = out_of(2 * kp, i, a), ob = out_of(2 * kp + 1, i, b);
+        if (active) st_pair(reinterpret_cast<V*>(B + out_idx(2 * kp, i)), oa, ob);
+      }
+  }
   if constexpr (ODD) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -693,23 +776,7 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
   // element offsets fit in 32 bits (the host guarantees K q cells < 2^32)
   const unsigned int plane = (unsigned int)p.ncell;
   const unsigned int cell = ((unsigned int)z * (unsigned int)p.ny + (unsigned int)y) * (unsigned int)p.nx + x;
-  if constexpr (MODE == MODE_REG && sizeof(S) == 2) {
-    // a1: binary16 storage keeps the stored pairs in registers (half the registers of
-    // converted values) and converts them where they are used
-    V hv[KP > 0 ? KP : 1][Q];
-    S ho[ODD ? Q : 1] = {};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const unsigned int src = pi.src<Lat>(i, p.nx, p.ny);
-#pragma unroll
-      for (int kp = 0; kp < KP; ++kp) hv[kp][i] = ldg_pair(reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, plane)));
-      if constexpr (ODD) ho[i] = __ldg(A + eidx<K, Q>(K - 1, i, src, plane));
-    }
-    finish_node<Lat, SysT, St, FOURIER>(
-        B, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { split(hv[kp][i], a, b); },
-        [&](int i) -> T { return to_c(ho[ODD ? i : 0]); }, tfac, DstSelf(),
-        [&](int kp, int i, T& a, T& b) { acc_h2(hv[kp][i], a, b); }, [&](int i, T& a) { acc_h1(ho[ODD ? i : 0], a); });
-  } else if constexpr (MODE == MODE_REG) {
+  if constexpr (MODE == MODE_REG) {
     // a1: pull every population of the node into registers, two components per access
     T fv[K][Q];
 #pragma unroll
@@ -1287,20 +1354,7 @@ __device__ __forceinline__ void step_node_inplace(typename St::S* F, const KPara
     return KIND == 1 ? eidx<K, Q>(k, opp<Lat>(i), pi.src<Lat>(opp<Lat>(i), p.nx, p.ny), plane)
                      : eidx<K, Q>(k, i, cell, plane);
   };
-  if constexpr (MODE == MODE_REG && sizeof(S) == 2) {
-    V hv[KP > 0 ? KP : 1][Q];
-    S ho[ODD ? Q : 1] = {};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-#pragma unroll
-      for (int kp = 0; kp < KP; ++kp) hv[kp][i] = ld_pair_rw(reinterpret_cast<const V*>(F + src(2 * kp, i)));
-      if constexpr (ODD) ho[i] = __ldg(F + src(K - 1, i));
-    }
-    finish_node<Lat, SysT, St, FOURIER>(
-        F, p, x, y, z, cell, step, true, [&](int kp, int i, T& a, T& b) { split(hv[kp][i], a, b); },
-        [&](int i) -> T { return to_c(ho[ODD ? i : 0]); }, tfac, dst,
-        [&](int kp, int i, T& a, T& b) { acc_h2(hv[kp][i], a, b); }, [&](int i, T& a) { acc_h1(ho[ODD ? i : 0], a); });
-  } else if constexpr (MODE == MODE_REG) {
+  if constexpr (MODE == MODE_REG) {
     T fv[K][Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

@@ -107,8 +107,9 @@ def test_mhd_d3q19_32_over_500_steps(mhd_32_oracle, prec):
 def test_fp32_adjoint_at_256_over_2000_steps_against_the_fp64_adjoint():
     """Config 5 at its own size: the FP32-shift gradient against the FP64 one (same
     checkpointing).  The gradient of the final misfit carries the FP32 rounding of 2000 forward
-    and 2000 reverse steps; bounds: relative L2 of dJ/dQ0 over each conserved field <= 1e-3,
-    dJ/dtau and J within 1e-4 relative."""
+    and 2000 reverse steps (about 1e-5 of each, measured 5e-6 to 7e-6 for dJ/dQ0 and 2e-6 for
+    dJ/dtau); bounds: relative L2 of dJ/dQ0 over each conserved field <= 1e-4, dJ/dtau and J
+    within 1e-4 relative."""
     n, steps, ck = 256, 2000, 64
     case = syn.NsfCase(n=n)
     Q, tgt = syn.nsf_fields(case), syn.density_target(n)
@@ -119,4 +120,4 @@ def test_fp32_adjoint_at_256_over_2000_steps_against_the_fp64_adjoint():
                       "rel_l2_dJ_dQ0_conserved": [float(f"{v:.3e}") for v in rel]}))
     assert abs(J32 - J64) <= 1e-4 * abs(J64)
     assert abs(t32 - t64) <= 1e-4 * abs(t64)
-    assert max(rel) <= 1e-3, rel
+    assert max(rel) <= 1e-4, rel
