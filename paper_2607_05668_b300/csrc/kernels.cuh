@@ -392,6 +392,12 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
 //              every population once.
 constexpr int MODE_REG = 0, MODE_SMEM = 1;
 
+// Whether the register-resident float32 kernels use the paired FP32 update as the staged
+// ones do (results are bitwise the same either way; only the instruction stream differs).
+#ifndef LBX_PACKED_REG
+#define LBX_PACKED_REG 1
+#endif
+
 // COLS: threads per block of a staged launch (the column stride of its layout).
 template <class Lat, template <typename> class SysT, class St, int COLS = 128>
 struct StepMode {
@@ -592,7 +598,8 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
   for (int k = 0; k < K; ++k) X[k] = T(0);
 #pragma unroll
   for (int kp = 0; kp < KP; ++kp) {
-    if constexpr (sizeof(T) == 4 && std::is_same<AccPair, std::nullptr_t>::value) {
+    if constexpr (sizeof(T) == 4 && std::is_same<AccPair, std::nullptr_t>::value &&
+                  (StepMode<Lat, SysT, St>::value == MODE_SMEM || LBX_PACKED_REG)) {
       float2 x2 = make_float2(0.f, 0.f);      // the pair's two sums in one paired add per velocity
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -672,7 +679,7 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
       return fma(p.omega[k], Fi - f, f);
     }
   };
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4 && (StepMode<Lat, SysT, St>::value == MODE_SMEM || LBX_PACKED_REG)) {
     // float32 arithmetic: the two components of a pair share the paired FP32 pipe (the
     // same operations as out_of, lane by lane, so bitwise its results); the projection of
     // a velocity is formed once for it and its opposite, w_i X's once per weight class
@@ -1021,7 +1028,8 @@ __global__ void __launch_bounds__(COLS, SplitMode<Lat, SysT, St, COLS>::min_bloc
 // side the shift reaches into so that it starts and ends on 16-byte boundaries, and
 // clamped to the row: the periodic wrap of the two edge nodes (x = 0 pulling along +x,
 // x = nx - 1 along -x) is filled by those threads with plain loads.  All copies complete
-// on one mbarrier; the wait is bounded and a timeout raises p.err and skips the node.
+// on one mbarrier.  Thread 0 alone waits on it, bounded (KParams::wait_ns), while the rest of
+// the block waits at a barrier; a timeout raises p.err and the block skips its nodes.
 // Needs nx % 8 == 0 and 16-byte aligned population buffers (the host checks both).
 template <class Lat, template <typename> class SysT, class St, int COLS>
 struct BulkMode {
@@ -1157,11 +1165,10 @@ __device__ __forceinline__ void bulk_step_body(const typename St::S* A, typename
     if (t == 0) mbar_arrive(bar);
   }
   const int x = x0 + t;
-  if (x >= nx) return;
   const PullIdx pi(x, y, z, nx, ny, nz);
 
   // periodic wrap at the row ends: the slot the clamped copy left empty
-  if (KIND != 2 && (x == 0 || x == nx - 1)) {
+  if (KIND != 2 && x < nx && (x == 0 || x == nx - 1)) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int cx = Lat::c(i, 0);
@@ -1175,11 +1182,20 @@ __device__ __forceinline__ void bulk_step_body(const typename St::S* A, typename
       }
     }
   }
-  if (!mbar_wait(bar, 0, p.wait_ns)) {
-    if (p.err) atomicOr(p.err, 1u);
-    mbar_wait(bar, 0, BULK_WAIT_NS);         // let copies in flight land before leaving
-    return;
+  // one thread waits for the copies; the others wait at the block barrier, where they take
+  // no issue slots from the blocks that compute (the phase completion the waiting thread
+  // observes makes the copied rows visible, and the barrier orders them for the block)
+  volatile int* timed_out = reinterpret_cast<volatile int*>(lbx_smem + 8);
+  if (t == 0) {
+    const bool ok = mbar_wait(bar, 0, p.wait_ns);
+    *timed_out = ok ? 0 : 1;
+    if (!ok) {
+      if (p.err) atomicOr(p.err, 1u);
+      mbar_wait(bar, 0, BULK_WAIT_NS);       // let copies in flight land before leaving
+    }
   }
+  __syncthreads();
+  if (*timed_out || x >= nx) return;
   const unsigned int cell = ((unsigned int)z * (unsigned int)ny + (unsigned int)y) * (unsigned int)nx + x;
   const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
   auto pair_at = [&](int kp, int i) { return rowv + (size_t)(kp * Q + i) * M::ROWP + t + sh(i, EP); };
@@ -1559,13 +1575,48 @@ __global__ void k_gather(const typename St::S* __restrict__ A, const KParams<dou
   const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
   const size_t plane = (size_t)p.ncell;
   const size_t cell = ((size_t)z * p.ny + y) * p.nx + x;
+  if (fout == nullptr) {
+    // moments only: every component pair of a velocity in one vector load, all loads of the
+    // node independent (the same per-component summation order as below)
+    using V = typename PairOf<typename St::S>::V;
+    constexpr int KP = K / 2;
+    double sm[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm[k] = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const unsigned int src = pi.src<Lat>(i, p.nx, p.ny);
+#pragma unroll
+      for (int kp = 0; kp < KP; ++kp) {
+        typename St::C a, b;
+        split(ldg_pair(reinterpret_cast<const V*>(A + eidx<K, Q>(2 * kp, i, src, (unsigned int)plane))), a, b);
+        double va = (double)a, vb = (double)b;
+        if (St::SCALE) {
+          va *= p.scale[2 * kp];
+          vb *= p.scale[2 * kp + 1];
+        }
+        sm[2 * kp] += va;
+        sm[2 * kp + 1] += vb;
+      }
+      if constexpr ((K & 1) != 0) {
+        double v = (double)ld_nc(A + eidx<K, Q>(K - 1, i, src, (unsigned int)plane));
+        if (St::SCALE) v *= p.scale[K - 1];
+        sm[K - 1] += v;
+      }
+    }
+    if (Qout) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) Qout[(size_t)k * plane + cell] = sm[k] + (St::SHIFT ? p.Q0[k] : 0.0);
+    }
+    return;
+  }
   for (int k = 0; k < K; ++k) {
     double s = 0.0;
     for (int i = 0; i < Q; ++i) {
       double v = (double)ld_nc(A + eidx<K, Q>(k, i, pi.src<Lat>(i, p.nx, p.ny), (unsigned int)plane));
       if (St::SCALE) v *= p.scale[k];
       s += v;
-      if (fout) fout[((size_t)k * Q + i) * plane + cell] = v + (St::SHIFT ? feq0[k * Q + i] : 0.0);
+      fout[((size_t)k * Q + i) * plane + cell] = v + (St::SHIFT ? feq0[k * Q + i] : 0.0);
     }
     if (Qout) Qout[(size_t)k * plane + cell] = s + (St::SHIFT ? p.Q0[k] : 0.0);
   }
