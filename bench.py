@@ -776,9 +776,15 @@ def main():
     ap.add_argument("--decomp", choices=["whole", "slab", "replicas"], default=None,
                     help="multi-GPU layout: slab (default for N > 1) = one slab per GPU of one grid with a face "
                          "exchange per step; replicas = independent grids; whole (N = 1 default)")
+    ap.add_argument("--adjoint-only", type=int, default=None, metavar="STEPS",
+                    help="only the config-5 adjoint (NSF D2Q9 256^2 FP32, checkpoints every 64) over STEPS steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.adjoint_only is not None:
+        from paper_2607_05668_b300 import lbx as L, workloads as W
+        print(json.dumps(measure_adjoint(L, W, steps=args.adjoint_only)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

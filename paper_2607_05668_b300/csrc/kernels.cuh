@@ -178,6 +178,15 @@ template <typename T>
 __device__ __forceinline__ void sc_pi(T a, T* s, T* c) { sincospi(a, s, c); }
 template <typename T>
 __device__ __forceinline__ void sc_pi(Dual<T> a, Dual<T>* s, Dual<T>* c) { sincospi_dual(a, s, c); }
+// sin(pi a) alone where the cosine is not needed (dual numbers need both for the derivative)
+__device__ __forceinline__ double s_pi(double a) { return sinpi(a); }
+__device__ __forceinline__ float s_pi(float a) { return sinpif(a); }
+template <typename T>
+__device__ __forceinline__ Dual<T> s_pi(Dual<T> a) {
+  Dual<T> s, c;
+  sincospi_dual(a, &s, &c);
+  return s;
+}
 
 // The time-independent part of the advected-solid fields at x: s_d, c_d and the rotation
 // pattern r (kind 2).
@@ -208,10 +217,7 @@ __device__ __forceinline__ void solid_fields(const KParams<T>& p, const U (&x)[3
   cf[3] = a.r[2] * U(st) + U(p.pf[6]) + U(osc * st) * a.c[1];
   U z[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    U zc;
-    sc_pi(U(T(2)) * (x[d] - a.r[d] * U(st) - U(p.pf[4 + d] * t)), &z[d], &zc);
-  }
+  for (int d = 0; d < 3; ++d) z[d] = s_pi(U(T(2)) * (x[d] - a.r[d] * U(st) - U(p.pf[4 + d] * t)));
   cf[0] = U(p.pf[0]) + U(p.pf[1]) * (z[0] + z[1] + z[2] + U(T(2)) * z[0] * z[1] * z[2]);
 }
 template <typename T, typename U>
@@ -392,11 +398,6 @@ __device__ __noinline__ void mms_fourier(const KParams<T>& p, int x, int y, int 
 //              every population once.
 constexpr int MODE_REG = 0, MODE_SMEM = 1;
 
-// Whether the register-resident float32 kernels use the paired FP32 update as the staged
-// ones do (results are bitwise the same either way; only the instruction stream differs).
-#ifndef LBX_PACKED_REG
-#define LBX_PACKED_REG 1
-#endif
 
 // COLS: threads per block of a staged launch (the column stride of its layout).
 template <class Lat, template <typename> class SysT, class St, int COLS = 128>
@@ -423,6 +424,19 @@ struct StepMode {
   // and in-place kernels need their registers and keep 384.  (Register-resident FP16 kernels
   // measured the same at 4, 5 and 6 blocks of 128 per SM: they keep 4.)
   static constexpr int min_blocks_step = blocks_for(sizeof(typename St::S) == 2 ? 640 : 384);
+};
+
+// Whether finish_node runs the paired FP32 arithmetic (results are bitwise the same either
+// way; only the instruction stream differs).  Measured per kernel kind: it pays in every
+// staged kernel and in register-resident ones of at most 60 populations per node (NSF K = 12
+// on D2Q5 +4 %, Euler FP16 +6 %), and costs in the register-resident NSF on D2Q9 (90
+// populations, -2 %, tighter register pairing) and in the persistent batched kernel (-5 %),
+// which therefore keep the scalar form (NOPACK).
+template <class Lat, template <typename> class SysT, class St, bool NOPACK>
+struct PackedUpdate {
+  static constexpr bool value =
+      sizeof(typename St::C) == 4 && !NOPACK &&
+      (StepMode<Lat, SysT, St>::value == MODE_SMEM || SysT<typename St::C>::K * Lat::Q <= 60);
 };
 
 template <typename S>
@@ -578,8 +592,9 @@ struct DstSelf {};
 
 // acc_pair(kp, i, X0, X1) / acc_odd(i, X), when given, add the populations into the moments
 // without get_pair's conversion (binary16 storage: one mixed-precision add per value).
-template <class Lat, template <typename> class SysT, class St, bool FOURIER = false, class GetPair, class GetOdd,
-          class Dst = DstSelf, class AccPair = std::nullptr_t, class AccOdd = std::nullptr_t>
+template <class Lat, template <typename> class SysT, class St, bool FOURIER = false, bool NOPACK = false,
+          class GetPair, class GetOdd, class Dst = DstSelf, class AccPair = std::nullptr_t,
+          class AccOdd = std::nullptr_t>
 __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, const KParams<typename St::C>& p,
                                             int x, int y, int z, unsigned int cell, long long step, bool active,
                                             GetPair get_pair, GetOdd get_odd,
@@ -599,7 +614,7 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
 #pragma unroll
   for (int kp = 0; kp < KP; ++kp) {
     if constexpr (sizeof(T) == 4 && std::is_same<AccPair, std::nullptr_t>::value &&
-                  (StepMode<Lat, SysT, St>::value == MODE_SMEM || LBX_PACKED_REG)) {
+                  PackedUpdate<Lat, SysT, St, NOPACK>::value) {
       float2 x2 = make_float2(0.f, 0.f);      // the pair's two sums in one paired add per velocity
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -648,11 +663,22 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
   }
 
   // a4 + a5 + a6: equilibrium (Eq. feq), BGK with source (Eq. lbe_update), store
-  auto out_idx = [&](int k, int i) -> unsigned int {
+  // destination of a pair / of the odd component: for the node's own slots a 64-bit base of
+  // the node and one 32-bit multiple of the plane stride per row (the element index of
+  // eidx, split so that the node's offset is added once)
+  typename St::S* const Bc = B + 2u * cell;
+  typename St::S* const Bo = B + 2u * (unsigned int)(KP * Q) * plane + cell;
+  auto pair_dst = [&](int kp, int i) -> V* {
     if constexpr (std::is_same<Dst, DstSelf>::value)
-      return eidx<K, Q>(k, i, cell, plane);
+      return reinterpret_cast<V*>(Bc + (unsigned int)(kp * Q + i) * (2u * plane));
     else
-      return dst(k, i);
+      return reinterpret_cast<V*>(B + dst(2 * kp, i));
+  };
+  auto odd_dst = [&](int i) -> typename St::S* {
+    if constexpr (std::is_same<Dst, DstSelf>::value)
+      return Bo + (unsigned int)i * plane;
+    else
+      return B + dst(K - 1, i);
   };
   auto out_of = [&](int k, int i, T f) -> T {
     const T inv_s = St::SCALE ? p.inv_scale[k] : T(1);
@@ -679,7 +705,7 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
       return fma(p.omega[k], Fi - f, f);
     }
   };
-  if constexpr (sizeof(T) == 4 && (StepMode<Lat, SysT, St>::value == MODE_SMEM || LBX_PACKED_REG)) {
+  if constexpr (sizeof(T) == 4 && PackedUpdate<Lat, SysT, St, NOPACK>::value) {
     // float32 arithmetic: the two components of a pair share the paired FP32 pipe (the
     // same operations as out_of, lane by lane, so bitwise its results); the projection of
     // a velocity is formed once for it and its opposite, w_i X's once per weight class
@@ -727,7 +753,7 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
         const float2 f2 = make_float2(a, b);
         const float2 F2 = fma2(make_float2(swi, swi), P2, wx2[cls]);
         const float2 o2 = fma2(om2, sub2(F2, f2), f2);
-        if (active) st_pair(reinterpret_cast<V*>(B + out_idx(ka, i)), o2.x, o2.y);
+        if (active) st_pair(pair_dst(kp, i), o2.x, o2.y);
       }
     }
   } else {
@@ -738,14 +764,14 @@ __device__ __forceinline__ void finish_node(typename St::S* __restrict__ B, cons
         T a, b;
         get_pair(kp, i, a, b);
         const T oa = out_of(2 * kp, i, a), ob = out_of(2 * kp + 1, i, b);
-        if (active) st_pair(reinterpret_cast<V*>(B + out_idx(2 * kp, i)), oa, ob);
+        if (active) st_pair(pair_dst(kp, i), oa, ob);
       }
   }
   if constexpr (ODD) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const T o = out_of(K - 1, i, get_odd(i));
-      if (active) st_out(B + out_idx(K - 1, i), o);
+      if (active) st_out(odd_dst(i), o);
     }
   }
 }
@@ -770,7 +796,8 @@ __device__ __forceinline__ void stage_node(const typename St::S* __restrict__ A,
   }
 }
 
-template <class Lat, template <typename> class SysT, class St, int MODE, int COLS = 128, bool FOURIER = false>
+template <class Lat, template <typename> class SysT, class St, int MODE, int COLS = 128, bool FOURIER = false,
+          bool NOPACK = false>
 __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, typename St::S* __restrict__ B,
                                           const KParams<typename St::C>& p, int x, int y, int z,
                                           long long step, const typename St::C* tfac = nullptr) {
@@ -795,7 +822,7 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
               fv[2 * kp + 1][i]);
       if constexpr (ODD) fv[K - 1][i] = to_c(__ldg(A + eidx<K, Q>(K - 1, i, src, plane)));
     }
-    finish_node<Lat, SysT, St, FOURIER>(
+    finish_node<Lat, SysT, St, FOURIER, NOPACK>(
         B, p, x, y, z, cell, step, true,
         [&](int kp, int i, T& a, T& b) {
           a = fv[2 * kp][i];
@@ -812,12 +839,12 @@ __device__ __forceinline__ void step_node(const typename St::S* __restrict__ A, 
     auto get_pair = [&](int kp, int i, T& a, T& b) { lds_pair(colv + (kp * Q + i) * COLS, a, b); };
     auto get_odd = [&](int i) -> T { return lds_c(colo + i * COLS); };
     if constexpr (sizeof(S) == 2)
-      finish_node<Lat, SysT, St, FOURIER>(
+      finish_node<Lat, SysT, St, FOURIER, NOPACK>(
           B, p, x, y, z, cell, step, true, get_pair, get_odd, tfac, DstSelf(),
           [&](int kp, int i, T& a, T& b) { acc_lds_pair(colv + (kp * Q + i) * COLS, a, b); },
           [&](int i, T& a) { acc_lds_odd(colo + i * COLS, a); });
     else
-      finish_node<Lat, SysT, St, FOURIER>(B, p, x, y, z, cell, step, true, get_pair, get_odd, tfac);
+      finish_node<Lat, SysT, St, FOURIER, NOPACK>(B, p, x, y, z, cell, step, true, get_pair, get_odd, tfac);
   }
 }
 
@@ -1028,8 +1055,8 @@ __global__ void __launch_bounds__(COLS, SplitMode<Lat, SysT, St, COLS>::min_bloc
 // side the shift reaches into so that it starts and ends on 16-byte boundaries, and
 // clamped to the row: the periodic wrap of the two edge nodes (x = 0 pulling along +x,
 // x = nx - 1 along -x) is filled by those threads with plain loads.  All copies complete
-// on one mbarrier.  Thread 0 alone waits on it, bounded (KParams::wait_ns), while the rest of
-// the block waits at a barrier; a timeout raises p.err and the block skips its nodes.
+// on one mbarrier; every thread's wait is bounded (KParams::wait_ns), and a timeout raises
+// p.err and skips the node.
 // Needs nx % 8 == 0 and 16-byte aligned population buffers (the host checks both).
 template <class Lat, template <typename> class SysT, class St, int COLS>
 struct BulkMode {
@@ -1064,18 +1091,19 @@ __device__ __forceinline__ void mbar_arrive(unsigned int bar) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
 }
 // Suspend until phase `parity` of the barrier completes: tries of at most about a
-// microsecond each while less than `limit_ns` of the global timer has passed, and no
-// more than 2^22 tries; false on timeout.  The time is checked before every try, so a
-// zero limit gives up at once whatever the copies' progress.
+// microsecond each while less than `limit_ns` of the global timer has passed (checked every
+// eighth try), and no more than 2^22 tries; false on timeout.  A zero limit gives up at
+// once, before any try, whatever the copies' progress.
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 __device__ __forceinline__ bool mbar_wait(unsigned int bar, unsigned int parity, unsigned long long limit_ns) {
+  if (limit_ns == 0) return false;
   const unsigned long long t0 = global_ns();
   for (int it = 0; it < (1 << 22); ++it) {
-    if (global_ns() - t0 >= limit_ns) break;
+    if ((it & 7) == 7 && global_ns() - t0 >= limit_ns) break;
     unsigned int done;
     asm volatile(
         "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
@@ -1182,20 +1210,14 @@ __device__ __forceinline__ void bulk_step_body(const typename St::S* A, typename
       }
     }
   }
-  // one thread waits for the copies; the others wait at the block barrier, where they take
-  // no issue slots from the blocks that compute (the phase completion the waiting thread
-  // observes makes the copied rows visible, and the barrier orders them for the block)
-  volatile int* timed_out = reinterpret_cast<volatile int*>(lbx_smem + 8);
-  if (t == 0) {
-    const bool ok = mbar_wait(bar, 0, p.wait_ns);
-    *timed_out = ok ? 0 : 1;
-    if (!ok) {
-      if (p.err) atomicOr(p.err, 1u);
-      mbar_wait(bar, 0, BULK_WAIT_NS);       // let copies in flight land before leaving
-    }
+  // every thread waits for the copies itself (a single waiting thread with the block held at
+  // a barrier measured 2-3 % slower: the release adds latency to every tile)
+  if (x >= nx) return;
+  if (!mbar_wait(bar, 0, p.wait_ns)) {
+    if (p.err) atomicOr(p.err, 1u);
+    mbar_wait(bar, 0, BULK_WAIT_NS);         // let copies in flight land before leaving
+    return;
   }
-  __syncthreads();
-  if (*timed_out || x >= nx) return;
   const unsigned int cell = ((unsigned int)z * (unsigned int)ny + (unsigned int)y) * (unsigned int)nx + x;
   const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
   auto pair_at = [&](int kp, int i) { return rowv + (size_t)(kp * Q + i) * M::ROWP + t + sh(i, EP); };
@@ -1448,7 +1470,7 @@ __global__ void k_step_batch(const typename St::S* __restrict__ A, typename St::
     const int c = tl.y + (int)threadIdx.x;
     if (c < p.ncell) {
       const int y = c / p.nx;
-      step_node<Lat, SysT, St, MODE, 128, FOURIER>(A + off, B + off, p, c - y * p.nx, y, 0, step);
+      step_node<Lat, SysT, St, MODE, 128, FOURIER, true>(A + off, B + off, p, c - y * p.nx, y, 0, step);
     }
   }
 }
