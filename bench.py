@@ -574,11 +574,15 @@ def run_ours(args):
         slab.close()
     else:
         st.close()
-    Qh = Q.contiguous().pin_memory()
-    out_h = torch.empty_like(Qh).pin_memory()
-    out_h.zero_()                 # the result buffer is resident (touched) before the timed region
+    Qh = torch.empty(Q.shape, dtype=Q.dtype, pin_memory=True)
+    Qh.copy_(Q)
+    out_h = torch.empty(Q.shape, dtype=Q.dtype, pin_memory=True)
     Qdev = torch.empty_like(Qh, device="cuda")
     Qout = torch.empty_like(Qdev)
+    # the host buffers are reused from run to run: one untimed copy each way maps them for the
+    # copy engines first (the first copy into a fresh pinned buffer measured about 5x slower)
+    Qdev.copy_(Qh)
+    out_h.copy_(Qdev)
     bufs = [torch.empty(sch.buffer_bytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
     faces = [torch.empty(max(sch.halo_bytes, 16), dtype=torch.uint8, device="cuda") for _ in range(4)]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
@@ -616,7 +620,7 @@ def run_ours(args):
            "h2d_bytes_per_step": Qh.numel() * 8 / args.steps,
            "d2h_bytes_per_step": out_h.numel() * 8 / args.steps,
            "run": f"fields H2D (pinned) + lbx_init + {args.steps} steps + lbx_moments + D2H (pinned), per run; "
-                  "population buffers allocated once outside",
+                  "population buffers and pinned host buffers allocated (and the host buffers used once) outside",
            "split_ms": {"h2d": ev[0].elapsed_time(ev[1]),
                         "init_incl_h2d_and_checks": (t1 - t0) * 1e3,
                         "steps": ev[2].elapsed_time(ev[3]),

@@ -70,6 +70,9 @@ struct KParams {
   int pf_kind;                 // prescribed coefficient fields (HCNSF): 0 none, 1 uniform, 2 advected
   T pf[8];                     // their parameters (see prescribed_fields)
   T pf_src_dt, pf_flux_dt;     // time offsets of the fields inside the source and the flux
+  const T* pf_tab;             // advected solid, float64: sin, cos of 2 pi x_d per node index
+                               // along each axis, [sx nx][cx nx][sy ny][cy ny][sz nz][cz nz];
+                               // null = computed
 };
 
 // Whether the step reads the step index: manufactured forcing or time-dependent prescribed
@@ -206,6 +209,37 @@ __device__ __forceinline__ SolidAt<U> solid_at(const KParams<T>& p, const U (&x)
   a.r[2] = U(rot) * a.c[0] * a.c[1] * a.s[2];
   return a;
 }
+// The same from the host's per-axis tables of sin(2 pi x_d) and cos(2 pi x_d) (global node
+// coordinates of a slab included): two loads per axis instead of a sincospi.
+template <typename T>
+__device__ __forceinline__ SolidAt<T> solid_at_tab(const KParams<T>& p, int x, int y, int z) {
+  SolidAt<T> a;
+  const T* tb = p.pf_tab;
+  const int nx = p.nx, ny = p.ny;
+  a.s[0] = tb[x];
+  a.c[0] = tb[nx + x];
+  a.s[1] = tb[2 * nx + y];
+  a.c[1] = tb[2 * nx + ny + y];
+  a.s[2] = tb[2 * nx + 2 * ny + z];
+  a.c[2] = tb[2 * nx + 2 * ny + p.nz + z];
+  const T rot = p.pf[2];
+  a.r[0] = rot * a.s[0] * a.c[1] * a.c[2];
+  a.r[1] = -rot * a.c[0] * a.s[1] * a.c[2];
+  a.r[2] = rot * a.c[0] * a.c[1] * a.s[2];
+  return a;
+}
+
+// The node's time-independent part: from the tables in float64 (the FP64 pipe bounds that
+// kernel, and the tables save three sincospi per node), computed in float32, where the two
+// table loads per axis measured slower than the sincospi.
+template <typename T>
+__device__ __forceinline__ SolidAt<T> solid_here(const KParams<T>& p, int x, int y, int z, const T (&xc)[3]) {
+  if constexpr (sizeof(T) == 8) {
+    if (p.pf_tab != nullptr) return solid_at_tab(p, x, y, z);
+  }
+  return solid_at(p, xc);
+}
+
 // The fields at time t from the node's time-independent part.
 template <typename T, typename U>
 __device__ __forceinline__ void solid_fields(const KParams<T>& p, const U (&x)[3], const SolidAt<U>& a, T t,
@@ -246,13 +280,16 @@ __device__ __forceinline__ void eval_node(const KParams<T>& p, int x, int y, int
     T cf[NcfOf<Sys>::value];
     if (p.pf_src_dt != p.pf_flux_dt && p.pf_kind == 2) {
       // two time levels of a moving solid: the spatial factors are shared
-      const SolidAt<T> a = solid_at(p, xc);
+      const SolidAt<T> a = solid_here(p, x, y, z, xc);
       T cs[NcfOf<Sys>::value];
       solid_fields(p, xc, a, t + p.pf_flux_dt, cf);
       solid_fields(p, xc, a, t + p.pf_src_dt, cs);
       Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cs);
     } else {
-      prescribed_fields(p, xc, t + p.pf_flux_dt, cf);
+      if (sizeof(T) == 8 && p.pf_kind == 2)
+        solid_fields(p, xc, solid_here(p, x, y, z, xc), t + p.pf_flux_dt, cf);
+      else
+        prescribed_fields(p, xc, t + p.pf_flux_dt, cf);
       Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cf);
     }
   } else {

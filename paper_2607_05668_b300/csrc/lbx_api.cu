@@ -635,6 +635,7 @@ static void fill_params(const lbx_state* st, KParams<T>& p, const double* scale)
     for (int q = 0; q < 8; ++q) p.mms_mean[q] = (T)s.d.mms_mean[q];
   }
   p.pf_kind = s.d.prescribed;
+  p.pf_tab = sizeof(T) == 8 ? (const T*)st->d_pf_tab64 : nullptr;
   for (int i = 0; i < 8; ++i) p.pf[i] = (T)s.d.prescribed_params[i];
   const bool moving = s.d.prescribed == LBX_PRESCRIBED_ADVECTED;
   p.pf_src_dt = (T)(moving ? s.d.prescribed_params[7] * s.dt : 0.0);
@@ -676,6 +677,7 @@ static void free_state(lbx_state* st) {
   cudaFree(st->d_mms_modes);
   cudaFree(st->d_mms_tab64);
   cudaFree(st->d_mms_tab32);
+  cudaFree(st->d_pf_tab64);
   delete st;
 }
 
@@ -807,6 +809,20 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
     CKI(cudaMalloc(&st->d_mms_tab32, sizeof(float) * t.size()));
     CKI(cudaMemcpyAsync(st->d_mms_tab64, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, st->stream));
     CKI(cudaMemcpyAsync(st->d_mms_tab32, tf.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice, st->stream));
+    CKI(cudaStreamSynchronize(st->stream));
+  }
+  if (sch->d.prescribed == LBX_PRESCRIBED_ADVECTED) {
+    // sin and cos of 2 pi x_d at every node index of each axis (global index of a slab), for
+    // the moving solid's time-independent factors in the float64 step
+    const int n3[3] = {sch->nx, sch->ny, sch->nz};
+    const long long o3[3] = {0, sch->sys.D == 2 ? sch->d.slab_origin : 0, sch->sys.D == 3 ? sch->d.slab_origin : 0};
+    std::vector<double> t;
+    for (int a = 0; a < 3; ++a) {
+      for (int i = 0; i < n3[a]; ++i) t.push_back(std::sin(2.0 * M_PI * ((double)(i + o3[a]) * sch->dx)));
+      for (int i = 0; i < n3[a]; ++i) t.push_back(std::cos(2.0 * M_PI * ((double)(i + o3[a]) * sch->dx)));
+    }
+    CKI(cudaMalloc(&st->d_pf_tab64, sizeof(double) * t.size()));
+    CKI(cudaMemcpyAsync(st->d_pf_tab64, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, st->stream));
     CKI(cudaStreamSynchronize(st->stream));
   }
   if (sch->d.mms == LBX_MMS_FOURIER) {

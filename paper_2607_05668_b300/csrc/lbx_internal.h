@@ -87,6 +87,7 @@ struct lbx_state {
   void* d_mms_modes = nullptr;  // lbx::MmsMode[n] of a FOURIER forcing
   double* d_mms_tab64 = nullptr;
   float* d_mms_tab32 = nullptr;
+  double* d_pf_tab64 = nullptr;  // sin/cos tables of the advected solid (HCNSF, float64 step)
   double scale[lbx::KMAX];
   lbx::KParams<double> pd;
   lbx::KParams<float> pf;
