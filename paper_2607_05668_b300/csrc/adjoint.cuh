@@ -8,8 +8,8 @@
 //   m0_k = sum_j w_j mu_{k,j},  m1_k = sum_j w_j c_j mu_{k,j}   (lattice weights w_j),
 // because df^eq_{k',j}/dQ_k = w_j (delta_kk' + (lam/c_s^2) c_j . dPhi_k'/dQ_k) (Eq. feq) and
 // dQ_k/dg_{k,i} = 1 (Eq. moments).  The node-local derivative of the flux and source is
-// taken in forward mode (dual numbers) through the same delta-form system code the step
-// uses, one tangent direction per component.  The relaxation-time derivative per node is
+// taken in forward mode (dual numbers with several tangents) through the same delta-form
+// system code the step uses.  The relaxation-time derivative per node is
 // sum_{k conserved, j} mu_{k,j} (g_{k,j} - f^eq_{k,j}), to be divided by tau^2.
 #pragma once
 
@@ -17,38 +17,59 @@
 
 namespace lbx {
 
-// h_k of the header at one node: w_k m0_k + gradient of
-// F(Q) = sum_k' w_k' lc m1_k' . Phi_k'(Q) + dt m0_k' S_k'(Q) with respect to Q (delta form:
-// Q = Q0 + dQ, the derivative with respect to dQ is the same).
-template <class Lat, template <typename> class SysT, typename T>
-__device__ __forceinline__ void adj_vjp(const KParams<T>& p, const T* dQ, const T (&m0)[SysT<T>::K],
-                                        const T (&m1)[SysT<T>::K][Lat::D], const T* omega, T lc, T dt,
-                                        T (&grad)[SysT<T>::K]) {
-  using D1 = Dual<T>;
-  using SysD = SysT<D1>;
-  constexpr int K = SysD::K, D = Lat::D;
-  D1 pd[NPRM], q0[KMAX];
+// Tangent directions per evaluation of the flux in adj_vjp.  Reverse sweep of NSF D2Q9 at
+// 256^2 over 2000 steps, FP32: 44.2 ms with one tangent per evaluation (K evaluations),
+// 39.4 ms with 2, 37.2 ms with 5, 47.0 ms with all 10 (register pressure).  Capping the
+// registers for 4 or 5 resident blocks spilled and measured slower still, and so did taking
+// the flux values from the first evaluation instead of a separate one (42.4 ms: they stay
+// live across the chunks).
+constexpr int ADJ_TANGENTS = 5;
+
+// One chunk of adj_vjp: tangent directions C0 .. C0+N-1 (compile-time unit seeds) in one
+// evaluation of the system code, then the next chunk.
+template <class Lat, template <typename> class SysT, typename T, int C0>
+__device__ __forceinline__ void adj_vjp_chunk(const KParams<T>& p, const T* dQ, const T (&m0)[SysT<T>::K],
+                                              const T (&m1)[SysT<T>::K][Lat::D], const T* omega, T lc, T dt,
+                                              T (&grad)[SysT<T>::K]) {
+  constexpr int K = SysT<T>::K, D = Lat::D;
+  constexpr int N = K - C0 < ADJ_TANGENTS ? K - C0 : ADJ_TANGENTS;
+  using DN = DualN<T, N>;
+  using SysD = SysT<DN>;
+  DN pd[NPRM], q0[KMAX], x[K];
 #pragma unroll
-  for (int i = 0; i < NPRM; ++i) pd[i] = D1(p.prm[i], T(0));
+  for (int i = 0; i < NPRM; ++i) pd[i] = DN(p.prm[i]);
 #pragma unroll
-  for (int k = 0; k < K; ++k) q0[k] = D1(p.Q0[k], T(0));
-#pragma unroll 1
-  for (int l = 0; l < K; ++l) {
-    D1 x[K];
+  for (int k = 0; k < K; ++k) {
+    q0[k] = DN(p.Q0[k]);
+    x[k] = DN(dQ[k]);
+    if (k >= C0 && k < C0 + N) x[k].d[k - C0] = T(1);
+  }
+  DN Phi[K][D], S[K];
+  SysD::eval(pd, q0, x, Phi, S);
 #pragma unroll
-    for (int k = 0; k < K; ++k) x[k] = D1(dQ[k], k == l ? T(1) : T(0));
-    D1 Phi[K][D], S[K];
-    SysD::eval(pd, q0, x, Phi, S);
+  for (int j = 0; j < N; ++j) {
     T acc = T(0);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       T a = T(0);
 #pragma unroll
-      for (int d = 0; d < D; ++d) a += m1[k][d] * Phi[k][d].d;
-      acc += omega[k] * lc * a + dt * m0[k] * S[k].d;
+      for (int d = 0; d < D; ++d) a += m1[k][d] * Phi[k][d].d[j];
+      acc += omega[k] * lc * a + dt * m0[k] * S[k].d[j];
     }
-    grad[l] = acc;
+    grad[C0 + j] = acc;
   }
+  if constexpr (C0 + N < K) adj_vjp_chunk<Lat, SysT, T, C0 + N>(p, dQ, m0, m1, omega, lc, dt, grad);
+}
+
+// h_k of the header at one node: w_k m0_k + gradient of
+// F(Q) = sum_k' w_k' lc m1_k' . Phi_k'(Q) + dt m0_k' S_k'(Q) with respect to Q (delta form:
+// Q = Q0 + dQ, the derivative with respect to dQ is the same), in forward mode: the K unit
+// directions in chunks of ADJ_TANGENTS tangents per evaluation.
+template <class Lat, template <typename> class SysT, typename T>
+__device__ __forceinline__ void adj_vjp(const KParams<T>& p, const T* dQ, const T (&m0)[SysT<T>::K],
+                                        const T (&m1)[SysT<T>::K][Lat::D], const T* omega, T lc, T dt,
+                                        T (&grad)[SysT<T>::K]) {
+  adj_vjp_chunk<Lat, SysT, T, 0>(p, dQ, m0, m1, omega, lc, dt, grad);
 }
 
 // One reverse step.  An: forward buffer before step n (storage type).  Lnext = Lam_{n+1},
