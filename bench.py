@@ -294,7 +294,7 @@ def launch_desc(L, rep):
     name = {L.STAGE_THREAD: "k_step (per-thread copies)", L.STAGE_BULK: "k_step_bulk (bulk row copies)",
             L.STAGE_PIPE: "k_step_pipe (pipelined per-thread copies)"}
     return {"kernel": name.get(rep["staging"], str(rep["staging"])), "block": rep["block"],
-            "tuned_ms_per_step": rep["ms_per_step"]}
+            "staging": rep["staging"], "tuned_ms_per_step": rep["ms_per_step"]}
 
 
 def measure_grid(L, W, workload, precision, n, steps, warmup, stream, graph=False, inplace=False):
@@ -503,10 +503,11 @@ def run_ours(args):
             state.step(n)
 
     if args.staging is not None:            # a fixed launch shape (profiling one staging)
-        st.set_staging({"thread": L.STAGE_THREAD, "bulk": L.STAGE_BULK, "lanes2": L.STAGE_LANES2,
-                        "pipe": L.STAGE_PIPE}[args.staging])
+        sg = {"thread": L.STAGE_THREAD, "bulk": L.STAGE_BULK, "lanes2": L.STAGE_LANES2,
+              "pipe": L.STAGE_PIPE}[args.staging]
+        st.set_staging(sg)
         st.set_block(args.block)
-        launch = {"kernel": f"staging {args.staging} (fixed)", "block": args.block}
+        launch = {"kernel": f"staging {args.staging} (fixed)", "block": args.block, "staging": sg}
     else:
         launch = launch_desc(L, st.tune())  # staged kernels: fastest launch shape, state unchanged
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -595,8 +596,8 @@ def run_ours(args):
     sl2 = SL.Slab(sch, Qdev, stream=stream, buffers=bufs, faces=faces) if decomp == "slab" else None
     st2 = sl2.state if sl2 else L.State(sch, Qdev, stream=stream, buffers=bufs)   # synchronous (checks)
     t1 = time.perf_counter()
-    if launch.get("tuned_ms_per_step") is not None:
-        st2.set_staging(L.STAGE_BULK if launch["kernel"].startswith("k_step_bulk") else L.STAGE_THREAD)
+    if launch.get("staging") is not None:
+        st2.set_staging(launch["staging"])
         st2.set_block(launch["block"])
     ev[2].record(stream)
     run_steps(args.steps, st2, sl2)
