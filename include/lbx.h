@@ -486,6 +486,62 @@ lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, int64_t n_st
  * results back to the host are outside all four.  -1 before any call. */
 lbx_status lbx_adjoint_timings(double* ms /* [4] host */);
 
+/* ---- step-wise adjoint: the reverse sweep driven by the caller -----------------------
+ * The pieces of lbx_adjoint, for a caller that runs the sweep itself, above all the slabs
+ * of a grid cut across processes (lbx_adjoint refuses slab schemes).  With Lam_n = dJ/dA_n
+ * in the pull layout, the reverse step of Eq. lbe_update is
+ *     Lam_n[k][i][x - c_i] = (1 - w_k) Lam_{n+1}[k][i][x] + h_k(x)
+ * (h: the node-local VJP of the equilibrium's flux and source), a push along -c_i.  An
+ * adjoint buffer holds Lam in the compute type (double for FP64, float for FP32_SHIFT
+ * storage) as [K][q][cells], lbx_adjoint_lam_bytes() bytes.  All calls run on the state's
+ * stream; they need a two-buffer state of an lbx_adjoint family and storage, else
+ * LBX_ERR_UNSUPPORTED.  Device pointers throughout.
+ *
+ * Sweep (one slab; a whole grid is the one-slab case, exchange = local copy):
+ *   forward: before each segment of k steps lbx_adjoint_checkpoint(st, ckpt[c]); step and
+ *            exchange the population faces as usual (lbx_halo_pack / unpack);
+ *   seed:    lbx_adjoint_seed(st, rho_target, lamA, &J_slab); reverse face exchange;
+ *   reverse, per segment from the last: lbx_adjoint_restore(st, ckpt[c], c k); keep the
+ *            segment's states A_m (lbx_adjoint_checkpoint before each forward step with
+ *            its exchange), then for m from the last down: lbx_adjoint_step(st, A_m,
+ *            lam_next, lam_out, tau_acc); reverse face exchange of lam_out; swap;
+ *   finish:  forward face exchange of Lam_0; lbx_adjoint_finish(st, Lam_0, Q_init,
+ *            dJ_dQ0, tau_acc, &dJ_dtau_slab).
+ * J and dJ/dtau add over the slabs; dJ/dQ_init is per node.
+ *
+ * Faces.  lbx_adjoint_halo_pack copies the slots of the upper face (plane P - 1, c_a = +1)
+ * and the lower face (plane 0, c_a = -1) of an adjoint buffer into face buffers of
+ * lbx_adjoint_halo_bytes() bytes ([face velocities][K][plane cells]); _unpack copies them
+ * back into the same slots.  After lbx_adjoint_seed and after every lbx_adjoint_step the
+ * transport is REVERSED: the push of plane 0's nodes has left the lower neighbour's values
+ * in this slab's upper-face slots, so each slab unpacks face_upper = its UPPER neighbour's
+ * packed face_upper and face_lower = its LOWER neighbour's packed face_lower.  Before
+ * lbx_adjoint_finish (whose initial VJP pulls Lam_0 at x - c_i) the transport runs
+ * FORWARD: face_upper = the LOWER neighbour's face_upper, face_lower = the UPPER
+ * neighbour's face_lower. */
+size_t lbx_adjoint_lam_bytes(const lbx_scheme* sch);     /* 0: NULL or no adjoint */
+size_t lbx_adjoint_halo_bytes(const lbx_scheme* sch);    /* 0: NULL or no adjoint */
+/* Copy the current populations (lbx_state_buffer_bytes() bytes, the storage layout as it
+ * is) into dst, asynchronously. */
+lbx_status lbx_adjoint_checkpoint(lbx_state* st, void* dst);
+/* Make src (a checkpoint) the current populations and `step` the state's step count (the
+ * time of time-dependent forcing and prescribed fields); synchronous. */
+lbx_status lbx_adjoint_restore(lbx_state* st, const void* src, int64_t step);
+/* The misfit of the current populations against rho_target ([cells], device) into *J
+ * (host, may be NULL; synchronous reduction) and the seed Lam_N into lam. */
+lbx_status lbx_adjoint_seed(lbx_state* st, const double* rho_target, void* lam, double* J);
+/* One reverse step from the forward populations An (before step n) and Lam_{n+1} =
+ * lam_next into lam_out = Lam_n (every slot written); tau_acc [cells] (float64, zeroed by
+ * the caller before the sweep) accumulates the relaxation-time term.  Asynchronous. */
+lbx_status lbx_adjoint_step(lbx_state* st, const void* An, const void* lam_next, void* lam_out,
+                            double* tau_acc);
+lbx_status lbx_adjoint_halo_pack(lbx_state* st, const void* lam, void* face_upper, void* face_lower);
+lbx_status lbx_adjoint_halo_unpack(lbx_state* st, void* lam, const void* face_upper, const void* face_lower);
+/* dJ/dQ_init [K][cells] (device) from Lam_0 and the initial fields Q_init ([K][cells],
+ * device), and this state's share of dJ/dtau (host) from tau_acc; synchronous. */
+lbx_status lbx_adjoint_finish(lbx_state* st, const void* lam0, const double* Q_init, double* dJ_dQ0,
+                              const double* tau_acc, double* dJ_dtau);
+
 /* ---- conserved sums without any device allocation --------------------------------------
  * The paper has no counterpart to this call; it exists for callers that must not
  * allocate device memory: code recorded into a CUDA graph or running under a latency

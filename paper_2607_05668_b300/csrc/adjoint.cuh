@@ -207,4 +207,36 @@ __global__ void k_adj_init(const typename St::C* __restrict__ L0, const double* 
   for (int k = 0; k < K; ++k) dJdQ[(size_t)k * plane + cell] = m0[k] + grad[k];
 }
 
+// Slab faces of an adjoint buffer L[k][i][cell] (compute type): the slots k_face moves for
+// the populations (upper face: plane P - 1, c_a = +1; lower face: plane 0, c_a = -1).  The
+// reverse step writes Lam_n at x - c_i, so with the local periodic wrap the nodes of plane 0
+// write the lower neighbour's plane P - 1, c_a = +1 values into this slab's upper-face slots
+// and the nodes of plane P - 1 write the upper neighbour's plane 0, c_a = -1 values into the
+// lower-face slots: after each reverse step the transport runs opposite to the forward
+// exchange.  One thread per (plane cell, face velocity j); blockIdx.z selects the face.
+// Face buffer layout: [NF velocities][K][plane cells].
+template <class Lat, template <typename> class SysT, typename T, bool PACK>
+__global__ void k_adj_face(T* __restrict__ L, T* __restrict__ up, T* __restrict__ dn, int nx, int ny, int nz) {
+  constexpr int K = SysT<T>::K, Q = Lat::Q, NF = FaceVel<Lat>::NF;
+  const unsigned int pc = Lat::D == 3 ? (unsigned int)nx * (unsigned int)ny : (unsigned int)nx;
+  const unsigned int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= pc) return;
+  const int j = (int)blockIdx.y, face = (int)blockIdx.z;
+  const int sgn = face == 0 ? 1 : -1;
+  int i = 0;
+#pragma unroll
+  for (int jj = 0; jj < NF; ++jj)
+    if (jj == j) i = FaceVel<Lat>::nth(jj, sgn);
+  const unsigned int planes = Lat::D == 3 ? (unsigned int)nz : (unsigned int)ny;
+  const size_t ncell = (size_t)pc * planes;
+  const size_t cell = (size_t)(face == 0 ? planes - 1u : 0u) * pc + c;
+  T* buf = face == 0 ? up : dn;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    T* g = L + ((size_t)k * Q + i) * ncell + cell;
+    T* h = buf + ((size_t)j * K + k) * pc + c;
+    if (PACK) *h = *g; else *g = *h;
+  }
+}
+
 }  // namespace lbx

@@ -1600,11 +1600,29 @@ __global__ void k_init(const double* __restrict__ Qf, typename St::S* __restrict
   int dxs[3] = {x == p.nx - 1 ? 0 : x + 1, x, x == 0 ? p.nx - 1 : x - 1};
   int dys[3] = {y == p.ny - 1 ? 0 : y + 1, y, y == 0 ? p.ny - 1 : y - 1};
   int dzs[3] = {z == p.nz - 1 ? 0 : z + 1, z, z == 0 ? p.nz - 1 : z - 1};
+#pragma unroll
   for (int k = 0; k < K; ++k) {
+    double lp[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) lp[d] = p.lc * Phi[k][d];
+#pragma unroll
     for (int i = 0; i < Q; ++i) {
+      // c_i . (lam/c_s^2) Phi_k: the components with c_i,d = +1 or -1 added or subtracted
+      // (no products with the lattice's 0 and +-1 entries; the FP64 pipe bounds this kernel)
       double cph = 0.0;
-      for (int d = 0; d < D; ++d) cph += Lat::c(i, d) * Phi[k][d];
-      double v = Lat::w(i) * (dQ[k] + p.lc * cph);          // f^eq(Q) - f^eq(Q0)
+      bool none = true;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (Lat::c(i, d) == 1) {
+          cph = none ? lp[d] : cph + lp[d];
+          none = false;
+        } else if (Lat::c(i, d) == -1) {
+          cph = none ? -lp[d] : cph - lp[d];
+          none = false;
+        }
+      }
+      const double wd = Lat::w(i) * dQ[k];
+      double v = none ? wd : fma(Lat::w(i), cph, wd);     // f^eq(Q) - f^eq(Q0)
       if (!St::SHIFT) v += feq0[k * Q + i];
       if (maxbits) atomicMax(&maxbits[k], (unsigned long long)__double_as_longlong(fabs(v)));
       if (write) {
@@ -1707,6 +1725,7 @@ __global__ void k_scatter(const double* __restrict__ fin, typename St::S* __rest
 //   0  sums:   acc0 = sum Q_k, acc3 = count of non-finite Q_k
 //   1  norms:  acc0 = sum (Q_k - R_k)^2, acc1 = sum R_k^2, acc2 = max|Q_k - R_k|, acc3 = max|R_k|
 //   2  subchar: acc2[0] = max over nodes of the closed-form wave-speed bound
+//   3  modes 0 and 2 in one pass (the checks of lbx_init)
 constexpr int RED_THREADS = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1730,13 +1749,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename St::S* __
   const size_t plane = (size_t)p.ncell;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t cell = (size_t)blockIdx.x * blockDim.x + threadIdx.x; cell < plane; cell += stride) {
-    const int x = (int)(cell % p.nx);
-    const int y = (int)((cell / p.nx) % p.ny);
-    const int z = (int)(cell / ((size_t)p.nx * p.ny));
+    // 32-bit index arithmetic (cell < plane < 2^32)
+    const unsigned int c32 = (unsigned int)cell, row = c32 / (unsigned int)p.nx;
+    const int x = (int)(c32 - row * (unsigned int)p.nx);
+    const int y = (int)(row % (unsigned int)p.ny);
+    const int z = (int)(row / (unsigned int)p.ny);
     const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
     double Qv[K];
+#pragma unroll
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
+#pragma unroll
       for (int i = 0; i < Q; ++i) {
         double v = (double)ld_nc(A + eidx<K, Q>(k, i, pi.src<Lat>(i, p.nx, p.ny), (unsigned int)plane));
         if (St::SCALE) v *= p.scale[k];
@@ -1744,12 +1767,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename St::S* __
       }
       Qv[k] = St::SHIFT ? s : s - p.Q0[k];     // fluctuation
     }
-    if (mode == 0) {
+    if (mode == 0 || mode == 3) {
       for (int k = 0; k < K; ++k) {
         const double q = Qv[k] + p.Q0[k];
         a0[k] += q;
         a3[k] += isfinite(q) ? 0.0 : 1.0;
       }
+      if (mode == 3) a2[0] = fmax(a2[0], Sys::max_speed(p.prm, p.Q0, Qv));
     } else if (mode == 1) {
       for (int k = 0; k < K; ++k) {
         const double r = Qref[(size_t)k * plane + cell];

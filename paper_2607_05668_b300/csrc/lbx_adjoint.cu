@@ -17,6 +17,8 @@ struct AdjOps {
   cudaError_t (*step)(const void* An, const void* Lnext, void* Lout, const lbx_state* st, double* tau_acc);
   cudaError_t (*seed)(const void* AN, const double* target, void* L, const lbx_state* st);
   cudaError_t (*init)(const void* L0, const double* Qinit, const lbx_state* st, double* dJdQ);
+  // slab faces of an adjoint buffer: pack (1) the face slots into up / dn, or unpack (0)
+  cudaError_t (*face)(void* L, void* up, void* dn, int pack, const lbx_state* st);
   size_t lam_bytes;
 };
 
@@ -42,18 +44,28 @@ struct AdjImpl {
     k_adj_init<Lat, SysT, St><<<grid(st->sch), block(st->sch), 0, st->stream>>>((const C*)L0, Qinit, st->pd, dJdQ);
     return cudaGetLastError();
   }
+  static cudaError_t face(void* L, void* up, void* dn, int pack, const lbx_state* st) {
+    const lbx_scheme& s = st->sch;
+    const unsigned int pc = Lat::D == 3 ? (unsigned int)(s.nx * s.ny) : (unsigned int)s.nx;
+    const dim3 b(128, 1, 1), g((pc + 127) / 128, FaceVel<Lat>::NF, 2);
+    if (pack)
+      k_adj_face<Lat, SysT, C, true><<<g, b, 0, st->stream>>>((C*)L, (C*)up, (C*)dn, s.nx, s.ny, s.nz);
+    else
+      k_adj_face<Lat, SysT, C, false><<<g, b, 0, st->stream>>>((C*)L, (C*)up, (C*)dn, s.nx, s.ny, s.nz);
+    return cudaGetLastError();
+  }
 };
 
 template <class Lat, template <typename> class SysT>
 bool pick(int precision, AdjOps* o) {
   if (precision == LBX_FP64) {
     using I = AdjImpl<Lat, SysT, StoreF64>;
-    *o = AdjOps{I::step, I::seed, I::init, sizeof(double)};
+    *o = AdjOps{I::step, I::seed, I::init, I::face, sizeof(double)};
     return true;
   }
   if (precision == LBX_FP32_SHIFT) {
     using I = AdjImpl<Lat, SysT, StoreF32>;
-    *o = AdjOps{I::step, I::seed, I::init, sizeof(float)};
+    *o = AdjOps{I::step, I::seed, I::init, I::face, sizeof(float)};
     return true;
   }
   return false;
@@ -149,7 +161,8 @@ extern "C" lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, i
   if (sch->d.streaming != LBX_STREAM_TWO_BUFFERS)
     return fail(LBX_ERR_UNSUPPORTED, "lbx_adjoint: two-buffer streaming needed");
   if (sch->d.slab_planes_global != 0)
-    return fail(LBX_ERR_UNSUPPORTED, "lbx_adjoint: whole grids only (no slab face exchange in the reverse sweep)");
+    return fail(LBX_ERR_UNSUPPORTED,
+                "lbx_adjoint: whole grids only; slabs run the step-wise calls (lbx_adjoint_seed, _step, _finish)");
   AdjOps adj;
   if (!find_adj(sch->sys.family, sch->d.lattice, sch->d.precision, &adj))
     return fail(LBX_ERR_UNSUPPORTED, "lbx_adjoint: FP64 or FP32_SHIFT storage of a compiled family needed");
@@ -266,3 +279,132 @@ extern "C" lbx_status lbx_adjoint(const lbx_scheme* sch, const double* Q_init, i
   return LBX_OK;
 #undef STEP
 }
+
+// ---------------------------------------------------------- step-wise reverse sweep
+// The pieces of lbx_adjoint for a caller that runs the sweep itself: the slabs of a grid cut
+// across processes, which exchange their faces between the steps (include/lbx.h).
+
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBX_ERR_OOM : LBX_ERR_CUDA, "%s: %s", #call,     \
+                  cudaGetErrorString(e_));                                                           \
+  } while (0)
+
+static lbx_status adj_of(const lbx_state* st, AdjOps* o, const char* who) {
+  if (!st) return fail(LBX_ERR_ARG, "%s: null state", who);
+  if (st->inplace) return fail(LBX_ERR_UNSUPPORTED, "%s: two-buffer streaming needed", who);
+  if (!find_adj(st->sch.sys.family, st->sch.d.lattice, st->sch.d.precision, o))
+    return fail(LBX_ERR_UNSUPPORTED, "%s: FP64 or FP32_SHIFT storage of a compiled family needed", who);
+  return LBX_OK;
+}
+
+extern "C" size_t lbx_adjoint_lam_bytes(const lbx_scheme* sch) {
+  AdjOps o{};
+  if (!sch || !find_adj(sch->sys.family, sch->d.lattice, sch->d.precision, &o)) return 0;
+  return (size_t)sch->sys.K * sch->q * (size_t)sch->ncell * o.lam_bytes;
+}
+
+extern "C" size_t lbx_adjoint_halo_bytes(const lbx_scheme* sch) {
+  AdjOps o{};
+  Ops po{};
+  if (!sch || !find_adj(sch->sys.family, sch->d.lattice, sch->d.precision, &o)) return 0;
+  if (!find_ops(sch->sys.family, sch->d.lattice, sch->d.precision, &po)) return 0;
+  const size_t pc = sch->sys.D == 3 ? (size_t)sch->nx * sch->ny : (size_t)sch->nx;
+  return (size_t)po.face_nf * sch->sys.K * pc * o.lam_bytes;
+}
+
+extern "C" lbx_status lbx_adjoint_checkpoint(lbx_state* st, void* dst) {
+  if (!st || !dst) return fail(LBX_ERR_ARG, "lbx_adjoint_checkpoint: null argument");
+  if (lbx_status s = require_standard_layout(st, "lbx_adjoint_checkpoint")) return s;
+  CK(cudaMemcpyAsync(dst, st->cur(), lbx_state_buffer_bytes(&st->sch), cudaMemcpyDeviceToDevice, st->stream));
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_adjoint_restore(lbx_state* st, const void* src, int64_t step) {
+  if (!st || !src) return fail(LBX_ERR_ARG, "lbx_adjoint_restore: null argument");
+  if (step < 0) return fail(LBX_ERR_ARG, "lbx_adjoint_restore: negative step");
+  if (lbx_status s = require_standard_layout(st, "lbx_adjoint_restore")) return s;
+  CK(cudaMemcpyAsync(st->cur(), src, lbx_state_buffer_bytes(&st->sch), cudaMemcpyDeviceToDevice, st->stream));
+  long long base = (long long)step;
+  CK(cudaMemcpyAsync(st->d_step, &base, sizeof(base), cudaMemcpyHostToDevice, st->stream));
+  CK(cudaStreamSynchronize(st->stream));   // `base` lives on this stack frame
+  st->step = base;
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_adjoint_seed(lbx_state* st, const double* rho_target, void* lam, double* J) {
+  AdjOps adj;
+  if (lbx_status s = adj_of(st, &adj, "lbx_adjoint_seed")) return s;
+  if (!rho_target || !lam) return fail(LBX_ERR_ARG, "lbx_adjoint_seed: null argument");
+  const int K = st->sch.sys.K;
+  const size_t ncell = (size_t)st->sch.ncell;
+  double* d_Qref = nullptr;
+  CK(cudaMalloc((void**)&d_Qref, sizeof(double) * K * ncell));
+  cudaError_t e = cudaMemsetAsync(d_Qref, 0, sizeof(double) * K * ncell, st->stream);
+  if (!e) e = cudaMemcpyAsync(d_Qref, rho_target, sizeof(double) * ncell, cudaMemcpyDeviceToDevice, st->stream);
+  if (e) {
+    cudaFree(d_Qref);
+    return fail(LBX_ERR_CUDA, "lbx_adjoint_seed: %s", cudaGetErrorString(e));
+  }
+  double out[KMAX * 4];
+  lbx_status rc = run_reduce(st, d_Qref, 1, out);    // synchronous
+  cudaFree(d_Qref);
+  if (rc) return rc;
+  if (J) *J = 0.5 * out[0];
+  if (cudaError_t e2 = adj.seed(st->cur(), rho_target, lam, st))
+    return fail(LBX_ERR_CUDA, "lbx_adjoint_seed: %s", cudaGetErrorString(e2));
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_adjoint_step(lbx_state* st, const void* An, const void* lam_next, void* lam_out,
+                                       double* tau_acc) {
+  AdjOps adj;
+  if (lbx_status s = adj_of(st, &adj, "lbx_adjoint_step")) return s;
+  if (!An || !lam_next || !lam_out || !tau_acc) return fail(LBX_ERR_ARG, "lbx_adjoint_step: null argument");
+  if (lam_next == lam_out) return fail(LBX_ERR_ARG, "lbx_adjoint_step: lam_next and lam_out must differ");
+  if (cudaError_t e = adj.step(An, lam_next, lam_out, st, tau_acc))
+    return fail(LBX_ERR_CUDA, "lbx_adjoint_step: %s", cudaGetErrorString(e));
+  return LBX_OK;
+}
+
+static lbx_status adj_face_call(lbx_state* st, void* lam, void* upper, void* lower, int pack, const char* who) {
+  AdjOps adj;
+  if (lbx_status s = adj_of(st, &adj, who)) return s;
+  if (!lam || !upper || !lower) return fail(LBX_ERR_ARG, "%s: null argument", who);
+  if (cudaError_t e = adj.face(lam, upper, lower, pack, st)) return fail(LBX_ERR_CUDA, "%s: %s", who, cudaGetErrorString(e));
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_adjoint_halo_pack(lbx_state* st, const void* lam, void* face_upper, void* face_lower) {
+  return adj_face_call(st, const_cast<void*>(lam), face_upper, face_lower, 1, "lbx_adjoint_halo_pack");
+}
+
+extern "C" lbx_status lbx_adjoint_halo_unpack(lbx_state* st, void* lam, const void* face_upper, const void* face_lower) {
+  return adj_face_call(st, lam, const_cast<void*>(face_upper), const_cast<void*>(face_lower), 0,
+                       "lbx_adjoint_halo_unpack");
+}
+
+extern "C" lbx_status lbx_adjoint_finish(lbx_state* st, const void* lam0, const double* Q_init, double* dJ_dQ0,
+                                         const double* tau_acc, double* dJ_dtau) {
+  AdjOps adj;
+  if (lbx_status s = adj_of(st, &adj, "lbx_adjoint_finish")) return s;
+  if (!lam0 || !Q_init || !dJ_dQ0 || !tau_acc) return fail(LBX_ERR_ARG, "lbx_adjoint_finish: null argument");
+  if (cudaError_t e = adj.init(lam0, Q_init, st, dJ_dQ0))
+    return fail(LBX_ERR_CUDA, "lbx_adjoint_finish: %s", cudaGetErrorString(e));
+  double* d_sum = nullptr;
+  CK(cudaMalloc((void**)&d_sum, sizeof(double)));
+  k_sum_f64<<<1, 256, 0, st->stream>>>(tau_acc, (long long)st->sch.ncell, d_sum);
+  cudaError_t e = cudaGetLastError();
+  double tsum = 0.0;
+  if (!e) e = cudaMemcpyAsync(&tsum, d_sum, sizeof(double), cudaMemcpyDeviceToHost, st->stream);
+  if (!e) e = cudaStreamSynchronize(st->stream);
+  cudaFree(d_sum);
+  if (e) return fail(LBX_ERR_CUDA, "lbx_adjoint_finish: %s", cudaGetErrorString(e));
+  const double tau = st->sch.tau[0];
+  if (dJ_dtau) *dJ_dtau = tsum / (tau * tau);
+  return LBX_OK;
+}
+
+#undef CK

@@ -889,16 +889,15 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
   }
   st->cur_a = true;
   {
+    // finite check and, unless waived, the sub-characteristic bound: one pass over the
+    // populations (reduction mode 3)
+    const bool subchar = !sch->d.allow_subchar_violation;
     double sums[KMAX * 4];
-    if ((rc = run_reduce(st, nullptr, 0, sums))) return bail(rc);
+    if ((rc = run_reduce(st, nullptr, subchar ? 3 : 0, sums))) return bail(rc);
     for (int k = 0; k < K; ++k)
       if (sums[4 * k + 3] != 0.0) return bail(fail(LBX_ERR_NONFINITE, "lbx_init: non-finite initial field"));
-  }
-  if (!sch->d.allow_subchar_violation) {
-    double ms;
-    int ok;
-    if ((rc = lbx_subchar_check(st, &ms, nullptr, nullptr, &ok))) return bail(rc);
-    if (!ok)
+    const double ms = sch->lam * sums[2];
+    if (subchar && !(ms <= std::sqrt(sch->cs2)))
       return bail(fail(LBX_ERR_SUBCHAR, "lbx_init: sub-characteristic bound violated: (dt/dx) max speed %.6g > c_s %.6g",
                        ms, std::sqrt(sch->cs2)));
   }

@@ -112,6 +112,15 @@ _sig("lbx_state_scales", C.c_int, [_P, _D])
 _sig("lbx_error_stats", C.c_int, [_P, _P, C.c_int, _D])
 _sig("lbx_adjoint", C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, _D, _P, _D])
 _sig("lbx_adjoint_timings", C.c_int, [_D])
+_sig("lbx_adjoint_lam_bytes", C.c_size_t, [_P])
+_sig("lbx_adjoint_halo_bytes", C.c_size_t, [_P])
+_sig("lbx_adjoint_checkpoint", C.c_int, [_P, _P])
+_sig("lbx_adjoint_restore", C.c_int, [_P, _P, C.c_int64])
+_sig("lbx_adjoint_seed", C.c_int, [_P, _P, _P, _D])
+_sig("lbx_adjoint_step", C.c_int, [_P, _P, _P, _P, _P])
+_sig("lbx_adjoint_halo_pack", C.c_int, [_P, _P, _P, _P])
+_sig("lbx_adjoint_halo_unpack", C.c_int, [_P, _P, _P, _P])
+_sig("lbx_adjoint_finish", C.c_int, [_P, _P, _P, _P, _P, _D])
 STATIC_REDUCE_MAX_BLOCKS = 512
 
 
@@ -247,6 +256,8 @@ class Scheme:
         self.grid = tuple(reversed(self.extent))          # (nz,) ny, nx
         self.buffer_bytes = _lib.lbx_state_buffer_bytes(h)
         self.halo_bytes = _lib.lbx_halo_bytes(h)
+        self.adjoint_lam_bytes = _lib.lbx_adjoint_lam_bytes(h)
+        self.adjoint_halo_bytes = _lib.lbx_adjoint_halo_bytes(h)
         self.slab_origin, self.slab_planes_global = int(slab_origin), int(slab_planes_global)
 
     def __del__(self):
@@ -390,6 +401,38 @@ class State:
 
     def populations_ptr(self):
         return _lib.lbx_state_populations(self._h)
+
+    # step-wise adjoint (include/lbx.h): device tensors throughout
+    def adjoint_checkpoint(self, dst):
+        """lbx_adjoint_checkpoint: the current populations' bytes into a uint8 CUDA tensor."""
+        check(_lib.lbx_adjoint_checkpoint(self._h, dst.data_ptr()))
+
+    def adjoint_restore(self, src, step):
+        check(_lib.lbx_adjoint_restore(self._h, src.data_ptr(), int(step)))
+
+    def adjoint_seed(self, rho_target, lam):
+        """lbx_adjoint_seed: returns this state's misfit J; rho_target float64 CUDA [cells]."""
+        J = C.c_double()
+        check(_lib.lbx_adjoint_seed(self._h, rho_target.data_ptr(), lam.data_ptr(), C.byref(J)))
+        return J.value
+
+    def adjoint_step(self, An, lam_next, lam_out, tau_acc):
+        An_ptr = An if isinstance(An, int) else An.data_ptr()
+        check(_lib.lbx_adjoint_step(self._h, An_ptr, lam_next.data_ptr(), lam_out.data_ptr(), tau_acc.data_ptr()))
+
+    def adjoint_halo_pack(self, lam, face_upper, face_lower):
+        check(_lib.lbx_adjoint_halo_pack(self._h, lam.data_ptr(), face_upper.data_ptr(), face_lower.data_ptr()))
+
+    def adjoint_halo_unpack(self, lam, face_upper, face_lower):
+        check(_lib.lbx_adjoint_halo_unpack(self._h, lam.data_ptr(), face_upper.data_ptr(), face_lower.data_ptr()))
+
+    def adjoint_finish(self, lam0, Q_init, dJ_dQ0, tau_acc):
+        """lbx_adjoint_finish: dJ/dQ_init into dJ_dQ0 (float64 CUDA [K, cells]); returns this
+        state's share of dJ/dtau."""
+        gt = C.c_double()
+        check(_lib.lbx_adjoint_finish(self._h, lam0.data_ptr(), Q_init.data_ptr(), dJ_dQ0.data_ptr(),
+                                      tau_acc.data_ptr(), C.byref(gt)))
+        return gt.value
 
     def synchronize(self):
         check(_lib.lbx_synchronize(self._h))

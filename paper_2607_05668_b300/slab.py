@@ -155,3 +155,110 @@ def shared_fp16_scales(scales_per_slab):
     derived scales (s_k = 2^ceil(log2(4 max|f*_k|)) grows with the maximum, so the largest
     slab scale is the scale of the whole grid)."""
     return np.max(np.asarray(scales_per_slab, dtype=np.float64), axis=0)
+
+
+# --------------------------------------------------------------------- adjoint sweep
+def _adj_faces(scheme):
+    nb = max(scheme.adjoint_halo_bytes, 16)
+    return [torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(4)]
+
+
+def _adj_exchange(slabs, lams, faces, ring, reverse):
+    """Face exchange of the adjoint buffers lams[s] (lbx_adjoint_halo_pack, a transport,
+    lbx_adjoint_halo_unpack).  reverse (after a seed or a reverse step): each slab takes its
+    upper neighbour's upper face and its lower neighbour's lower face; forward (before the
+    initial VJP, which pulls): its lower neighbour's upper face and its upper neighbour's
+    lower face.  faces[s] = [packed upper, packed lower, received upper, received lower]."""
+    for s, lam, f in zip(slabs, lams, faces):
+        s.state.adjoint_halo_pack(lam, f[0], f[1])
+    if ring is not None:
+        pu, pl, ru, rl = faces[0]
+        if reverse:     # upper face down, lower face up
+            ring.exchange(pl, pu, rl, ru)
+        else:           # as the populations: upper face up, lower face down
+            ring.exchange(pu, pl, ru, rl)
+    else:
+        m = len(slabs)
+        for i, f in enumerate(faces):
+            up, dn = faces[(i + 1) % m], faces[(i - 1) % m]
+            f[2].copy_(up[0] if reverse else dn[0])
+            f[3].copy_(dn[1] if reverse else up[1])
+    for s, lam, f in zip(slabs, lams, faces):
+        s.state.adjoint_halo_unpack(lam, f[2], f[3])
+
+
+def slab_adjoint(slabs, Q_init, rho_target, n_steps, ckpt_every, ring=None):
+    """Gradient of J = 1/2 sum_x (rho(x, T) - rho*(x))^2 over a grid cut into slabs, by the
+    step-wise adjoint of liblbx.so (the reverse of Eq. lbe_update, face exchanges reversed).
+
+    slabs: this process's slabs of the grid, freshly initialised from Q_init and listed from
+    the lowest plane up (with `ring`, exactly one slab per process).  Q_init[s], rho_target[s]:
+    float64 CUDA tensors [K, cells] and [cells] of slab s.  Every step of the forward sweep,
+    of the recomputation and of the reverse sweep is followed by its face exchange; the
+    forward state is checkpointed every ckpt_every steps and each segment is recomputed
+    before its reverse steps, as lbx_adjoint does for a whole grid.
+    Returns (J, [dJ/dQ_init per slab, float64 CUDA [K, cells]], dJ/dtau), J and dJ/dtau
+    summed over the grid."""
+    slabs = list(slabs)
+    if ring is not None and len(slabs) != 1:
+        raise ValueError("slab_adjoint: one slab per process with a ring")
+    sch = slabs[0].scheme
+    n_steps, ckpt_every = int(n_steps), int(ckpt_every)
+    if n_steps < 0 or ckpt_every < 1:
+        raise ValueError("slab_adjoint: n_steps >= 0 and ckpt_every >= 1")
+    if sch.adjoint_lam_bytes == 0:
+        raise L.LbxError(-1, "slab_adjoint: no adjoint for this family and storage")
+    k = min(ckpt_every, max(n_steps, 1))
+    nck = 0 if n_steps == 0 else -(-n_steps // k)
+
+    def fwd_step():
+        if ring is not None:
+            step_ring(slabs[0], ring, 1)
+        else:
+            step_local(slabs, 1)
+
+    def buf(nbytes):
+        return torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+
+    ckpt = [[buf(s.scheme.buffer_bytes) for _ in range(nck)] for s in slabs]
+    seg = [[buf(s.scheme.buffer_bytes) for _ in range(k)] for s in slabs]
+    lam = [[buf(s.scheme.adjoint_lam_bytes) for _ in range(2)] for s in slabs]
+    ncell = [int(np.prod(s.scheme.grid)) for s in slabs]
+    tau = [torch.zeros(n, dtype=torch.float64, device="cuda") for n in ncell]
+    faces = [_adj_faces(s.scheme) for s in slabs]
+
+    # forward sweep, keeping the state at the start of every segment
+    for c in range(nck):
+        for s, ck in zip(slabs, ckpt):
+            s.state.adjoint_checkpoint(ck[c])
+        for _ in range(min(k, n_steps - c * k)):
+            fwd_step()
+    # misfit and seed Lam_N
+    J = np.array([sum(s.state.adjoint_seed(r, lm[0]) for s, r, lm in zip(slabs, rho_target, lam))])
+    cur = 0
+    _adj_exchange(slabs, [lm[cur] for lm in lam], faces, ring, reverse=True)
+    # reverse sweep: recompute each segment from its checkpoint, then step the adjoint back
+    for c in range(nck - 1, -1, -1):
+        ln = min(k, n_steps - c * k)
+        for s, ck in zip(slabs, ckpt):
+            s.state.adjoint_restore(ck[c], c * k)
+        for j in range(ln):
+            for s, sg in zip(slabs, seg):
+                s.state.adjoint_checkpoint(sg[j])
+            if j + 1 < ln:
+                fwd_step()
+        for j in range(ln - 1, -1, -1):
+            for s, sg, lm, t in zip(slabs, seg, lam, tau):
+                s.state.adjoint_step(sg[j], lm[cur], lm[1 - cur], t)
+            cur = 1 - cur
+            _adj_exchange(slabs, [lm[cur] for lm in lam], faces, ring, reverse=True)
+    # the initial VJP pulls Lam_0 across the faces: forward exchange first
+    _adj_exchange(slabs, [lm[cur] for lm in lam], faces, ring, reverse=False)
+    grads, gt = [], np.zeros(1)
+    for s, lm, q, t, n in zip(slabs, lam, Q_init, tau, ncell):
+        g = torch.empty((s.scheme.system.K, n), dtype=torch.float64, device="cuda")
+        gt[0] += s.state.adjoint_finish(lm[cur], q, g, t)
+        grads.append(g)
+    if ring is not None:
+        J, gt = ring.sum(J), ring.sum(gt)
+    return float(J[0]), grads, float(gt[0])

@@ -222,12 +222,12 @@ def nsf_fields(case: NsfCase):
     return torch.stack(comps)
 
 
-def density_target(n: int, seed: int = 1, amp_max: float = 0.05):
-    """rho*(x) = 1 + seeded Fourier field (<= amp_max per mode), for the misfit
-    J = 1/2 sum_x (rho(x, T) - rho*(x))^2."""
+def density_target(n: int, seed: int = 1, amp_max: float = 0.05, dim: int = 2):
+    """rho*(x) = 1 + seeded Fourier field (<= amp_max per mode) on the n^dim grid, for the
+    misfit J = 1/2 sum_x (rho(x, T) - rho*(x))^2."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    fld = fourier_field(rng, 1.0, 4, 3, amp_max)
-    return fld.value(coords((n, n)))
+    fld = fourier_field(rng, 1.0, 4, 3, amp_max, dim=dim)
+    return fld.value(coords((n,) * dim))
 
 
 # --------------------------------------------------------------------------------------

@@ -157,3 +157,111 @@ def test_ring_exchange_reproduces_the_whole_grid(tmp_path, world):
     sums = [np.load(tmp_path / f"sum{r}.npy") for r in range(world)]
     assert all(np.array_equal(s, sums[0]) for s in sums)
     np.testing.assert_allclose(sums[0], _whole()[-1].sum(axis=(1, 2, 3)), rtol=1e-12)
+
+
+# --------------------------------------------- the adjoint's reversed exchange schedule
+# The reverse step of the library's adjoint pushes: node x writes Lam_n[k][i][x - c_i].  The
+# model below stands in for it (a node-local map of the incoming adjoint, then the push with
+# the slab's own periodic wrap); the product's slab._adj_exchange packs, exchanges and
+# unpacks the adjoint face slots (the slots k_adj_face copies) between the steps.  The slabs'
+# adjoint arrays must equal the whole grid's bitwise after every reverse step, and after
+# the forward exchange a pull (the initial VJP's access pattern) must match too.
+class _FakeAdjState:
+    """The adjoint face copies of lbx_adjoint_halo_pack / _unpack on host arrays."""
+
+    def adjoint_halo_pack(self, lam, face_upper, face_lower):
+        face_upper.copy_(torch.from_numpy(lam[:, UP, -1, :].copy()))
+        face_lower.copy_(torch.from_numpy(lam[:, DN, 0, :].copy()))
+
+    def adjoint_halo_unpack(self, lam, face_upper, face_lower):
+        lam[:, UP, -1, :] = face_upper.numpy()
+        lam[:, DN, 0, :] = face_lower.numpy()
+
+
+class _FakeSlab:
+    def __init__(self):
+        self.state = _FakeAdjState()
+
+
+def _push(lam):
+    """Lam_n[k, i, x - c_i] = g(Lam_{n+1})[k, i, x] (periodic), g node-local."""
+    g = 0.7 * lam + 0.1 * lam.mean(axis=1, keepdims=True) + 0.02 * np.roll(lam, 1, axis=0)
+    out = np.empty_like(g)
+    for i, (cx, cy) in enumerate(D2Q9):
+        out[:, i] = np.roll(np.roll(g[:, i], -cy, axis=1), -cx, axis=2)
+    return out
+
+
+def _adj_whole():
+    lam = np.random.default_rng(7).standard_normal((K, 9, NY, NX))
+    out = [lam]
+    for _ in range(STEPS):
+        lam = _push(lam)
+        out.append(lam)
+    return out
+
+
+def _adj_rank_main(rank, world, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ring = SL.RingExchange()
+        o, c = SL.slab_bounds(NY, world, rank)
+        whole = _adj_whole()
+        lam = whole[0][:, :, o:o + c, :].copy()
+        shape = (K, len(UP), NX)
+        faces = [[torch.empty(shape, dtype=torch.float64) for _ in range(4)]]
+        slabs = [_FakeSlab()]
+        for n in range(STEPS):
+            lam = _push(lam)
+            SL._adj_exchange(slabs, [lam], faces, ring, reverse=True)
+            if not np.array_equal(lam, whole[n + 1][:, :, o:o + c, :]):
+                raise AssertionError(f"rank {rank}: reverse step {n} differs")
+        SL._adj_exchange(slabs, [lam], faces, ring, reverse=False)
+        np.save(os.path.join(out_dir, f"adj{rank}.npy"), _pull(lam))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3])
+def test_adjoint_ring_exchange_reproduces_the_whole_grid(tmp_path, world):
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_adj_rank_main, args=(r, world, port, str(tmp_path))) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = np.concatenate([np.load(tmp_path / f"adj{r}.npy") for r in range(world)], axis=2)
+    assert np.array_equal(got, _pull(_adj_whole()[-1]))
+
+
+def test_adjoint_face_buffer_bytes():
+    case = syn.NsfCase(n=32)
+    sch = W.nsf_scheme(case, lbx.FP32_SHIFT, extent=(32, 8), slab_origin=8, slab_planes_global=32)
+    assert sch.adjoint_halo_bytes == 3 * 10 * 32 * 4               # compute type float
+    assert sch.adjoint_lam_bytes == 10 * 9 * 32 * 8 * 4
+    sd = W.nsf_scheme(case, lbx.FP64, extent=(32, 8), slab_origin=8, slab_planes_global=32)
+    assert sd.adjoint_halo_bytes == 3 * 10 * 32 * 8
+    s16 = W.nsf_scheme(case, lbx.FP16_SCALED)
+    assert s16.adjoint_lam_bytes == 0 and s16.adjoint_halo_bytes == 0   # no FP16 adjoint
+
+
+@pytest.mark.parametrize("nslabs", [1, 2, 3])
+def test_adjoint_local_exchange_reproduces_the_whole_grid(nslabs):
+    """Several slabs in one process (the device-copy branch of slab._adj_exchange).  With
+    three slabs the forward direction after a reverse step would not reproduce the whole
+    grid (with one or two, the upper and the lower neighbour are the same slab)."""
+    whole = _adj_whole()
+    spans = [SL.slab_bounds(NY, nslabs, s) for s in range(nslabs)]
+    for reverse in (True, False):
+        lams = [whole[0][:, :, o:o + c, :].copy() for o, c in spans]
+        faces = [[torch.empty((K, len(UP), NX), dtype=torch.float64) for _ in range(4)] for _ in spans]
+        slabs = [_FakeSlab() for _ in spans]
+        for n in range(STEPS):
+            lams = [_push(lam) for lam in lams]
+            SL._adj_exchange(slabs, lams, faces, None, reverse=reverse)
+        ok = all(np.array_equal(lam, whole[-1][:, :, o:o + c, :]) for lam, (o, c) in zip(lams, spans))
+        assert ok == (reverse or nslabs <= 2)
