@@ -262,7 +262,12 @@ lbx_status lbx_lattice_velocities(int lattice, int* q, int* c, double* w);
 
 /* ---- 3. state: init / step / moments / checks ---------------------------------------- */
 /* Populations start at the (shifted) equilibrium of Q (supplement, recipes paragraph).
- * Q: float64 [K][cells], on the host (q_on_device = 0) or device (1).
+ * Q: float64 [K][cells], on the host (q_on_device = 0) or device (1).  Page-locked host
+ * fields (pinned or registered) are read by the init kernel directly over the bus, with
+ * no staging copy.  Pageable host fields are copied in chunks of planes of the last axis
+ * on a second stream of the state, each chunk's equilibrium computed while the next one
+ * is copied (FP16_SCALED without given scales copies them whole first, since the scales
+ * need every field).
  * stream: a cudaStream_t (NULL = the legacy default stream).
  * f_buf_a, f_buf_b: NULL to let the library allocate the two population buffers, or
  * two device buffers of lbx_state_buffer_bytes() bytes each, owned by the caller.  An
@@ -337,7 +342,10 @@ lbx_status lbx_state_tune(lbx_state* st, int trials, int* staging, int* block, d
 lbx_status lbx_state_use_graph(lbx_state* st, int enable);
 
 /* Q_k = sum_i f_{k,i} (Eq. moments) at the current time, float64 [K][cells] into host
- * (out_on_device = 0, synchronous) or device memory (1, asynchronous). */
+ * (out_on_device = 0, synchronous: the moments kernel writes page-locked host memory
+ * directly over the bus; for pageable memory chunks of planes are copied back on the
+ * state's second stream while the next chunk's moments are computed) or device memory
+ * (1, asynchronous). */
 lbx_status lbx_moments(lbx_state* st, double* Q_out, int out_on_device);
 
 /* sum over nodes of Q_k, float64, fixed reduction order (deterministic). */

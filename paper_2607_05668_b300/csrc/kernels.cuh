@@ -1583,12 +1583,13 @@ __global__ void k_face(typename St::S* __restrict__ A, typename St::S* __restric
 template <class Lat, template <typename> class SysT, class St>
 __global__ void k_init(const double* __restrict__ Qf, typename St::S* __restrict__ A,
                        const KParams<double> p, const double* __restrict__ feq0,
-                       unsigned long long* maxbits, int write) {
+                       unsigned long long* maxbits, int write, int plane0) {
   using Sys = SysT<double>;
   constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  // planes plane0 .. of the last axis (the whole grid from plane0 = 0)
+  const int y = (int)blockIdx.y + (D == 2 ? plane0 : 0), z = (int)blockIdx.z + (D == 3 ? plane0 : 0);
   const size_t plane = (size_t)p.ncell;
   const size_t cell = ((size_t)z * p.ny + y) * p.nx + x;
   double dQ[K];
@@ -1642,11 +1643,11 @@ __global__ void k_init(const double* __restrict__ Qf, typename St::S* __restrict
 template <class Lat, template <typename> class SysT, class St>
 __global__ void k_gather(const typename St::S* __restrict__ A, const KParams<double> p,
                          const double* __restrict__ feq0, double* __restrict__ Qout,
-                         double* __restrict__ fout) {
+                         double* __restrict__ fout, int plane0) {
   constexpr int K = SysT<double>::K, Q = Lat::Q;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = (int)blockIdx.y + (Lat::D == 2 ? plane0 : 0), z = (int)blockIdx.z + (Lat::D == 3 ? plane0 : 0);
   const PullIdx pi(x, y, z, p.nx, p.ny, p.nz);
   const size_t plane = (size_t)p.ncell;
   const size_t cell = ((size_t)z * p.ny + y) * p.nx + x;

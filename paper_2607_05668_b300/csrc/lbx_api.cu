@@ -664,9 +664,98 @@ static lbx_status check_err_word(lbx_state* st) {
                   cudaGetErrorString(e_), __FILE__, __LINE__);                                       \
   } while (0)
 
+// Host <-> device copies of the fields in chunks of planes of the last axis, overlapped with
+// the kernels that produce or consume them (lbx_init and lbx_moments with host arrays): the
+// copies run on the state's second stream, ordered against the kernels by one event per
+// chunk.  Returns after both streams have finished the chunks.
+constexpr int kCopyChunks = 8;
+
+static cudaError_t copy_stream_of(lbx_state* st, cudaStream_t* cs) {
+  if (!st->copy_stream) {
+    if (cudaError_t e = cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking)) return e;
+  }
+  *cs = st->copy_stream;
+  return cudaSuccess;
+}
+
+static void plane_chunk(const lbx_scheme& s, int j, int nch, int* p0, int* np) {
+  const int P = s.sys.D == 3 ? s.nz : s.ny;
+  const int a = (int)((long long)P * j / nch), b = (int)((long long)P * (j + 1) / nch);
+  *p0 = a;
+  *np = b - a;
+}
+
+// fields Qh (host) -> dQ (device) chunk by chunk, each chunk's equilibrium populations
+// written as soon as its planes have arrived
+static cudaError_t init_pipelined(lbx_state* st, const double* Qh, double* dQ) {
+  const lbx_scheme& s = st->sch;
+  const int P = s.sys.D == 3 ? s.nz : s.ny, nch = std::min(P, kCopyChunks);
+  const size_t pc = s.sys.D == 3 ? (size_t)s.nx * s.ny : (size_t)s.nx;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = copy_stream_of(st, &cs);
+  if (e) return e;
+  cudaEvent_t ev[kCopyChunks] = {};
+  for (int j = 0; j < nch && !e; ++j) e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+  for (int j = 0; j < nch && !e; ++j) {
+    int p0, np;
+    plane_chunk(s, j, nch, &p0, &np);
+    for (int k = 0; k < s.sys.K && !e; ++k) {
+      const size_t off = (size_t)k * s.ncell + (size_t)p0 * pc;
+      e = cudaMemcpyAsync(dQ + off, Qh + off, sizeof(double) * np * pc, cudaMemcpyHostToDevice, cs);
+    }
+    if (!e) e = cudaEventRecord(ev[j], cs);
+    if (!e) e = cudaStreamWaitEvent(st->stream, ev[j], 0);
+    if (!e) e = st->ops.init_planes(st, dQ, st->fa, p0, np);
+  }
+  const cudaError_t e1 = cudaStreamSynchronize(cs), e2 = cudaStreamSynchronize(st->stream);
+  for (int j = 0; j < nch; ++j)
+    if (ev[j]) cudaEventDestroy(ev[j]);
+  return e ? e : (e1 ? e1 : e2);
+}
+
+// moments of the current populations into Qh (host) chunk by chunk: each chunk's copy back
+// starts as soon as its moments are computed
+static cudaError_t moments_pipelined(lbx_state* st, double* d, double* Qh) {
+  const lbx_scheme& s = st->sch;
+  const int P = s.sys.D == 3 ? s.nz : s.ny, nch = std::min(P, kCopyChunks);
+  const size_t pc = s.sys.D == 3 ? (size_t)s.nx * s.ny : (size_t)s.nx;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = copy_stream_of(st, &cs);
+  if (e) return e;
+  cudaEvent_t ev[kCopyChunks] = {};
+  for (int j = 0; j < nch && !e; ++j) e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+  for (int j = 0; j < nch && !e; ++j) {
+    int p0, np;
+    plane_chunk(s, j, nch, &p0, &np);
+    e = st->ops.gather_planes(st, st->cur(), d, p0, np);
+    if (!e) e = cudaEventRecord(ev[j], st->stream);
+    if (!e) e = cudaStreamWaitEvent(cs, ev[j], 0);
+    for (int k = 0; k < s.sys.K && !e; ++k) {
+      const size_t off = (size_t)k * s.ncell + (size_t)p0 * pc;
+      e = cudaMemcpyAsync(Qh + off, d + off, sizeof(double) * np * pc, cudaMemcpyDeviceToHost, cs);
+    }
+  }
+  const cudaError_t e1 = cudaStreamSynchronize(st->stream), e2 = cudaStreamSynchronize(cs);
+  for (int j = 0; j < nch; ++j)
+    if (ev[j]) cudaEventDestroy(ev[j]);
+  return e ? e : (e1 ? e1 : e2);
+}
+
+// Device address of page-locked host memory (pinned or registered, mapped into the device's
+// address space), else null: kernels read and write such memory directly over the bus.
+static void* mapped_host(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 static void free_state(lbx_state* st) {
   if (!st) return;
   for (auto& g : st->graphs) cudaGraphExecDestroy(g.second);
+  if (st->copy_stream) cudaStreamDestroy(st->copy_stream);
   if (st->own_a && st->fa) cudaFree(st->fa);
   if (st->own_b && st->fb) cudaFree(st->fb);
   cudaFree(st->d_step);
@@ -750,7 +839,7 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
   const size_t bytes = lbx_state_buffer_bytes(sch);
   const int K = sch->sys.K, q = sch->q;
   auto bail = [&](lbx_status s) {
-    if (dQ && !q_on_device) cudaFree(dQ);
+    if (dQ && !q_on_device && dQ != mapped_host(Q)) cudaFree(dQ);
     free_state(st);
     return s;
   };
@@ -845,11 +934,17 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
   refresh_params(st);
   // fields on the device
   const size_t qbytes = sizeof(double) * K * (size_t)sch->ncell;
-  if (q_on_device) {
-    dQ = const_cast<double*>(Q);
+  // host fields without a float16 scale pass (which needs all of them first) arrive in
+  // chunks of planes, each chunk initialised while the next is copied
+  const bool derive_scales = sch->d.precision == LBX_FP16_SCALED && !(sch->d.fp16_scales[0] > 0.0);
+  // page-locked host fields: the init kernel reads them over the bus (no staging copy)
+  double* mapped = q_on_device ? nullptr : (double*)mapped_host(Q);
+  const bool pipelined = !q_on_device && !mapped && !derive_scales;
+  if (q_on_device || mapped) {
+    dQ = mapped ? mapped : const_cast<double*>(Q);
   } else {
     CKI(cudaMalloc(&dQ, qbytes));
-    CKI(cudaMemcpyAsync(dQ, Q, qbytes, cudaMemcpyHostToDevice, st->stream));
+    if (!pipelined) CKI(cudaMemcpyAsync(dQ, Q, qbytes, cudaMemcpyHostToDevice, st->stream));
   }
   if (sch->d.precision == LBX_FP16_SCALED && sch->d.fp16_scales[0] > 0.0) {
     for (int k = 0; k < K; ++k) st->scale[k] = sch->d.fp16_scales[k];    // given (shared by slabs)
@@ -881,9 +976,13 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
     }
     refresh_params(st);
   }
-  CKI(st->ops.init(st, dQ, st->fa, nullptr, 1));
-  CKI(cudaStreamSynchronize(st->stream));
-  if (!q_on_device) {
+  if (pipelined) {
+    CKI(init_pipelined(st, Q, dQ));
+  } else {
+    CKI(st->ops.init(st, dQ, st->fa, nullptr, 1));
+    CKI(cudaStreamSynchronize(st->stream));
+  }
+  if (!q_on_device && !mapped) {
     cudaFree(dQ);
     dQ = nullptr;
   }
@@ -1093,11 +1192,16 @@ extern "C" lbx_status lbx_moments(lbx_state* st, double* Q_out, int out_on_devic
       return fail(LBX_ERR_CUDA, "lbx_moments: %s", cudaGetErrorString(e));
     return LBX_OK;
   }
+  if (double* m = (double*)mapped_host(Q_out)) {
+    // page-locked host memory: the moments kernel writes it over the bus
+    cudaError_t e = st->ops.gather(st, st->cur(), m, nullptr);
+    if (!e) e = cudaStreamSynchronize(st->stream);
+    CK(e);
+    return LBX_OK;
+  }
   double* d = nullptr;
   CK(cudaMalloc(&d, bytes));
-  cudaError_t e = st->ops.gather(st, st->cur(), d, nullptr);
-  if (!e) e = cudaMemcpyAsync(Q_out, d, bytes, cudaMemcpyDeviceToHost, st->stream);
-  if (!e) e = cudaStreamSynchronize(st->stream);
+  const cudaError_t e = moments_pipelined(st, d, Q_out);
   cudaFree(d);
   CK(e);
   return LBX_OK;

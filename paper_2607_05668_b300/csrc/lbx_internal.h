@@ -57,6 +57,9 @@ struct Ops {
   // slab faces: copy the face slots of A into (pack = 1) or from (0) the two face buffers
   cudaError_t (*face)(const lbx_state*, void* A, void* up, void* dn, int pack);
   int face_nf;         // velocities crossing one face (c_a = +1 along the slab axis)
+  // init / moments of the planes plane0 .. plane0 + nplanes - 1 of the last axis
+  cudaError_t (*init_planes)(const lbx_state*, const double* Q, void* A, int plane0, int nplanes);
+  cudaError_t (*gather_planes)(const lbx_state*, const void* A, double* Qout, int plane0, int nplanes);
 };
 
 lbx_status fail(lbx_status s, const char* fmt, ...);
@@ -69,6 +72,7 @@ size_t storage_size(int precision);
 struct lbx_state {
   lbx_scheme sch;
   cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;   // host copies overlapped with kernels (created on use)
   lbx::Ops ops{};
   void* fa = nullptr;
   void* fb = nullptr;

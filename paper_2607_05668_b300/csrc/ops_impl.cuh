@@ -137,12 +137,27 @@ struct OpsImpl {
   }
   static cudaError_t init(const lbx_state* st, const double* Q, void* A, unsigned long long* maxbits, int write) {
     dim3 b = block(st->sch), g = grid(st->sch, b);
-    k_init<Lat, SysT, St><<<g, b, 0, st->stream>>>(Q, (S*)A, st->pd, st->d_feq0, maxbits, write);
+    k_init<Lat, SysT, St><<<g, b, 0, st->stream>>>(Q, (S*)A, st->pd, st->d_feq0, maxbits, write, 0);
     return cudaGetLastError();
   }
   static cudaError_t gather(const lbx_state* st, const void* A, double* Qout, double* fout) {
     dim3 b = block(st->sch), g = grid(st->sch, b);
-    k_gather<Lat, SysT, St><<<g, b, 0, st->stream>>>((const S*)A, st->pd, st->d_feq0, Qout, fout);
+    k_gather<Lat, SysT, St><<<g, b, 0, st->stream>>>((const S*)A, st->pd, st->d_feq0, Qout, fout, 0);
+    return cudaGetLastError();
+  }
+  // The same for the planes plane0 .. plane0 + nplanes - 1 of the last axis (pipelined
+  // host copies: lbx_init and lbx_moments with host arrays).
+  static dim3 plane_grid(const lbx_scheme& s, dim3 b, int nplanes) {
+    return dim3((s.nx + b.x - 1) / b.x, Lat::D == 3 ? s.ny : nplanes, Lat::D == 3 ? nplanes : 1);
+  }
+  static cudaError_t init_planes(const lbx_state* st, const double* Q, void* A, int plane0, int nplanes) {
+    dim3 b = block(st->sch), g = plane_grid(st->sch, b, nplanes);
+    k_init<Lat, SysT, St><<<g, b, 0, st->stream>>>(Q, (S*)A, st->pd, st->d_feq0, nullptr, 1, plane0);
+    return cudaGetLastError();
+  }
+  static cudaError_t gather_planes(const lbx_state* st, const void* A, double* Qout, int plane0, int nplanes) {
+    dim3 b = block(st->sch), g = plane_grid(st->sch, b, nplanes);
+    k_gather<Lat, SysT, St><<<g, b, 0, st->stream>>>((const S*)A, st->pd, st->d_feq0, Qout, nullptr, plane0);
     return cudaGetLastError();
   }
   static cudaError_t scatter(const lbx_state* st, const double* fin, void* A) {
@@ -239,7 +254,7 @@ inline Ops make_ops() {
              I::scatter,    I::reduce,   I::step_fn,
              I::REG,        I::batch_step, I::batch_fn, I::smem_bytes,
              sizeof(BatchInst<typename St::C>), sizeof(typename St::S), I::step_inplace,
-             I::face, FaceVel<Lat>::NF};
+             I::face, FaceVel<Lat>::NF, I::init_planes, I::gather_planes};
 }
 
 template <class Lat, template <typename> class SysT>

@@ -326,12 +326,12 @@ class State:
         return torch.from_numpy(out)
 
     def moments_into(self, out):
-        """lbx_moments into a caller-owned CUDA float64 tensor [K, *grid] (asynchronous on
-        the state's stream)."""
+        """lbx_moments into a caller-owned float64 tensor [K, *grid]: CUDA (asynchronous on the
+        state's stream) or host memory, best page-locked (synchronous)."""
         shape = (self.K,) + self.scheme.grid
-        if not (out.is_cuda and out.dtype == torch.float64 and tuple(out.shape) == shape and out.is_contiguous()):
-            raise ValueError(f"moments_into needs a contiguous CUDA float64 tensor of shape {shape}")
-        check(_lib.lbx_moments(self._h, out.data_ptr(), 1))
+        if not (out.dtype == torch.float64 and tuple(out.shape) == shape and out.is_contiguous()):
+            raise ValueError(f"moments_into needs a contiguous float64 tensor of shape {shape}")
+        check(_lib.lbx_moments(self._h, out.data_ptr(), 1 if out.is_cuda else 0))
         return out
 
     def halo_pack(self, to_upper, to_lower):
