@@ -10,8 +10,10 @@ grid (one kernel launch).  Prints one JSON line.
                   [--workload nsf|mhd|adr|nsf12|mhd18|hcnsf] [--precision fp32|fp64|fp16]
 
 --impl reference times the CPU FP64 oracle on bounded samples of the same workload.
-Under torchrun (N > 1) every rank advances its own replica (weak scaling, no exchange)
-and rank 0 prints the line; the reference arm runs on rank 0 only.
+Under torchrun (N > 1) every rank holds one case-sized slab of a grid N times as long along
+its last axis and exchanges the faces of every step with its neighbours (NCCL, behind the
+interior planes; weak scaling; --decomp replicas: independent grids); rank 0 prints the
+line; the reference arm runs on rank 0 only.
 """
 from __future__ import annotations
 
@@ -495,10 +497,14 @@ def run_ours(args):
         slab = SL.Slab(sch, Q.cuda(), stream=stream) if decomp == "slab" else None
     st = slab.state if slab else L.State(sch, Q.cuda(), stream=stream)
 
+    side = SL.side_stream() if decomp == "slab" else None
+
     def run_steps(n, state=None, sl=None):
         if sl is not None:
-            with torch.cuda.stream(stream):   # NCCL orders its messages with this stream
-                SL.step_ring(sl, ring, n)
+            # the face exchange (pack, NCCL send/recv, unpack) on a second stream behind the
+            # interior planes of every step
+            with torch.cuda.stream(stream):
+                SL.step_ring_overlap(sl, ring, n, side)
         else:
             state.step(n)
 
@@ -626,14 +632,14 @@ def run_ours(args):
         g[-1] = case.n * ws
         config["parallelism"] = (f"slab x{ws}: one {'z' if args.workload in DIM3 else 'y'}-slab of "
                                  f"{'x'.join(map(str, config['grid']))} per GPU of a {'x'.join(map(str, g))} "
-                                 "grid, one face exchange per step (lbx_halo_pack, NCCL send/recv, "
-                                 "lbx_halo_unpack)")
+                                 "grid, one face exchange per step (boundary planes, lbx_halo_pack_next, NCCL "
+                                 "send/recv, lbx_halo_unpack_next on a second stream behind the interior planes)")
     result = {
         "metric": "Lattice updates/s", "value": value, "unit": "LUP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAME[args.precision], "data": "synthetic",
         "config": config,
-        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps * (3 if decomp == "slab" else 1),
+        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps * (5 if decomp == "slab" else 1),
         "finite": finite, "launch": launch, "clocks": clk.summary(),
         "timing": {"graph_replay": graph, "pre_warm_steps": pre, "pre_warm_s": t_pre,
                    "note": "the W warm-up steps, then untimed pre-warm steps in calls of K steps (at least "

@@ -424,6 +424,28 @@ lbx_status lbx_halo_pack(lbx_state* st, void* to_upper, void* to_lower);
  * in the state's storage representation (shifted and scaled), so slabs that exchange must
  * share the scheme's storage, background state and (FP16) scales. */
 lbx_status lbx_halo_unpack(lbx_state* st, const void* from_lower, const void* from_upper);
+/* The exchange hidden behind the interior: a step in pieces.  Only the nodes of planes 0
+ * and P - 1 write the face slots, and the interior planes never read them, so a slab can
+ * step its two boundary planes first, exchange their faces on a second stream while the
+ * interior planes step, and join before the next step:
+ *     lbx_step_planes(st, 0, 1, side);  lbx_step_planes(st, P - 1, 1, side);
+ *     lbx_step_planes(st, 1, P - 2, NULL);              (the state's stream)
+ *     lbx_halo_pack_next(st, to_upper, to_lower, side);  transport on side;
+ *     lbx_halo_unpack_next(st, from_lower, from_upper, side);
+ *     the state's stream waits for side;  lbx_step_commit(st);
+ * lbx_step_planes updates planes [plane0, plane0 + nplanes) of the last axis from the
+ * current populations into the other buffer on `stream` (NULL: the state's stream),
+ * asynchronously, without swapping the buffers; the same kernels and arithmetic as
+ * lbx_step, so the pieces of a step are bitwise one lbx_step(st, 1).  LBX_ERR_ARG for a
+ * range outside the grid, LBX_ERR_UNSUPPORTED for in-place states and the persistent
+ * LBX_STAGE_PIPE kernel.  lbx_step_commit makes the other buffer current and advances the
+ * step count (the device counter of time-dependent systems on the state's stream, so
+ * every piece of the step must be ordered before it).  The _next face calls act on the
+ * buffer being written (before lbx_step_commit), on `stream` (NULL: the state's). */
+lbx_status lbx_step_planes(lbx_state* st, int64_t plane0, int64_t nplanes, void* stream);
+lbx_status lbx_step_commit(lbx_state* st);
+lbx_status lbx_halo_pack_next(lbx_state* st, void* to_upper, void* to_lower, void* stream);
+lbx_status lbx_halo_unpack_next(lbx_state* st, const void* from_lower, const void* from_upper, void* stream);
 /* The storage scales s_k of the state (1 unless FP16_SCALED), float64 [K] host array. */
 lbx_status lbx_state_scales(const lbx_state* st, double* scales);
 /* Raw error statistics per component against Q_ref [K][cells] (host or device): stats[k][0]

@@ -44,6 +44,7 @@ template <typename T>
 struct KParams {
   int nx, ny, nz, pad_;
   int oy, oz;                  // slab origin: global index of local row 0 (2D) or plane 0 (3D)
+  int plane0;                  // first plane of the last axis a step launch covers (0: all)
   long long ncell;             // nodes per population plane
   T Q0[KMAX];                  // background state (shift reference)
   T F0l[KMAX][3];              // (dt/dx)/c_s^2 * Phi(Q0), used by the unshifted mode
@@ -80,6 +81,17 @@ struct KParams {
 template <typename T>
 __host__ __device__ __forceinline__ bool time_dependent(const KParams<T>& p) {
   return p.mms_tab != nullptr || p.mms_modes != nullptr || p.pf_kind == 2;
+}
+
+// Node rows of a step block: the block's y and z indices, the last axis offset by plane0
+// (a launch over a range of planes of that axis).
+template <class Lat, typename T>
+__device__ __forceinline__ int block_y(const KParams<T>& p) {
+  return (int)blockIdx.y + (Lat::D == 2 ? p.plane0 : 0);
+}
+template <class Lat, typename T>
+__device__ __forceinline__ int block_z(const KParams<T>& p) {
+  return (int)blockIdx.z + (Lat::D == 3 ? p.plane0 : 0);
 }
 
 // Element index of population (k, i) at `cell` (see the storage layout above).
@@ -1077,7 +1089,8 @@ __global__ void __launch_bounds__(COLS, SplitMode<Lat, SysT, St, COLS>::min_bloc
   const bool active = xr < p.nx;
   const int x = active ? xr : p.nx - 1;
   const long long step = time_dependent(p) ? *p.step_ptr + p.step_rel : 0;
-  step_node_split<Lat, SysT, St, COLS>(A, B, p, x, blockIdx.y, blockIdx.z, step, (int)(threadIdx.x & 1), active);
+  step_node_split<Lat, SysT, St, COLS>(A, B, p, x, block_y<Lat>(p), block_z<Lat>(p), step, (int)(threadIdx.x & 1),
+                                       active);
 }
 
 // ------------------------------------------------------------ bulk-copied rows (TMA)
@@ -1182,7 +1195,7 @@ __device__ __forceinline__ void bulk_step_body(const typename St::S* A, typename
   V* rowv = reinterpret_cast<V*>(lbx_smem + 16);                 // [KP q][ROWP]
   S* rowo = reinterpret_cast<S*>(rowv + (size_t)KP * Q * M::ROWP); // [q][ROWO]
   const unsigned int bar = smem_u32(lbx_smem);
-  const int t = (int)threadIdx.x, x0 = (int)blockIdx.x * COLS, y = (int)blockIdx.y, z = (int)blockIdx.z;
+  const int t = (int)threadIdx.x, x0 = (int)blockIdx.x * COLS, y = block_y<Lat>(p), z = block_z<Lat>(p);
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const unsigned int plane = (unsigned int)p.ncell;
   // offset of the element a thread uses in the shared row of velocity i
@@ -1306,11 +1319,11 @@ __global__ void __launch_bounds__(COLS, FOURIER ? StepMode<Lat, SysT, St, COLS>:
     __shared__ typename St::C tf[2 * MMS_MAX_MODES];
     mms_time_table(p, step, tf);
     if (x >= p.nx) return;
-    step_node<Lat, SysT, St, MODE, COLS, FOURIER>(A, B, p, x, blockIdx.y, blockIdx.z, step,
+    step_node<Lat, SysT, St, MODE, COLS, FOURIER>(A, B, p, x, block_y<Lat>(p), block_z<Lat>(p), step,
                                                   p.mms_modes != nullptr ? tf : nullptr);
   } else {
     if (x >= p.nx) return;
-    step_node<Lat, SysT, St, MODE, COLS, FOURIER>(A, B, p, x, blockIdx.y, blockIdx.z, step);
+    step_node<Lat, SysT, St, MODE, COLS, FOURIER>(A, B, p, x, block_y<Lat>(p), block_z<Lat>(p), step);
   }
 }
 

@@ -331,6 +331,7 @@ extern "C" lbx_status lbx_adjoint_restore(lbx_state* st, const void* src, int64_
   CK(cudaMemcpyAsync(st->d_step, &base, sizeof(base), cudaMemcpyHostToDevice, st->stream));
   CK(cudaStreamSynchronize(st->stream));   // `base` lives on this stack frame
   st->step = base;
+  st->step_dirty = false;
   return LBX_OK;
 }
 

@@ -1285,22 +1285,68 @@ extern "C" size_t lbx_halo_bytes(const lbx_scheme* s) {
   return (size_t)o.face_nf * s->sys.K * pc * storage_size(s->d.precision);
 }
 
-static lbx_status face_call(lbx_state* st, void* a, void* b, int pack, const char* who) {
+static lbx_status face_call(lbx_state* st, void* a, void* b, int pack, bool next, void* stream, const char* who) {
   if (!st || !a || !b) return fail(LBX_ERR_ARG, "%s: null argument", who);
   if (st->inplace) return fail(LBX_ERR_UNSUPPORTED, "%s: two-buffer states only", who);
   if (((uintptr_t)a % 16) != 0 || ((uintptr_t)b % 16) != 0)
     return fail(LBX_ERR_ARG, "%s: face buffers must be 16-byte aligned", who);
-  if (cudaError_t e = st->ops.face(st, st->cur(), a, b, pack))
+  const cudaStream_t s = stream ? (cudaStream_t)stream : st->stream;
+  if (cudaError_t e = st->ops.face(st, next ? st->nxt() : st->cur(), a, b, pack, s))
     return fail(LBX_ERR_CUDA, "%s: %s", who, cudaGetErrorString(e));
   return LBX_OK;
 }
 
 extern "C" lbx_status lbx_halo_pack(lbx_state* st, void* to_upper, void* to_lower) {
-  return face_call(st, to_upper, to_lower, 1, "lbx_halo_pack");
+  return face_call(st, to_upper, to_lower, 1, false, nullptr, "lbx_halo_pack");
 }
 
 extern "C" lbx_status lbx_halo_unpack(lbx_state* st, const void* from_lower, const void* from_upper) {
-  return face_call(st, const_cast<void*>(from_lower), const_cast<void*>(from_upper), 0, "lbx_halo_unpack");
+  return face_call(st, const_cast<void*>(from_lower), const_cast<void*>(from_upper), 0, false, nullptr,
+                   "lbx_halo_unpack");
+}
+
+extern "C" lbx_status lbx_halo_pack_next(lbx_state* st, void* to_upper, void* to_lower, void* stream) {
+  return face_call(st, to_upper, to_lower, 1, true, stream, "lbx_halo_pack_next");
+}
+
+extern "C" lbx_status lbx_halo_unpack_next(lbx_state* st, const void* from_lower, const void* from_upper,
+                                           void* stream) {
+  return face_call(st, const_cast<void*>(from_lower), const_cast<void*>(from_upper), 0, true, stream,
+                   "lbx_halo_unpack_next");
+}
+
+extern "C" lbx_status lbx_step_planes(lbx_state* st, int64_t plane0, int64_t nplanes, void* stream) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_step_planes: null state");
+  if (st->inplace) return fail(LBX_ERR_UNSUPPORTED, "lbx_step_planes: two-buffer states only");
+  if (st->nonfinite) return fail(LBX_ERR_NONFINITE, "lbx_step_planes: state holds non-finite values");
+  const int P = st->sch.sys.D == 3 ? st->sch.nz : st->sch.ny;
+  if (plane0 < 0 || nplanes < 0 || plane0 + nplanes > P)
+    return fail(LBX_ERR_ARG, "lbx_step_planes: planes [%lld, %lld) outside 0..%d", (long long)plane0,
+                (long long)(plane0 + nplanes), P);
+  if (!st->ops.reg && resolved_staging(st) == LBX_STAGE_PIPE)
+    return fail(LBX_ERR_UNSUPPORTED, "lbx_step_planes: the persistent LBX_STAGE_PIPE kernel steps whole grids only");
+  if (nplanes == 0) return LBX_OK;
+  st->plane_lo = (int)plane0;
+  st->plane_n = (int)nplanes;
+  const cudaError_t e = st->ops.step(st, st->cur(), st->nxt(), 0, stream ? (cudaStream_t)stream : st->stream);
+  st->plane_lo = 0;
+  st->plane_n = 0;
+  if (e) return fail(LBX_ERR_CUDA, "lbx_step_planes: %s", cudaGetErrorString(e));
+  return LBX_OK;
+}
+
+extern "C" lbx_status lbx_step_commit(lbx_state* st) {
+  if (!st) return fail(LBX_ERR_ARG, "lbx_step_commit: null state");
+  if (st->inplace) return fail(LBX_ERR_UNSUPPORTED, "lbx_step_commit: two-buffer states only");
+  if (time_dependent(st->sch)) {
+    if (cudaError_t e = launch_advance(st->d_step, 1, st->stream))
+      return fail(LBX_ERR_CUDA, "lbx_step_commit: %s", cudaGetErrorString(e));
+  } else {
+    st->step_dirty = true;
+  }
+  st->cur_a = !st->cur_a;
+  st->step += 1;
+  return LBX_OK;
 }
 
 extern "C" lbx_status lbx_state_scales(const lbx_state* st, double* scales) {

@@ -55,7 +55,7 @@ struct Ops {
   // in-place step of the given kind (1 or 2) on the single buffer F (see k_step_inplace)
   cudaError_t (*step_inplace)(const lbx_state*, void* F, int kind, int rel, cudaStream_t);
   // slab faces: copy the face slots of A into (pack = 1) or from (0) the two face buffers
-  cudaError_t (*face)(const lbx_state*, void* A, void* up, void* dn, int pack);
+  cudaError_t (*face)(const lbx_state*, void* A, void* up, void* dn, int pack, cudaStream_t);
   int face_nf;         // velocities crossing one face (c_a = +1 along the slab axis)
   // init / moments of the planes plane0 .. plane0 + nplanes - 1 of the last axis
   cudaError_t (*init_planes)(const lbx_state*, const double* Q, void* A, int plane0, int nplanes);
@@ -73,6 +73,10 @@ struct lbx_state {
   lbx_scheme sch;
   cudaStream_t stream = nullptr;
   cudaStream_t copy_stream = nullptr;   // host copies overlapped with kernels (created on use)
+  // planes [plane_lo, plane_lo + plane_n) of the last axis that a step launch covers
+  // (lbx_step_planes; plane_n = 0: all planes)
+  int plane_lo = 0, plane_n = 0;
+  int step_planes() const { return plane_n > 0 ? plane_n : (sch.sys.D == 3 ? sch.nz : sch.ny); }
   lbx::Ops ops{};
   void* fa = nullptr;
   void* fb = nullptr;

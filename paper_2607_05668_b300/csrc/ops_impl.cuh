@@ -26,6 +26,11 @@ struct OpsImpl {
     return dim3(bx, 1, 1);
   }
   static dim3 grid(const lbx_scheme& s, dim3 b) { return dim3((s.nx + b.x - 1) / b.x, s.ny, s.nz); }
+  // A step launch's blocks along y and z: the state's plane range of the last axis.
+  static dim3 step_grid(const lbx_state* st, unsigned int gx) {
+    const int n = st->step_planes();
+    return Lat::D == 3 ? dim3(gx, st->sch.ny, n) : dim3(gx, n, st->sch.nz);
+  }
   static size_t smem(int threads) { return StepMode<Lat, SysT, St, 128>::smem_bytes; }
   // Opt a staged kernel into the shared memory it needs.
   static cudaError_t prepare(const void* fn, size_t bytes) {
@@ -37,7 +42,7 @@ struct OpsImpl {
     const size_t bytes = StepMode<Lat, SysT, St, COLS>::smem_bytes;
     static cudaError_t prep = prepare((const void*)k_step<Lat, SysT, St, MODE, COLS>, bytes);
     if (prep != cudaSuccess) return prep;
-    const dim3 b(COLS, 1, 1), g((st->sch.nx + COLS - 1) / COLS, st->sch.ny, st->sch.nz);
+    const dim3 b(COLS, 1, 1), g = step_grid(st, (st->sch.nx + COLS - 1) / COLS);
     k_step<Lat, SysT, St, MODE, COLS><<<g, b, bytes, strm>>>((const S*)A, (S*)B, p);
     return cudaGetLastError();
   }
@@ -70,7 +75,7 @@ struct OpsImpl {
     const size_t bytes = SplitMode<Lat, SysT, St, COLS>::smem_bytes;
     static cudaError_t prep = prepare((const void*)k_step_split<Lat, SysT, St, COLS>, bytes);
     if (prep != cudaSuccess) return prep;
-    const dim3 b(COLS, 1, 1), g((st->sch.nx + COLS / 2 - 1) / (COLS / 2), st->sch.ny, st->sch.nz);
+    const dim3 b(COLS, 1, 1), g = step_grid(st, (st->sch.nx + COLS / 2 - 1) / (COLS / 2));
     k_step_split<Lat, SysT, St, COLS><<<g, b, bytes, strm>>>((const S*)A, (S*)B, p);
     return cudaGetLastError();
   }
@@ -81,7 +86,7 @@ struct OpsImpl {
     const size_t bytes = BulkMode<Lat, SysT, St, COLS>::smem_bytes;
     static cudaError_t prep = prepare((const void*)k_step_bulk<Lat, SysT, St, COLS>, bytes);
     if (prep != cudaSuccess) return prep;
-    const dim3 b(COLS, 1, 1), g((st->sch.nx + COLS - 1) / COLS, st->sch.ny, st->sch.nz);
+    const dim3 b(COLS, 1, 1), g = step_grid(st, (st->sch.nx + COLS - 1) / COLS);
     k_step_bulk<Lat, SysT, St, COLS><<<g, b, bytes, strm>>>((const S*)A, (S*)B, p);
     return cudaGetLastError();
   }
@@ -92,17 +97,18 @@ struct OpsImpl {
   static cudaError_t step(const lbx_state* st, const void* A, void* B, int rel, cudaStream_t strm) {
     KParams<C> p = st->pc<C>();
     p.step_rel = rel;
+    p.plane0 = st->plane_lo;
     if (p.mms_modes != nullptr) {
       // mode-table forcing: its own instantiation, 128 threads, per-thread staging
       const size_t bytes = StepMode<Lat, SysT, St, 128>::smem_bytes;
       static cudaError_t prep = prepare((const void*)k_step<Lat, SysT, St, MODE, 128, true>, bytes);
       if (prep != cudaSuccess) return prep;
-      dim3 b = MODE == MODE_REG ? block(st->sch) : dim3(128, 1, 1), g = grid(st->sch, b);
+      dim3 b = MODE == MODE_REG ? block(st->sch) : dim3(128, 1, 1), g = step_grid(st, grid(st->sch, b).x);
       k_step<Lat, SysT, St, MODE, 128, true><<<g, b, bytes, strm>>>((const S*)A, (S*)B, p);
       return cudaGetLastError();
     }
     if constexpr (MODE == MODE_REG) {
-      dim3 b = block(st->sch), g = grid(st->sch, b);
+      dim3 b = block(st->sch), g = step_grid(st, grid(st->sch, b).x);
       k_step<Lat, SysT, St, MODE, 128><<<g, b, 0, strm>>>((const S*)A, (S*)B, p);
       return cudaGetLastError();
     } else {
@@ -233,14 +239,14 @@ struct OpsImpl {
     return kind == 1 ? launch_inplace<false, 1>(st, F, p, strm) : launch_inplace<false, 2>(st, F, p, strm);
   }
   // Slab faces (k_face): one thread per plane cell, face velocity and face.
-  static cudaError_t face(const lbx_state* st, void* A, void* up, void* dn, int pack) {
+  static cudaError_t face(const lbx_state* st, void* A, void* up, void* dn, int pack, cudaStream_t strm) {
     const lbx_scheme& s = st->sch;
     const unsigned int pc = Lat::D == 3 ? (unsigned int)(s.nx * s.ny) : (unsigned int)s.nx;
     const dim3 b(128, 1, 1), g((pc + 127) / 128, FaceVel<Lat>::NF, 2);
     if (pack)
-      k_face<Lat, SysT, St, true><<<g, b, 0, st->stream>>>((S*)A, (S*)up, (S*)dn, st->pc<C>());
+      k_face<Lat, SysT, St, true><<<g, b, 0, strm>>>((S*)A, (S*)up, (S*)dn, st->pc<C>());
     else
-      k_face<Lat, SysT, St, false><<<g, b, 0, st->stream>>>((S*)A, (S*)up, (S*)dn, st->pc<C>());
+      k_face<Lat, SysT, St, false><<<g, b, 0, strm>>>((S*)A, (S*)up, (S*)dn, st->pc<C>());
     return cudaGetLastError();
   }
   // staged kernels keep a fixed 128-column layout: larger blocks cannot launch

@@ -108,6 +108,10 @@ _sig("lbx_conserved_sums_static", C.c_int, [_P, _P, _P, C.c_int, _P])
 _sig("lbx_halo_bytes", C.c_size_t, [_P])
 _sig("lbx_halo_pack", C.c_int, [_P, _P, _P])
 _sig("lbx_halo_unpack", C.c_int, [_P, _P, _P])
+_sig("lbx_halo_pack_next", C.c_int, [_P, _P, _P, _P])
+_sig("lbx_halo_unpack_next", C.c_int, [_P, _P, _P, _P])
+_sig("lbx_step_planes", C.c_int, [_P, C.c_int64, C.c_int64, _P])
+_sig("lbx_step_commit", C.c_int, [_P])
 _sig("lbx_state_scales", C.c_int, [_P, _D])
 _sig("lbx_error_stats", C.c_int, [_P, _P, C.c_int, _D])
 _sig("lbx_adjoint", C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, _D, _P, _D])
@@ -143,6 +147,11 @@ def _host_f64(a):
     if isinstance(a, torch.Tensor):
         a = a.detach().cpu().numpy()
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _side(stream):
+    """A stream argument of the calls where NULL means the state's own stream."""
+    return None if stream is None else _stream_handle(stream)
 
 
 def _stream_handle(stream):
@@ -337,6 +346,20 @@ class State:
     def halo_pack(self, to_upper, to_lower):
         """lbx_halo_pack into two CUDA uint8 tensors of scheme.halo_bytes bytes."""
         check(_lib.lbx_halo_pack(self._h, to_upper.data_ptr(), to_lower.data_ptr()))
+
+    def step_planes(self, plane0, nplanes, stream=None):
+        """lbx_step_planes: planes [plane0, plane0 + nplanes) of the next step (stream None:
+        the state's)."""
+        check(_lib.lbx_step_planes(self._h, int(plane0), int(nplanes), _side(stream)))
+
+    def step_commit(self):
+        check(_lib.lbx_step_commit(self._h))
+
+    def halo_pack_next(self, to_upper, to_lower, stream=None):
+        check(_lib.lbx_halo_pack_next(self._h, to_upper.data_ptr(), to_lower.data_ptr(), _side(stream)))
+
+    def halo_unpack_next(self, from_lower, from_upper, stream=None):
+        check(_lib.lbx_halo_unpack_next(self._h, from_lower.data_ptr(), from_upper.data_ptr(), _side(stream)))
 
     def halo_unpack(self, from_lower, from_upper):
         """lbx_halo_unpack from the neighbours' face buffers (CUDA tensors)."""

@@ -133,6 +133,69 @@ def step_local(slabs, n=1):
             s.unpack()
 
 
+def _split_step(slabs, side, exchange):
+    """One step of slabs with the exchange behind the interior: the boundary planes 0 and
+    P - 1 of every slab step on `side`, whose faces are packed, exchanged (exchange(), on
+    side) and unpacked into the buffer being written while the interior planes 1 .. P - 2
+    step on torch's current stream (the states' stream); then that stream waits for side
+    and every state commits its step (lbx_step_planes, lbx_halo_pack_next / _unpack_next,
+    lbx_step_commit)."""
+    main = torch.cuda.current_stream()
+    side.wait_stream(main)
+    for s in slabs:
+        P = s.scheme.grid[0]
+        s.state.step_planes(0, 1, side)
+        if P > 1:
+            s.state.step_planes(P - 1, 1, side)
+        s.state.step_planes(1, max(P - 2, 0))
+    exchange()
+    main.wait_stream(side)
+    for s in slabs:
+        s.state.step_commit()
+
+
+def side_stream():
+    """The second stream of the overlapped exchange, at high priority: the block scheduler
+    then dispatches its small kernels (boundary planes, pack, unpack) as soon as SMs free
+    up instead of after every block of the interior launch."""
+    lo, hi = torch.cuda.Stream.priority_range()
+    return torch.cuda.Stream(priority=hi)
+
+
+def step_ring_overlap(slab: Slab, ring: RingExchange, n=1, side=None):
+    """step_ring with the face exchange hidden behind the interior planes of every step
+    (bitwise the result of step_ring).  The slab's state must run on torch's current
+    stream; `side` is a second stream (side_stream() if None)."""
+    side = side or side_stream()
+
+    def exchange():
+        slab.state.halo_pack_next(slab.to_upper, slab.to_lower, side)
+        with torch.cuda.stream(side):
+            ring.exchange(slab.to_upper, slab.to_lower, slab.from_lower, slab.from_upper)
+        slab.state.halo_unpack_next(slab.from_lower, slab.from_upper, side)
+    for _ in range(int(n)):
+        _split_step([slab], side, exchange)
+
+
+def step_local_overlap(slabs, n=1, side=None):
+    """step_local with the face exchange hidden behind the interior planes (bitwise the
+    result of step_local)."""
+    side = side or side_stream()
+    m = len(slabs)
+
+    def exchange():
+        for s in slabs:
+            s.state.halo_pack_next(s.to_upper, s.to_lower, side)
+        with torch.cuda.stream(side):
+            for i, s in enumerate(slabs):
+                s.from_lower.copy_(slabs[(i - 1) % m].to_upper)
+                s.from_upper.copy_(slabs[(i + 1) % m].to_lower)
+        for s in slabs:
+            s.state.halo_unpack_next(s.from_lower, s.from_upper, side)
+    for _ in range(int(n)):
+        _split_step(slabs, side, exchange)
+
+
 def combine_error_stats(stats):
     """relative L2 and L-infinity per component (Sec. 4, as lbx_error_norms) from the
     [K, 4] statistics of every slab (lbx_error_stats) combined over the grid."""

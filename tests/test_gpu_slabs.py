@@ -38,9 +38,9 @@ def _slabs(make_scheme, Q, planes, nslabs, scales=None):
     return out
 
 
-def _compare(whole, slabs, steps, planes):
+def _compare(whole, slabs, steps, planes, stepper=None):
     whole.step(steps)
-    SL.step_local(slabs, steps)
+    (stepper or SL.step_local)(slabs, steps)
     Qw = whole.moments()
     Qs = torch.cat([s.state.moments() for s in slabs], dim=1)
     assert torch.equal(Qs, Qw)
@@ -132,3 +132,73 @@ def test_forced_nsf_slabs_equal_the_whole_grid():
     Qo = och.moments(och.run(och.init(Q), steps))
     Qs = torch.cat([s.state.moments() for s in slabs], dim=1)
     assert H.rel_linf_per_field(Qs, Qo).max() <= 1e-12
+
+
+# ------------------------------------------- the exchange hidden behind the interior planes
+def test_step_pieces_equal_one_step():
+    """lbx_step_planes over a split of the planes, then lbx_step_commit, is bitwise one
+    lbx_step: register-resident FP32, bulk-staged FP16 3D, and the homogenized NSF with
+    time-dependent fields (the device step counter advances at the commit)."""
+    nsf, mhd, hc = syn.NsfCase(n=40), syn.MhdCase(n=16), syn.HcnsfPaperCase(n=16)
+    hq = hc.table().augmented(syn.coords((16, 16, 16)), 0.0)
+    cases = [(lambda: W.nsf_scheme(nsf, lbx.FP32_SHIFT), syn.nsf_fields(nsf), (0, 1, 17, 40)),
+             (lambda: W.mhd_scheme(mhd, lbx.FP16_SCALED), syn.mhd_fields(mhd), (0, 5, 16)),
+             (lambda: W.hcnsf_scheme(hc, lbx.FP64), hq, (0, 1, 15, 16))]
+    for make, Q, cuts in cases:
+        ref, st = lbx.State(make(), Q), lbx.State(make(), Q)
+        ref.step(3)
+        for _ in range(3):
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                st.step_planes(a, b - a)
+            st.step_commit()
+        assert st.time == ref.time
+        assert torch.equal(st.get_populations(), ref.get_populations())
+
+
+def test_step_planes_refuses_bad_ranges_and_the_persistent_kernel():
+    case = syn.MhdCase(n=8)
+    st = lbx.State(W.mhd_scheme(case, lbx.FP32_SHIFT), syn.mhd_fields(case))
+    for a, n in ((-1, 2), (0, 9), (7, 2)):
+        with pytest.raises(lbx.LbxError, match="ERR_ARG"):
+            st.step_planes(a, n)
+    st.set_staging(lbx.STAGE_PIPE)
+    with pytest.raises(lbx.LbxError, match="ERR_UNSUPPORTED"):
+        st.step_planes(0, 1)
+
+
+@pytest.mark.parametrize("nslabs", [1, 3])
+def test_overlapped_exchange_slabs_equal_the_whole_grid(nslabs):
+    """step_local_overlap: boundary planes, face exchange and unpack on a second stream while
+    the interior planes step; NSF D2Q9 in FP16 (shared scales) and MHD D3Q19 in FP32 (bulk
+    row copies), 1 and 3 slabs, bitwise equal to the whole grid."""
+    case = syn.NsfCase(n=48)
+    Q = syn.nsf_fields(case)
+    whole = lbx.State(W.nsf_scheme(case, lbx.FP16_SCALED), Q)
+    scales = list(whole.scales())
+
+    def make(c, o, sc):
+        return W.nsf_scheme(case, lbx.FP16_SCALED, extent=(case.n, c), slab_origin=o, slab_planes_global=case.n,
+                            fp16_scales=sc)
+    _compare(whole, _slabs(make, Q, case.n, nslabs, scales), 12, case.n, SL.step_local_overlap)
+
+    m = syn.MhdCase(n=16)
+    Qm = syn.mhd_fields(m)
+    wm = lbx.State(W.mhd_scheme(m, lbx.FP32_SHIFT), Qm)
+    slabs = _slabs(lambda c, o, sc: W.mhd_scheme(m, lbx.FP32_SHIFT, extent=(16, 16, c), slab_origin=o,
+                                                 slab_planes_global=16), Qm, 16, nslabs)
+    for s in slabs:
+        s.state.set_staging(lbx.STAGE_BULK)
+    _compare(wm, slabs, 6, 16, SL.step_local_overlap)
+
+
+def test_overlapped_exchange_with_time_dependent_fields():
+    """The homogenized NSF's moving porosity reads the device step counter: the pieces of a
+    step and the commit keep it in order across the two streams."""
+    hc = syn.HcnsfPaperCase(n=16)
+    Q = hc.table().augmented(syn.coords((16, 16, 16)), 0.0)
+    whole = lbx.State(W.hcnsf_scheme(hc, lbx.FP64, forced=True), Q)
+
+    def make(c, o, sc):
+        return W.hcnsf_scheme(hc, lbx.FP64, forced=True, extent=(16, 16, c), slab_origin=o, slab_planes_global=16)
+    _compare(whole, _slabs(make, Q, 16, 2), 5, 16, SL.step_local_overlap)
+
