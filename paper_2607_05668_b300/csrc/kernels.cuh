@@ -146,6 +146,21 @@ __device__ __forceinline__ float ld_again(const __half* p) {
 __device__ __forceinline__ void store_f64(double* p, double v) { *p = v; }
 __device__ __forceinline__ void store_f64(float* p, double v) { *p = (float)v; }
 __device__ __forceinline__ void store_f64(__half* p, double v) { *p = __double2half(v); }
+// The same, returning whether the stored value is finite (float16 storage overflows to inf).
+__device__ __forceinline__ bool store_f64_finite(double* p, double v) {
+  *p = v;
+  return isfinite(v);
+}
+__device__ __forceinline__ bool store_f64_finite(float* p, double v) {
+  const float f = (float)v;
+  *p = f;
+  return isfinite(f);
+}
+__device__ __forceinline__ bool store_f64_finite(__half* p, double v) {
+  const __half h = __double2half(v);
+  *p = h;
+  return !__hisinf(h) && !__hisnan(h);
+}
 
 __device__ __forceinline__ void st_out(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st_out(float* p, float v) { *p = v; }
@@ -1590,23 +1605,20 @@ __global__ void k_face(typename St::S* __restrict__ A, typename St::S* __restric
 }
 
 // --------------------------------------------------------------------------- init
-// Populations at the (shifted) equilibrium of Q (FP64): node x computes its equilibrium
-// once and writes population i where the pull of the first step reads it, x - c_i.
-// With maxbits != null it also records max |value| per component (for float16 scales).
+// One node of k_init; with `check` it also returns the node's closed-form wave-speed bound
+// of the initial fields and whether every value it stored is finite.
 template <class Lat, template <typename> class SysT, class St>
-__global__ void k_init(const double* __restrict__ Qf, typename St::S* __restrict__ A,
-                       const KParams<double> p, const double* __restrict__ feq0,
-                       unsigned long long* maxbits, int write, int plane0) {
+__device__ __forceinline__ void init_node(const double* __restrict__ Qf, typename St::S* __restrict__ A,
+                                          const KParams<double>& p, const double* __restrict__ feq0,
+                                          unsigned long long* maxbits, int write, int x, int y, int z, bool check,
+                                          double& speed, bool& finite) {
   using Sys = SysT<double>;
   constexpr int K = Sys::K, Q = Lat::Q, D = Lat::D;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= p.nx) return;
-  // planes plane0 .. of the last axis (the whole grid from plane0 = 0)
-  const int y = (int)blockIdx.y + (D == 2 ? plane0 : 0), z = (int)blockIdx.z + (D == 3 ? plane0 : 0);
   const size_t plane = (size_t)p.ncell;
   const size_t cell = ((size_t)z * p.ny + y) * p.nx + x;
   double dQ[K];
   for (int k = 0; k < K; ++k) dQ[k] = Qf[(size_t)k * plane + cell] - p.Q0[k];
+  if (check) speed = Sys::max_speed(p.prm, p.Q0, dQ);
   double Phi[K][D], Src[K];
   eval_node<SysT>(p, x, y, z, 0.0, dQ, Phi, Src);      // the initial state is at t = 0
   // destination of population i: the pull at node x reads x - c_i, so the node y = x
@@ -1644,8 +1656,39 @@ __global__ void k_init(const double* __restrict__ Qf, typename St::S* __restrict
                            dxs[Lat::c(i, 0) + 1];
         typename St::S* o = A + eidx<K, Q>(k, i, (unsigned int)dst, (unsigned int)plane);
         if (St::SCALE) v *= p.inv_scale[k];
-        store_f64(o, v);
+        if (check)
+          finite = store_f64_finite(o, v) && finite;
+        else
+          store_f64(o, v);
       }
+    }
+  }
+}
+
+// Populations at the (shifted) equilibrium of Q (FP64): node x computes its equilibrium
+// once and writes population i where the pull of the first step reads it, x - c_i.
+// With maxbits != null it also records max |value| per component (for float16 scales).
+// With chk != null it records the checks of lbx_init: chk[0] = max over nodes of the
+// closed-form wave-speed bound of the initial fields (bits of a non-negative double),
+// chk[1] += 1 per warp that stored a non-finite value.
+template <class Lat, template <typename> class SysT, class St>
+__global__ void k_init(const double* __restrict__ Qf, typename St::S* __restrict__ A,
+                       const KParams<double> p, const double* __restrict__ feq0,
+                       unsigned long long* maxbits, int write, int plane0, unsigned long long* chk) {
+  constexpr int D = Lat::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  // planes plane0 .. of the last axis (the whole grid from plane0 = 0)
+  const int y = (int)blockIdx.y + (D == 2 ? plane0 : 0), z = (int)blockIdx.z + (D == 3 ? plane0 : 0);
+  double speed = 0.0;
+  bool finite = true;
+  if (x < p.nx) init_node<Lat, SysT, St>(Qf, A, p, feq0, maxbits, write, x, y, z, chk != nullptr, speed, finite);
+  if (chk != nullptr) {
+    // whole warps (block sizes are multiples of 32; idle lanes contribute 0 and finite)
+    for (int o = 16; o > 0; o >>= 1) speed = fmax(speed, __shfl_xor_sync(0xffffffffu, speed, o));
+    const bool any_bad = __any_sync(0xffffffffu, !finite);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&chk[0], (unsigned long long)__double_as_longlong(speed));
+      if (any_bad) atomicAdd(&chk[1], 1ull);
     }
   }
 }
@@ -1739,7 +1782,6 @@ __global__ void k_scatter(const double* __restrict__ fin, typename St::S* __rest
 //   0  sums:   acc0 = sum Q_k, acc3 = count of non-finite Q_k
 //   1  norms:  acc0 = sum (Q_k - R_k)^2, acc1 = sum R_k^2, acc2 = max|Q_k - R_k|, acc3 = max|R_k|
 //   2  subchar: acc2[0] = max over nodes of the closed-form wave-speed bound
-//   3  modes 0 and 2 in one pass (the checks of lbx_init)
 constexpr int RED_THREADS = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1781,13 +1823,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename St::S* __
       }
       Qv[k] = St::SHIFT ? s : s - p.Q0[k];     // fluctuation
     }
-    if (mode == 0 || mode == 3) {
+    if (mode == 0) {
       for (int k = 0; k < K; ++k) {
         const double q = Qv[k] + p.Q0[k];
         a0[k] += q;
         a3[k] += isfinite(q) ? 0.0 : 1.0;
       }
-      if (mode == 3) a2[0] = fmax(a2[0], Sys::max_speed(p.prm, p.Q0, Qv));
     } else if (mode == 1) {
       for (int k = 0; k < K; ++k) {
         const double r = Qref[(size_t)k * plane + cell];

@@ -687,7 +687,7 @@ static void plane_chunk(const lbx_scheme& s, int j, int nch, int* p0, int* np) {
 
 // fields Qh (host) -> dQ (device) chunk by chunk, each chunk's equilibrium populations
 // written as soon as its planes have arrived
-static cudaError_t init_pipelined(lbx_state* st, const double* Qh, double* dQ) {
+static cudaError_t init_pipelined(lbx_state* st, const double* Qh, double* dQ, unsigned long long* chk) {
   const lbx_scheme& s = st->sch;
   const int P = s.sys.D == 3 ? s.nz : s.ny, nch = std::min(P, kCopyChunks);
   const size_t pc = s.sys.D == 3 ? (size_t)s.nx * s.ny : (size_t)s.nx;
@@ -705,7 +705,7 @@ static cudaError_t init_pipelined(lbx_state* st, const double* Qh, double* dQ) {
     }
     if (!e) e = cudaEventRecord(ev[j], cs);
     if (!e) e = cudaStreamWaitEvent(st->stream, ev[j], 0);
-    if (!e) e = st->ops.init_planes(st, dQ, st->fa, p0, np);
+    if (!e) e = st->ops.init_planes(st, dQ, st->fa, p0, np, chk);
   }
   const cudaError_t e1 = cudaStreamSynchronize(cs), e2 = cudaStreamSynchronize(st->stream);
   for (int j = 0; j < nch; ++j)
@@ -953,7 +953,7 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
     unsigned long long* dmax = nullptr;
     CKI(cudaMalloc(&dmax, sizeof(unsigned long long) * K));
     cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long) * K, st->stream);
-    if (!e) e = st->ops.init(st, dQ, st->fa, dmax, 0);
+    if (!e) e = st->ops.init(st, dQ, st->fa, dmax, 0, nullptr);
     unsigned long long hm[KMAX];
     if (!e) e = cudaMemcpyAsync(hm, dmax, sizeof(unsigned long long) * K, cudaMemcpyDeviceToHost, st->stream);
     if (!e) e = cudaStreamSynchronize(st->stream);
@@ -976,27 +976,29 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
     }
     refresh_params(st);
   }
+  // the init kernel records the checks of the initial state (two words in the reduction
+  // result buffer): the closed-form wave-speed bound of the fields and non-finite stores
+  unsigned long long* chk = reinterpret_cast<unsigned long long*>(st->d_red_out);
+  CKI(cudaMemsetAsync(chk, 0, 2 * sizeof(unsigned long long), st->stream));
   if (pipelined) {
-    CKI(init_pipelined(st, Q, dQ));
+    CKI(init_pipelined(st, Q, dQ, chk));
   } else {
-    CKI(st->ops.init(st, dQ, st->fa, nullptr, 1));
-    CKI(cudaStreamSynchronize(st->stream));
+    CKI(st->ops.init(st, dQ, st->fa, nullptr, 1, chk));
   }
+  unsigned long long hchk[2] = {0, 0};
+  CKI(cudaMemcpyAsync(hchk, chk, sizeof(hchk), cudaMemcpyDeviceToHost, st->stream));
+  CKI(cudaStreamSynchronize(st->stream));
   if (!q_on_device && !mapped) {
     cudaFree(dQ);
     dQ = nullptr;
   }
   st->cur_a = true;
-  {
-    // finite check and, unless waived, the sub-characteristic bound: one pass over the
-    // populations (reduction mode 3)
-    const bool subchar = !sch->d.allow_subchar_violation;
-    double sums[KMAX * 4];
-    if ((rc = run_reduce(st, nullptr, subchar ? 3 : 0, sums))) return bail(rc);
-    for (int k = 0; k < K; ++k)
-      if (sums[4 * k + 3] != 0.0) return bail(fail(LBX_ERR_NONFINITE, "lbx_init: non-finite initial field"));
-    const double ms = sch->lam * sums[2];
-    if (subchar && !(ms <= std::sqrt(sch->cs2)))
+  if (hchk[1] != 0) return bail(fail(LBX_ERR_NONFINITE, "lbx_init: non-finite initial field"));
+  if (!sch->d.allow_subchar_violation) {
+    double speed;
+    memcpy(&speed, &hchk[0], sizeof(speed));
+    const double ms = sch->lam * speed;
+    if (!(ms <= std::sqrt(sch->cs2)))
       return bail(fail(LBX_ERR_SUBCHAR, "lbx_init: sub-characteristic bound violated: (dt/dx) max speed %.6g > c_s %.6g",
                        ms, std::sqrt(sch->cs2)));
   }

@@ -265,7 +265,7 @@ extern "C" lbx_status lbx_batch_create(const lbx_scheme* const* schemes, int n, 
       lbx_state v;
       make_view(b, j, &v);
       e = cudaMemcpyAsync(dQ, Q[j], sizeof(double) * b->K * b->sch[j].ncell, cudaMemcpyHostToDevice, b->stream);
-      if (e == cudaSuccess) e = b->ops.init(&v, dQ, b->at(b->fa, j), nullptr, 1);
+      if (e == cudaSuccess) e = b->ops.init(&v, dQ, b->at(b->fa, j), nullptr, 1, nullptr);
       if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     }
     cudaFree(dQ);

@@ -38,7 +38,9 @@ inline bool time_dependent(const lbx_scheme& s) {
 
 struct Ops {
   cudaError_t (*step)(const lbx_state*, const void* A, void* B, int rel, cudaStream_t);
-  cudaError_t (*init)(const lbx_state*, const double* Q, void* A, unsigned long long* maxbits, int write);
+  // chk: null, or two words the init checks accumulate into (k_init)
+  cudaError_t (*init)(const lbx_state*, const double* Q, void* A, unsigned long long* maxbits, int write,
+                      unsigned long long* chk);
   cudaError_t (*gather)(const lbx_state*, const void* A, double* Qout, double* fout);
   cudaError_t (*scatter)(const lbx_state*, const double* fin, void* A);
   cudaError_t (*reduce)(const lbx_state*, const void* A, const double* Qref, double* partials, int nblk, int mode);
@@ -58,7 +60,8 @@ struct Ops {
   cudaError_t (*face)(const lbx_state*, void* A, void* up, void* dn, int pack, cudaStream_t);
   int face_nf;         // velocities crossing one face (c_a = +1 along the slab axis)
   // init / moments of the planes plane0 .. plane0 + nplanes - 1 of the last axis
-  cudaError_t (*init_planes)(const lbx_state*, const double* Q, void* A, int plane0, int nplanes);
+  cudaError_t (*init_planes)(const lbx_state*, const double* Q, void* A, int plane0, int nplanes,
+                             unsigned long long* chk);
   cudaError_t (*gather_planes)(const lbx_state*, const void* A, double* Qout, int plane0, int nplanes);
 };
 

@@ -141,9 +141,10 @@ struct OpsImpl {
       }
     }
   }
-  static cudaError_t init(const lbx_state* st, const double* Q, void* A, unsigned long long* maxbits, int write) {
+  static cudaError_t init(const lbx_state* st, const double* Q, void* A, unsigned long long* maxbits, int write,
+                          unsigned long long* chk) {
     dim3 b = block(st->sch), g = grid(st->sch, b);
-    k_init<Lat, SysT, St><<<g, b, 0, st->stream>>>(Q, (S*)A, st->pd, st->d_feq0, maxbits, write, 0);
+    k_init<Lat, SysT, St><<<g, b, 0, st->stream>>>(Q, (S*)A, st->pd, st->d_feq0, maxbits, write, 0, chk);
     return cudaGetLastError();
   }
   static cudaError_t gather(const lbx_state* st, const void* A, double* Qout, double* fout) {
@@ -156,9 +157,10 @@ struct OpsImpl {
   static dim3 plane_grid(const lbx_scheme& s, dim3 b, int nplanes) {
     return dim3((s.nx + b.x - 1) / b.x, Lat::D == 3 ? s.ny : nplanes, Lat::D == 3 ? nplanes : 1);
   }
-  static cudaError_t init_planes(const lbx_state* st, const double* Q, void* A, int plane0, int nplanes) {
+  static cudaError_t init_planes(const lbx_state* st, const double* Q, void* A, int plane0, int nplanes,
+                                 unsigned long long* chk) {
     dim3 b = block(st->sch), g = plane_grid(st->sch, b, nplanes);
-    k_init<Lat, SysT, St><<<g, b, 0, st->stream>>>(Q, (S*)A, st->pd, st->d_feq0, nullptr, 1, plane0);
+    k_init<Lat, SysT, St><<<g, b, 0, st->stream>>>(Q, (S*)A, st->pd, st->d_feq0, nullptr, 1, plane0, chk);
     return cudaGetLastError();
   }
   static cudaError_t gather_planes(const lbx_state* st, const void* A, double* Qout, int plane0, int nplanes) {

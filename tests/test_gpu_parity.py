@@ -302,6 +302,15 @@ def test_nonfinite_detection_on_host_injected_nan():
     assert e.value.name == "ERR_NONFINITE"
 
 
+def test_nonfinite_float16_store_at_init_is_detected():
+    """Given float16 scales far too small, the init's stores overflow binary16: the init
+    kernel's own check reports it (the fields themselves are finite)."""
+    case = syn.NsfCase(n=32)
+    with pytest.raises(lbx.LbxError) as e:
+        lbx.State(W.nsf_scheme(case, lbx.FP16_SCALED, fp16_scales=[2.0 ** -24] * 10), syn.nsf_fields(case))
+    assert e.value.name == "ERR_NONFINITE"
+
+
 # ---------------------------------------------------------- sub-characteristic check
 
 def test_subchar_maxwell_bound_f_le_cs_over_c():
