@@ -71,6 +71,8 @@ struct KParams {
   int pf_kind;                 // prescribed coefficient fields (HCNSF): 0 none, 1 uniform, 2 advected
   T pf[8];                     // their parameters (see prescribed_fields)
   T pf_src_dt, pf_flux_dt;     // time offsets of the fields inside the source and the flux
+  const T* pf_trig;            // advected solid: sin, cos of the field times of this step (flux,
+                               // then source; k_pf_trig), or null: computed per node
   const T* pf_tab;             // advected solid, float64: sin, cos of 2 pi x_d per node index
                                // along each axis, [sx nx][cx nx][sy ny][cy ny][sz nz][cz nz];
                                // null = computed
@@ -267,12 +269,10 @@ __device__ __forceinline__ SolidAt<T> solid_here(const KParams<T>& p, int x, int
   return solid_at(p, xc);
 }
 
-// The fields at time t from the node's time-independent part.
+// The fields at time t (st, ct = sin t, cos t) from the node's time-independent part.
 template <typename T, typename U>
-__device__ __forceinline__ void solid_fields(const KParams<T>& p, const U (&x)[3], const SolidAt<U>& a, T t,
-                                             U (&cf)[4]) {
-  T st, ct;
-  sincos(t, &st, &ct);
+__device__ __forceinline__ void solid_fields(const KParams<T>& p, const U (&x)[3], const SolidAt<U>& a, T t, T st,
+                                             T ct, U (&cf)[4]) {
   const T osc = p.pf[3];
   cf[1] = a.r[0] * U(ct) + U(p.pf[4]) + U(osc * st) * a.c[2];
   cf[2] = a.r[1] * U(ct) + U(p.pf[5]) + U(osc * ct) * a.c[0];
@@ -293,7 +293,46 @@ __device__ __forceinline__ void prescribed_fields(const KParams<T>& p, const U (
     cf[1] = cf[2] = cf[3] = U(T(0));
     return;
   }
-  solid_fields(p, x, solid_at(p, x), t, cf);
+  T st, ct;
+  sincos(t, &st, &ct);
+  solid_fields(p, x, solid_at(p, x), t, st, ct, cf);
+}
+
+// Time of the prescribed fields inside the flux or the source of a float64 step: t_n + offset
+// with t_n = step dt, each rounded on its own (no contraction), so that the step kernels and
+// k_pf_trig, which precomputes the sines once per step, agree to the bit.
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+// The table serves the float64 step (two sincos per node on the FP64 pipe: 4.5 % of the
+// HCNSF FP64 step); in float32 the per-node sincos measured as fast as the table and its
+// extra launch, so the float32 steps keep their own expression t + offset.
+template <typename T>
+__device__ __forceinline__ T field_time(T t, T off) {
+  if constexpr (sizeof(T) == 8) return add_rn(t, off);
+  return t + off;
+}
+template <typename T>
+__device__ __forceinline__ void field_sincos(const KParams<T>& p, T tl, int level, T& st, T& ct) {
+  if constexpr (sizeof(T) == 8) {
+    if (p.pf_trig != nullptr) {
+      st = p.pf_trig[2 * level];
+      ct = p.pf_trig[2 * level + 1];
+      return;
+    }
+  }
+  sincos(tl, &st, &ct);
+}
+
+// sin and cos of the advected solid's flux and source times of step *step_ptr + rel (one
+// thread; launched before each step kernel of a state with a moving solid).
+template <typename T>
+__global__ void k_pf_trig(const long long* __restrict__ step_ptr, int rel, T dt, T off_flux, T off_src,
+                          T* __restrict__ out) {
+  const T t = mul_rn(T(*step_ptr + rel), dt);
+  sincos(add_rn(t, off_flux), &out[0], &out[1]);
+  sincos(add_rn(t, off_src), &out[2], &out[3]);
 }
 
 // Flux and source at a node at state time t (the family's eval()), with the prescribed
@@ -305,18 +344,25 @@ __device__ __forceinline__ void eval_node(const KParams<T>& p, int x, int y, int
   if constexpr (NcfOf<Sys>::value > 0) {
     const T xc[3] = {T(x) * p.dx, T(y + p.oy) * p.dx, T(z + p.oz) * p.dx};
     T cf[NcfOf<Sys>::value];
-    if (p.pf_src_dt != p.pf_flux_dt && p.pf_kind == 2) {
-      // two time levels of a moving solid: the spatial factors are shared
+    if (p.pf_kind == 2) {
+      // a moving solid: the spatial factors are shared by the two time levels
       const SolidAt<T> a = solid_here(p, x, y, z, xc);
-      T cs[NcfOf<Sys>::value];
-      solid_fields(p, xc, a, t + p.pf_flux_dt, cf);
-      solid_fields(p, xc, a, t + p.pf_src_dt, cs);
-      Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cs);
+      const T tf = field_time(t, p.pf_flux_dt);
+      T sf, cfl;
+      field_sincos(p, tf, 0, sf, cfl);
+      solid_fields(p, xc, a, tf, sf, cfl, cf);
+      if (p.pf_src_dt != p.pf_flux_dt) {
+        const T ts = field_time(t, p.pf_src_dt);
+        T ss, csl;
+        field_sincos(p, ts, 1, ss, csl);
+        T cs[NcfOf<Sys>::value];
+        solid_fields(p, xc, a, ts, ss, csl, cs);
+        Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cs);
+      } else {
+        Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cf);
+      }
     } else {
-      if (sizeof(T) == 8 && p.pf_kind == 2)
-        solid_fields(p, xc, solid_here(p, x, y, z, xc), t + p.pf_flux_dt, cf);
-      else
-        prescribed_fields(p, xc, t + p.pf_flux_dt, cf);
+      prescribed_fields(p, xc, t + p.pf_flux_dt, cf);
       Sys::eval(p.prm, p.Q0, dQ, Phi, Src, cf, cf);
     }
   } else {

@@ -767,6 +767,7 @@ static void free_state(lbx_state* st) {
   cudaFree(st->d_mms_tab64);
   cudaFree(st->d_mms_tab32);
   cudaFree(st->d_pf_tab64);
+  cudaFree(st->d_pf_trig);
   delete st;
 }
 
@@ -912,6 +913,8 @@ extern "C" lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_
     }
     CKI(cudaMalloc(&st->d_pf_tab64, sizeof(double) * t.size()));
     CKI(cudaMemcpyAsync(st->d_pf_tab64, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, st->stream));
+    CKI(cudaMalloc(&st->d_pf_trig, 4 * sizeof(double)));
+    CKI(cudaMemsetAsync(st->d_pf_trig, 0, 4 * sizeof(double), st->stream));
     CKI(cudaStreamSynchronize(st->stream));
   }
   if (sch->d.mms == LBX_MMS_FOURIER) {

@@ -99,6 +99,7 @@ struct lbx_state {
   double* d_mms_tab64 = nullptr;
   float* d_mms_tab32 = nullptr;
   double* d_pf_tab64 = nullptr;  // sin/cos tables of the advected solid (HCNSF, float64 step)
+  void* d_pf_trig = nullptr;     // sin/cos of the advected solid's field times of a step (4 values)
   double scale[lbx::KMAX];
   lbx::KParams<double> pd;
   lbx::KParams<float> pf;

@@ -94,10 +94,21 @@ struct OpsImpl {
   // Register-resident kernels use 128-thread blocks (narrower grids: the smallest multiple
   // of 32 covering nx); staged kernels use st->block in {32, 64, 128} and the staging
   // st->staging resolves to.
+  // A moving solid's sines of this step's field times, once per float64 step before the
+  // step kernel (a launch over a plane range computes them per node instead: its pieces run
+  // on two streams).
+  static cudaError_t prepare_trig(const lbx_state* st, KParams<C>& p, int rel, cudaStream_t strm) {
+    if (sizeof(C) != 8 || p.pf_kind != 2 || st->d_pf_trig == nullptr || st->plane_n > 0) return cudaSuccess;
+    C* out = reinterpret_cast<C*>(st->d_pf_trig);
+    k_pf_trig<C><<<1, 1, 0, strm>>>(p.step_ptr, rel, p.dt, p.pf_flux_dt, p.pf_src_dt, out);
+    p.pf_trig = out;
+    return cudaGetLastError();
+  }
   static cudaError_t step(const lbx_state* st, const void* A, void* B, int rel, cudaStream_t strm) {
     KParams<C> p = st->pc<C>();
     p.step_rel = rel;
     p.plane0 = st->plane_lo;
+    if (cudaError_t e = prepare_trig(st, p, rel, strm)) return e;
     if (p.mms_modes != nullptr) {
       // mode-table forcing: its own instantiation, 128 threads, per-thread staging
       const size_t bytes = StepMode<Lat, SysT, St, 128>::smem_bytes;
@@ -232,6 +243,7 @@ struct OpsImpl {
   static cudaError_t step_inplace(const lbx_state* st, void* F, int kind, int rel, cudaStream_t strm) {
     KParams<C> p = st->pc<C>();
     p.step_rel = rel;
+    if (cudaError_t e = prepare_trig(st, p, rel, strm)) return e;
     if (p.mms_modes != nullptr)
       return kind == 1 ? launch_inplace<true, 1>(st, F, p, strm) : launch_inplace<true, 2>(st, F, p, strm);
     if constexpr (MODE == MODE_SMEM) {
