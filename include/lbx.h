@@ -281,9 +281,11 @@ lbx_status lbx_init(const lbx_scheme* sch, const double* Q, int q_on_device, voi
 size_t lbx_state_buffer_bytes(const lbx_scheme* sch);
 
 /* Advance 0 <= n <= 2^30 steps of Eq. lbe_update (fused pull collide-and-stream),
- * asynchronous.  Fails with LBX_ERR_NONFINITE without stepping if a previous check found
- * a NaN/Inf.  With graph replay enabled, the n launches are recorded into a CUDA graph
- * the first time this (n, buffer parity) occurs and replayed afterwards. */
+ * asynchronous: one step kernel per step (FP64 states with an advected solid also launch
+ * a one-thread kernel before each step, which computes the sines of the step's field
+ * times).  Fails with LBX_ERR_NONFINITE without stepping if a previous check found a
+ * NaN/Inf.  With graph replay enabled, the launches are recorded into a CUDA graph the
+ * first time this (n, buffer parity) occurs and replayed afterwards. */
 lbx_status lbx_step(lbx_state* st, int64_t n);
 /* Threads per block (32, 64 or 128; default 128) of the step kernels that stage a node's
  * populations in shared memory (K q s > 360 bytes or K > 12: MHD on D3Q19, FP64 NSF, the
