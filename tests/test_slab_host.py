@@ -265,3 +265,10 @@ def test_adjoint_local_exchange_reproduces_the_whole_grid(nslabs):
             SL._adj_exchange(slabs, lams, faces, None, reverse=reverse)
         ok = all(np.array_equal(lam, whole[-1][:, :, o:o + c, :]) for lam, (o, c) in zip(lams, spans))
         assert ok == (reverse or nslabs <= 2)
+
+
+def test_slab_adjoint_checks_its_arguments_before_any_device_work():
+    class _Ring:
+        pass
+    with pytest.raises(ValueError, match="one slab per process"):
+        SL.slab_adjoint([object(), object()], [], [], 4, 2, ring=_Ring())
